@@ -1,0 +1,371 @@
+"""Plain, slow, FP64 CPU oracle for the order-18 hyperpower iteration.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module; only
+the tests, the package's smoke check and the benchmark's CPU-baseline leg call
+it.  It shares no code with the CUDA path: the only thing both sides consume is
+the seeded matrices from the input generator module.
+
+What it computes (Pan, Soleymani, Zhao, "Highly efficient computation of
+generalized inverse of a matrix"):
+
+* the outer inverse X = A^(2)_{R(G),N(G)} (Section 1.1, Eq. 1 and the
+  lemma after it) reached from X0 = alpha*G (Section 2);
+* each loop forms the order-18 hyperpower step the obvious way,
+  X_{k+1} = X_k (I + R_k + R_k^2 + ... + R_k^17), R_k = I - A X_k
+  (Eq. hyper18), with 17 successive products -- NOT the factorised seven-product
+  step, which the CUDA path uses and which this module only contains so that a
+  test can show the two agree (Eq. PM, Section 2);
+* the stabilised loop appends X <- X A X (Eq. PM-modified, Section 7), switched
+  on once the step size falls below a threshold (the switching recipe closing
+  Section 7);
+* stopping by the relative Frobenius step, or by the criterion of Eq.
+  stopreliable (Section 4), and stopping once a step in the converged regime
+  is no longer a convergent step (the first remark closing Section 6: the
+  iteration is not self-correcting for generalized inverses);
+* initial values of Section 4: alpha*A^T, A^l/Tr(A^{l+1}), alpha*G, with
+  alpha = 2/(sigma_1^2 + sigma_r^2) or 1/(||A||_1 ||A||_inf);
+* residual checks: the Penrose equations and the Drazin equations;
+* the computational order of convergence of Eq. COC (Section 8).
+
+Readings where the paper is silent or garbled are listed in the design notes
+of the repository; each is also stated where it is used below.
+
+All functions accept float64 numpy arrays.  The step, X0 and norm helpers are
+written with ``@``, ``+`` and ``abs`` only, so they also run on numpy object
+arrays of mpmath numbers (the 150-digit reproduction of Table 1).
+
+Parity: every function here is pinned by ``tests/test_oracle.py`` (closed-form
+inverses from the generators' factors, the printed Table 1 values, the Penrose
+and Drazin equations, exact coefficient identities, Newton-Schulz at p = 2).
+"""
+
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+P_ORDER = 18  # order of the method (Eq. hyper18)
+
+
+# ----------------------------------------------------------------------------
+# small helpers (generic over float64 and object arrays)
+# ----------------------------------------------------------------------------
+
+def _eye(n: int, like: np.ndarray) -> np.ndarray:
+    if like.dtype == object:
+        one = like.flat[0] * 0 + 1
+        zero = like.flat[0] * 0
+        e = np.full((n, n), zero, dtype=object)
+        for i in range(n):
+            e[i, i] = one
+        return e
+    return np.eye(n, dtype=like.dtype)
+
+
+def fro(x: np.ndarray):
+    """Frobenius norm sqrt(sum x_ij^2)."""
+    return (x * x).sum() ** 0.5
+
+
+def norm_inf(x: np.ndarray):
+    """Infinity norm: the largest absolute row sum (used in Section 8, Example 1)."""
+    return max(abs(v).sum() for v in x)
+
+
+def trace(x: np.ndarray):
+    return sum(x[i, i] for i in range(x.shape[0]))
+
+
+def matpow(A: np.ndarray, l: int) -> np.ndarray:
+    """A^l by l-1 successive products (A^0 = I)."""
+    out = _eye(A.shape[0], A)
+    for _ in range(l):
+        out = out @ A
+    return out
+
+
+# ----------------------------------------------------------------------------
+# the coefficients of the factorisation (Section 2)
+# ----------------------------------------------------------------------------
+
+def coefficients() -> dict:
+    """Closed forms printed in Section 2 for the parameters of Eq. hyper18-33,
+    Eq. simplify1 and Eq. simplify2.  Only the factorised reference step and
+    the coefficient pins use them; the oracle's own step does not."""
+    s93 = math.sqrt(93.0)
+    a1 = 5.0 / 496.0 * (31.0 + s93)
+    a2 = (3.0 + s93) / 8.0
+    a3 = 0.5
+    b1 = -5.0 / 496.0 * (s93 - 31.0)
+    b2 = (3.0 - s93) / 8.0
+    mu = 3.0 / 8.0
+    psi = 321.0 / 1984.0
+    q = math.sqrt(27.0 - 2.0 * s93)
+    c1 = (q + 1.0) / 4.0
+    c2 = (1.0 - q) / 4.0
+    c3 = (5.0 * s93 - 93.0) / 496.0
+    d1 = (-93.0 - 5.0 * s93) / 496.0
+    d2 = -s93 / 4.0
+    return dict(a1=a1, a2=a2, a3=a3, b1=b1, b2=b2, b3=a3, mu=mu, psi=psi,
+                c1=c1, c2=c2, c3=c3, d1=d1, d2=d2)
+
+
+# ----------------------------------------------------------------------------
+# the step
+# ----------------------------------------------------------------------------
+
+def choose_side(m: int, n: int) -> str:
+    """Which residual to form.  Reading: the paper writes R = I - AX (m x m);
+    in exact arithmetic X (I - AX)^j = (I - XA)^j X, so when n < m the same
+    iterate comes from the n x n residual I - XA multiplied from the left.
+    'right' (the paper's own form) when m <= n, else 'left'."""
+    return "right" if m <= n else "left"
+
+
+def residual(A: np.ndarray, X: np.ndarray, side: str) -> np.ndarray:
+    """R = I - A X (right, m x m; Eq. Hyperpower1) or I - X A (left, n x n)."""
+    if side == "right":
+        P = A @ X
+    elif side == "left":
+        P = X @ A
+    else:
+        raise ValueError(side)
+    return _eye(P.shape[0], P) - P
+
+
+def hyperpower_step(A: np.ndarray, X: np.ndarray, p: int = P_ORDER, side: str = "right") -> np.ndarray:
+    """One loop of the order-p hyperpower method, formed naively (Eq. Hyperpower1;
+    Eq. hyper18 for p = 18): S = I + R + R^2 + ... + R^{p-1} by p-1 successive
+    products, then X S (right) or S X (left)."""
+    R = residual(A, X, side)
+    term = _eye(R.shape[0], R)
+    S = term.copy()
+    for _ in range(p - 1):
+        term = term @ R
+        S = S + term
+    return X @ S if side == "right" else S @ X
+
+
+def pm_step(A: np.ndarray, X: np.ndarray, side: str = "right") -> np.ndarray:
+    """The factorised seven-product loop of Eq. PM.  Reference for the pin
+    'factorised step equals the naive step'; the oracle's solve never calls it."""
+    c = coefficients()
+    R = residual(A, X, side)
+    I = _eye(R.shape[0], R)
+    R2 = R @ R
+    R4 = R2 @ R2
+    M = (I + c["c1"] * R2 + R4) @ (I + c["c2"] * R2 + R4)
+    T = M + c["c3"] * R2
+    S = M + c["d1"] * R2 + c["d2"] * R4
+    Y = (I + R) @ (T @ S + c["mu"] * R2 + c["psi"] * R4)
+    return X @ Y if side == "right" else Y @ X
+
+
+def stabilised_step(A: np.ndarray, X: np.ndarray, p: int = P_ORDER, side: str = "right") -> np.ndarray:
+    """Eq. PM-modified: X_{k+1/2} = hyperpower step, X_{k+1} = X_{k+1/2} A X_{k+1/2}."""
+    Xh = hyperpower_step(A, X, p, side)
+    return Xh @ A @ Xh
+
+
+# ----------------------------------------------------------------------------
+# initial values and scaling (Section 4)
+# ----------------------------------------------------------------------------
+
+def x0_moore_penrose(A: np.ndarray, alpha) -> np.ndarray:
+    """X0 = alpha A^T (real case of alpha A^*; Section 4, Theorem 6.2)."""
+    return alpha * A.T.copy()
+
+
+def x0_general(G: np.ndarray, alpha) -> np.ndarray:
+    """X0 = alpha G (Section 2)."""
+    return alpha * G
+
+
+def x0_drazin(A: np.ndarray, l: int, alpha=None) -> np.ndarray:
+    """X0 = A^l / Tr(A^{l+1}) (Section 4), or alpha A^l when alpha is given."""
+    Al = matpow(A, l)
+    if alpha is None:
+        tr = trace(Al @ A)
+        if not tr > 0:
+            raise ValueError("Tr(A^{l+1}) must be positive for the trace scaling")
+        alpha = 1 / tr
+    return alpha * Al
+
+
+def alpha_pan_schreiber(sigma_1: float, sigma_r: float) -> float:
+    """alpha = 2 / (sigma_1^2 + sigma_r^2) (Section 4), sigma_1 >= sigma_r > 0 the
+    extreme nonzero singular values of A (reading of 'eigenvalues of GA' for
+    G = A^T: those eigenvalues are sigma_i^2, so the formula squares the
+    singular values)."""
+    return 2.0 / (sigma_1 ** 2 + sigma_r ** 2)
+
+
+def alpha_rectangular(A: np.ndarray) -> float:
+    """alpha = 1 / (||A||_1 ||A||_inf) (Section 4's recipe for rectangular A)."""
+    n1 = float(np.abs(A).sum(axis=0).max())
+    ninf = float(np.abs(A).sum(axis=1).max())
+    return 1.0 / (n1 * ninf)
+
+
+# ----------------------------------------------------------------------------
+# cleanup projections (build-introduced; motivated by Theorems 6.2 and 7.1)
+# ----------------------------------------------------------------------------
+
+def cleanup_moore_penrose(A: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """X <- (XA)^T X (AX)^T.  With X = A^+ + E in the SVD blocks of Theorem 6.2
+    this removes the E12, E21 and E22 blocks to first order (they are the parts
+    the iteration does not contract) and leaves A^+ fixed."""
+    return (X @ A).T @ X @ (A @ X).T
+
+
+def cleanup_drazin(A: np.ndarray, X: np.ndarray, l: int) -> np.ndarray:
+    """X <- A^l X^{2l+1} A^l; fixes A^D (A^D = A^l (A^D)^{2l+1} A^l) and
+    projects an approximate Drazin inverse back onto R(A^l), N(A^l)."""
+    Al = matpow(A, l)
+    return Al @ matpow(X, 2 * l + 1) @ Al
+
+
+# ----------------------------------------------------------------------------
+# stopping (Section 4 and the remarks closing Section 6)
+# ----------------------------------------------------------------------------
+
+STOP_REL_FRO = 0   # ||X_{k+1} - X_k||_F / ||X_k||_F < tol
+STOP_PAPER = 1     # ||X_{k+1} - X_k||_F / (18^k alpha) < tol   (Eq. stopreliable)
+
+
+def stop_measure(Xn: np.ndarray, X: np.ndarray, k: int, alpha: float, mode: int) -> float:
+    d = float(fro(Xn - X))
+    if mode == STOP_REL_FRO:
+        nx = float(fro(X))
+        return d / nx if nx > 0 else math.inf
+    if mode == STOP_PAPER:
+        return d / (P_ORDER ** k * alpha)
+    raise ValueError(mode)
+
+
+@dataclass
+class SolveInfo:
+    iters: int = 0                    # loops whose result was kept
+    loops_run: int = 0                # loops executed (one more when stopped at the minimum)
+    stabilised_loops: int = 0
+    status: str = "maxiter"           # 'converged' | 'minimum' | 'maxiter' | 'nonfinite'
+    history: list = field(default_factory=list)   # stop measure of every loop
+    finished: bool = False            # cleanup + one loop applied
+
+
+def solve(A: np.ndarray, X0: np.ndarray, tol: float = 1e-12, stop: int = STOP_REL_FRO,
+          alpha: float = 1.0, max_iter: int = 100, variant: str = "plain",
+          switch_tol: float = 1e-3, floor_guard: float = 1e-3, side: str | None = None,
+          p: int = P_ORDER, finish: str | None = None, drazin_index: int = 0):
+    """Run the iteration from X0 (Theorem 3.1 / Section 7).
+
+    Loop k computes X_{k+1} from X_k with the naive order-p step (plus X A X
+    once the stabilised variant is switched on) and the stop measure e_k.
+    * e_k < tol: keep X_{k+1}, status 'converged'.
+    * Plain loops, reading of the first remark closing Section 6: once the
+      previous step e_{k-1} was below ``floor_guard`` (the converged regime,
+      where order 18 makes e_k of order e_{k-1}^18), a step with
+      e_k >= e_{k-1}^2 is not a convergent step but rounding growth (Theorem
+      6.2: the null block grows by 18 per loop); keep X_k, status 'minimum'.
+    * Stabilised loops (Theorem 7.1: rounding no longer grows): stop when the
+      step no longer decreases, e_k >= e_{k-1}; keep X_k, status 'minimum'.
+    * Stabilised variant: loops after the first one with e < switch_tol use
+      the extra X A X (the Pan-Schreiber switch closing Section 7).
+    * ``finish`` ('moore_penrose' or 'drazin'): after the loop ends, apply the
+      cleanup projection and one more plain loop.  The projection removes the
+      blocks Theorem 6.2 shows are not contracted (E12, E21 persist, E22
+      grows); the loop after it contracts the range block again.
+    max_iter defaults to the paper's 100 (Section 8).
+    """
+    X, info = _iterate(A, X0, tol, stop, alpha, max_iter, variant, switch_tol, floor_guard,
+                       side or choose_side(*A.shape), p)
+    if finish is not None and info.status != "nonfinite":
+        if finish == "moore_penrose":
+            Xc = cleanup_moore_penrose(A, X)
+        elif finish == "drazin":
+            Xc = cleanup_drazin(A, X, drazin_index)
+        else:
+            raise ValueError(finish)
+        X = hyperpower_step(A, Xc, p, side or choose_side(*A.shape))
+        info.finished = True
+    return X, info
+
+
+def _iterate(A, X0, tol, stop, alpha, max_iter, variant, switch_tol, floor_guard, side, p):
+    info = SolveInfo()
+    X = X0
+    prev = math.inf
+    stabilise = False
+    for k in range(max_iter):
+        stabilised_now = stabilise
+        if stabilised_now:
+            Xn = stabilised_step(A, X, p, side)
+            info.stabilised_loops += 1
+        else:
+            Xn = hyperpower_step(A, X, p, side)
+        e = stop_measure(Xn, X, k, alpha, stop)
+        info.loops_run = k + 1
+        info.history.append(e)
+        if not math.isfinite(e):
+            info.status = "nonfinite"
+            info.iters = k
+            return X, info
+        if e < tol:
+            info.status = "converged"
+            info.iters = k + 1
+            return Xn, info
+        stalled = (e >= prev) if stabilised_now else (prev < floor_guard and e >= prev * prev)
+        if stalled:
+            info.status = "minimum"
+            info.iters = k
+            return X, info
+        if variant == "stabilised" and e < switch_tol:
+            stabilise = True
+        prev = e
+        X = Xn
+    info.iters = max_iter
+    return X, info
+
+
+# ----------------------------------------------------------------------------
+# residual checks (Eq. 1; the Penrose and Drazin equations; Eq. COC)
+# ----------------------------------------------------------------------------
+
+def penrose_residuals(A: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """Relative Frobenius residuals of the four Penrose equations:
+    ||AXA - A||/||A||, ||XAX - X||/||X||, ||(AX)^T - AX||/||AX||, ||(XA)^T - XA||/||XA||."""
+    AX = A @ X
+    XA = X @ A
+    return np.array([
+        float(fro(AX @ A - A) / fro(A)),
+        float(fro(X @ AX - X) / fro(X)),
+        float(fro(AX.T - AX) / fro(AX)),
+        float(fro(XA.T - XA) / fro(XA)),
+    ])
+
+
+def drazin_residuals(A: np.ndarray, X: np.ndarray, l: int) -> np.ndarray:
+    """Relative residuals of XAX = X, AX = XA and A^{l+1} X = A^l."""
+    Al = matpow(A, l)
+    AX = A @ X
+    return np.array([
+        float(fro(X @ AX - X) / fro(X)),
+        float(fro(AX - X @ A) / fro(AX)),
+        float(fro(Al @ AX - Al) / fro(Al)),
+    ])
+
+
+def coc(d: list) -> list:
+    """Computational order of convergence (Eq. COC, Section 8).  The printed
+    fraction is garbled; read as rho_k = ln(d_{k+1}/d_k) / ln(d_k/d_{k-1}) with
+    d_k = ||X_k - X_{k-1}||_inf."""
+    out = []
+    for k in range(1, len(d) - 1):
+        out.append(math.log(d[k + 1] / d[k]) / math.log(d[k] / d[k - 1]))
+    return out
+
+
+def relative_error(X: np.ndarray, Xref: np.ndarray) -> float:
+    return float(fro(X - Xref) / fro(Xref))
