@@ -1,0 +1,200 @@
+/*
+ * pinv.h -- C ABI of the GB300 library for generalized inverses by the
+ * order-18 hyperpower iteration of Pan, Soleymani and Zhao.
+ *
+ * The problem (Section 2): given A (m x n, real), an initial value
+ * X0 = alpha * G with R(G) = T and N(G) = S, compute the outer inverse
+ * X = A^(2)_{T,S}, the unique X with XAX = X, R(X) = T, N(X) = S (Section 1.1,
+ * Eq. 1 and the lemma after it).  The Moore-Penrose inverse (G = A^T) and the
+ * Drazin inverse (G = A^l, l >= ind(A)) are the special cases named in
+ * Section 1.1; Section 4 gives their initial values.
+ *
+ * Each loop is the factorised seven-product step of Eq. PM (Section 2):
+ *   R = I - AX,  R2 = R R,  R4 = R2 R2,
+ *   M = (I + c1 R2 + R4)(I + c2 R2 + R4),
+ *   T = M + c3 R2,  S = M + d1 R2 + d2 R4,
+ *   X <- X (I + R)(T S + mu R2 + psi R4),
+ * which equals X (I + R + ... + R^17) (Eq. hyper18).  The stabilised variant
+ * appends X <- X A X (Eq. PM-modified, Section 7).  When n < m the library
+ * forms the n x n residual I - XA and multiplies from the left; in exact
+ * arithmetic this is the same iterate.
+ *
+ * Conventions for every entry point
+ *   - Matrices are dense, real, row-major, with a leading dimension (elements
+ *     between consecutive rows) >= the number of columns.
+ *   - Unless a field says otherwise, matrix pointers are DEVICE pointers on the
+ *     handle's device, owned by the caller; the library never frees them and
+ *     reads/writes them only on the stream passed to the call.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.
+ *   - Return value: PINV_OK or one of the PINV_ERR_* codes below.  On error the
+ *     output matrix is unspecified and info->status (when info is given)
+ *     repeats the code.
+ *   - Device work never waits without a bound; no entry point traps or faults
+ *     the GPU on bad input: arguments are validated on the host first.
+ */
+#ifndef PINV_H
+#define PINV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------------ codes */
+#define PINV_OK              0
+#define PINV_PENDING         1   /* pinv_poll: request not finished yet           */
+#define PINV_ERR_ARG        -1   /* bad shape, leading dimension, kind, pointer   */
+#define PINV_ERR_BUDGET     -2   /* workspace would exceed the HBM budget         */
+#define PINV_ERR_NONFINITE  -3   /* NaN/Inf in a stop norm (bad input or blow-up) */
+#define PINV_ERR_DIVERGED   -4   /* step size grew past the divergence guard      */
+#define PINV_ERR_MAXITER    -5   /* max_iter loops without meeting a stop rule    */
+#define PINV_ERR_TIMEOUT    -6   /* a bounded device-side wait gave up            */
+#define PINV_ERR_CUDA       -7   /* a CUDA runtime call failed                    */
+#define PINV_ERR_UNKNOWN_ID -8   /* pinv_poll: no such request                     */
+
+/* ------------------------------------------------------------------ enums */
+typedef enum {
+    PINV_MOORE_PENROSE = 0,  /* G = A^T (Section 4; Theorem 6.2)                  */
+    PINV_DRAZIN        = 1,  /* G = A^l, l = drazin_index >= ind(A) (Section 4)   */
+    PINV_OUTER_G       = 2   /* caller's G (n x m): A^(2)_{R(G),N(G)} (Thm 3.1)   */
+} pinv_kind;
+
+typedef enum {
+    PINV_STOP_REL_FRO = 0,   /* ||X_{k+1} - X_k||_F / ||X_k||_F < tol             */
+    PINV_STOP_PAPER   = 1    /* ||X_{k+1} - X_k||_F / (18^k alpha) < tol (Eq. stopreliable) */
+} pinv_stop;
+
+typedef enum {
+    PINV_PREC_FP64       = 0, /* every product in FP64                             */
+    PINV_PREC_MIXED_BF16 = 1, /* early loops BF16 tensor cores, FP32-class finish, FP64 final */
+    PINV_PREC_MIXED_FP8  = 2, /* reserved: FP8 early loops (returns PINV_ERR_ARG)  */
+    PINV_PREC_FP32       = 3  /* FP32-class (split TF32 tensor-core) loops, FP64 final */
+} pinv_prec;
+
+typedef enum {
+    PINV_VARIANT_PLAIN      = 0, /* Eq. PM, 7 products per loop                    */
+    PINV_VARIANT_STABILIZED = 1  /* Eq. PM-modified once the step < switch_tol:
+                                    7 + 2 products per loop (the paper counts 8)   */
+} pinv_variant;
+
+typedef enum {
+    PINV_FINISH_NONE  = 0,
+    PINV_FINISH_CLEAN = 1    /* after the loops: projection X <- (XA)^T X (AX)^T
+                                (Moore-Penrose) or A^l X^{2l+1} A^l (Drazin),
+                                then one more FP64 loop                           */
+} pinv_finish;
+
+/* --------------------------------------------------------------- structs */
+typedef struct {
+    size_t hbm_budget_bytes; /* cap on the handle's workspace; 0 = no cap           */
+    int    device;           /* CUDA device ordinal                                 */
+    int    reserved[6];
+} pinv_config;
+
+typedef struct {
+    int m, n;                /* A is m x n; X and G are n x m                       */
+    const double *A; int lda;
+    double       *X; int ldx;/* output; also the initial value when kind == OUTER_G
+                                and G == NULL is not allowed                         */
+    const double *G; int ldg;/* PINV_OUTER_G only                                    */
+    pinv_kind    kind;
+    int          drazin_index;  /* l >= ind(A), required for PINV_DRAZIN            */
+    double       alpha;      /* > 0: X0 = alpha * G.  0: the Section 4 recipe:
+                                1/(||A||_1 ||A||_inf) for MOORE_PENROSE/OUTER_G,
+                                1/Tr(A^{l+1}) for DRAZIN                             */
+    double       tol;        /* stop tolerance for `stop`                            */
+    pinv_stop    stop;
+    int          max_iter;   /* 0 = the paper's 100 (Section 8)                      */
+    pinv_prec    prec;
+    pinv_variant variant;
+    double       switch_tol; /* stabilised switch threshold; 0 = 1e-3                */
+    pinv_finish  finish;
+    int          host_buffers; /* 1: A, G and X are HOST pointers; the call copies
+                                  A (and G) in and X out on `stream` and returns
+                                  after the copy back has completed                  */
+    int          check;      /* 1: fill info->penrose / info->drazin (extra GEMMs)   */
+    int          profile;    /* 1: time every GEMM with CUDA events on `stream`
+                                (info->gemm_ms / gemm_flops)                         */
+    int          reserved[3];
+} pinv_desc;
+
+#define PINV_HISTORY 128
+typedef struct {
+    int    status;           /* PINV_OK or the error code                           */
+    int    iters;            /* loops whose result was kept                          */
+    int    loops_run;        /* loops executed (one more when stopped at a minimum)  */
+    int    stabilized_loops;
+    int    stop_reason;      /* 0 tol met, 1 minimum, 2 max_iter                     */
+    int    side;             /* 0: right residual I - AX (m x m); 1: left I - XA     */
+    double rel_step;         /* stop measure of the last kept loop                   */
+    double alpha;            /* alpha actually used                                  */
+    double penrose[4];       /* relative ||AXA-A||, ||XAX-X||, ||AX-(AX)^T||, ||XA-(XA)^T|| */
+    double drazin[3];        /* relative ||XAX-X||, ||AX-XA||, ||A^{l+1}X - A^l||     */
+    float  ms;               /* wall time of the call on the host                    */
+    int    gemms;            /* GEMM launches issued                                  */
+    int    kernels;          /* all kernel launches issued (GEMMs included)          */
+    float  gemm_ms;          /* desc->profile: summed CUDA-event time of the GEMMs   */
+    double gemm_flops;       /* algorithmic flops of those GEMMs (2 M N K each)       */
+    double history[PINV_HISTORY];  /* stop measure per loop                          */
+    signed char precision[PINV_HISTORY]; /* per loop: 0 FP64, 1 BF16, 3 FP32-class  */
+} pinv_info;
+
+typedef struct pinv_handle pinv_handle;
+
+/* ---------------------------------------------------------- entry points */
+
+/* Create a handle on cfg->device (cfg may be NULL: device 0, no budget).
+ * The handle owns its workspace (grown on demand, kept between calls) and a
+ * pinned host block for stop-norm readback.  PINV_ERR_CUDA if the device
+ * cannot be used. */
+int  pinv_init(pinv_handle **h, const pinv_config *cfg);
+
+/* Release the handle and its workspace; never touches caller memory. */
+void pinv_destroy(pinv_handle *h);
+
+/* Solve one problem (Theorem 3.1 / Section 7): X0 from kind/alpha (Section 4),
+ * then loops of Eq. PM (or Eq. PM-modified after the switch) until the stop
+ * rule: the measure < tol; or, in the converged regime, a plain loop whose
+ * step is not at least quadratically smaller than the previous one, or a
+ * stabilised loop whose step did not decrease (the remark closing Section 6:
+ * the iteration is not self-correcting; the iterate before that loop is
+ * kept).  Blocks the host until the result is in desc->X.  Not re-entrant on
+ * one handle. */
+int  pinv_solve(pinv_handle *h, const pinv_desc *desc, void *stream, pinv_info *info);
+
+/* Solve `count` independent problems (same kind/prec/variant/stop fields are
+ * read per descriptor).  info may be NULL or an array of `count`. */
+int  pinv_solve_batched(pinv_handle *h, int count, const pinv_desc *descs, void *stream,
+                        pinv_info *infos);
+
+/* Non-blocking: queue a problem for the handle's serving loop and return its
+ * id.  The descriptor is copied; A, G and X must stay valid until pinv_poll
+ * reports a final status.  PINV_ERR_BUDGET if the problem's workspace alone
+ * exceeds the budget. */
+int  pinv_submit(pinv_handle *h, const pinv_desc *desc, uint64_t *request_id);
+
+/* Drive the serving loop one round and report request `id`: PINV_PENDING, or
+ * the final status with *info filled (the request is then forgotten). */
+int  pinv_poll(pinv_handle *h, uint64_t request_id, pinv_info *info);
+
+/* Section 4's scaling for rectangular A: *alpha = 1/(||A||_1 ||A||_inf),
+ * computed on the device; desc->A (device) and shape are read. */
+int  pinv_alpha_estimate(pinv_handle *h, const pinv_desc *desc, void *stream, double *alpha);
+
+/* One loop from X_in to X_out (n x m device buffers, may not alias):
+ * Eq. PM (stabilized = 0) or Eq. PM-modified (stabilized = 1), in `prec`
+ * (FP64 or FP32-class or BF16 products), residual side chosen as in
+ * pinv_solve.  *rel_step (host) receives ||X_out - X_in||_F / ||X_in||_F.
+ * Exposed so one factorised loop can be checked against the naive order-18
+ * step. */
+int  pinv_step(pinv_handle *h, int m, int n, const double *A, int lda,
+               const double *X_in, double *X_out, int ldx,
+               pinv_prec prec, int stabilized, void *stream, double *rel_step);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PINV_H */

@@ -1,0 +1,238 @@
+"""ctypes binding of ``include/pinv.h``: argument marshalling only.
+
+Every step of the computation runs in ``libpinv.so``; this module converts
+torch tensors (device memory and streams) or numpy arrays (host buffers) into
+the C structures and back.  If the library has not been built it raises: there
+is no other code path.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libpinv.so")
+
+PINV_OK, PINV_PENDING = 0, 1
+ERRORS = {-1: "PINV_ERR_ARG", -2: "PINV_ERR_BUDGET", -3: "PINV_ERR_NONFINITE", -4: "PINV_ERR_DIVERGED",
+          -5: "PINV_ERR_MAXITER", -6: "PINV_ERR_TIMEOUT", -7: "PINV_ERR_CUDA", -8: "PINV_ERR_UNKNOWN_ID"}
+KIND = {"moore_penrose": 0, "drazin": 1, "outer_g": 2}
+STOP = {"rel_fro": 0, "paper": 1}
+PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3}
+VARIANT = {"plain": 0, "stabilized": 1}
+FINISH = {None: 0, "none": 0, "clean": 1}
+HISTORY = 128
+
+EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_batched", "pinv_submit",
+           "pinv_poll", "pinv_alpha_estimate", "pinv_step")
+
+
+class Config(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("device", C.c_int), ("reserved", C.c_int * 6)]
+
+
+class Desc(C.Structure):
+    _fields_ = [("m", C.c_int), ("n", C.c_int),
+                ("A", C.c_void_p), ("lda", C.c_int),
+                ("X", C.c_void_p), ("ldx", C.c_int),
+                ("G", C.c_void_p), ("ldg", C.c_int),
+                ("kind", C.c_int), ("drazin_index", C.c_int),
+                ("alpha", C.c_double), ("tol", C.c_double), ("stop", C.c_int),
+                ("max_iter", C.c_int), ("prec", C.c_int), ("variant", C.c_int),
+                ("switch_tol", C.c_double), ("finish", C.c_int), ("host_buffers", C.c_int),
+                ("check", C.c_int), ("profile", C.c_int), ("reserved", C.c_int * 3)]
+
+
+class Info(C.Structure):
+    _fields_ = [("status", C.c_int), ("iters", C.c_int), ("loops_run", C.c_int),
+                ("stabilized_loops", C.c_int), ("stop_reason", C.c_int), ("side", C.c_int),
+                ("rel_step", C.c_double), ("alpha", C.c_double),
+                ("penrose", C.c_double * 4), ("drazin", C.c_double * 3), ("ms", C.c_float),
+                ("gemms", C.c_int), ("kernels", C.c_int), ("gemm_ms", C.c_float),
+                ("gemm_flops", C.c_double), ("history", C.c_double * HISTORY),
+                ("precision", C.c_byte * HISTORY)]
+
+    def to_dict(self) -> dict:
+        n = min(self.loops_run, HISTORY)
+        return dict(status=self.status, iters=self.iters, loops_run=self.loops_run,
+                    stabilized_loops=self.stabilized_loops, stop_reason=self.stop_reason,
+                    side="left" if self.side else "right", rel_step=self.rel_step, alpha=self.alpha,
+                    penrose=list(self.penrose), drazin=list(self.drazin), ms=self.ms,
+                    gemms=self.gemms, kernels=self.kernels, gemm_ms=self.gemm_ms,
+                    gemm_flops=self.gemm_flops, history=list(self.history[:n]),
+                    precision=list(self.precision[:n]))
+
+
+_lib = None
+
+
+def load() -> C.CDLL:
+    """Load libpinv.so (built in-tree by ``build.py``); raise if it is absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: run paper_1604_07893_gb300.build.build() first")
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    lib.pinv_init.argtypes = [P(C.c_void_p), P(Config)]
+    lib.pinv_destroy.argtypes = [C.c_void_p]
+    lib.pinv_destroy.restype = None
+    lib.pinv_solve.argtypes = [C.c_void_p, P(Desc), C.c_void_p, P(Info)]
+    lib.pinv_solve_batched.argtypes = [C.c_void_p, C.c_int, P(Desc), C.c_void_p, P(Info)]
+    lib.pinv_submit.argtypes = [C.c_void_p, P(Desc), P(C.c_uint64)]
+    lib.pinv_poll.argtypes = [C.c_void_p, C.c_uint64, P(Info)]
+    lib.pinv_alpha_estimate.argtypes = [C.c_void_p, P(Desc), C.c_void_p, P(C.c_double)]
+    lib.pinv_step.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                              C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
+    for name in EXPORTS:
+        if name != "pinv_destroy":
+            getattr(lib, name).restype = C.c_int
+    _lib = lib
+    return lib
+
+
+class PinvError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}")
+        self.code = code
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+def _dev_ptr(t) -> int:
+    import torch
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
+        raise TypeError("expected a CUDA float64 tensor")
+    if t.stride(1) != 1:
+        raise ValueError("matrices must be row-major (unit column stride)")
+    return t.data_ptr()
+
+
+class Handle:
+    """pinv_init / pinv_destroy."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        lib = load()
+        self._lib = lib
+        self._h = C.c_void_p()
+        cfg = Config(hbm_budget_bytes=hbm_budget_bytes, device=device)
+        rc = lib.pinv_init(C.byref(self._h), C.byref(cfg))
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_init")
+
+    def close(self):
+        if self._h:
+            self._lib.pinv_destroy(self._h)
+            self._h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- helpers
+    @staticmethod
+    def make_desc(A, X, *, kind="moore_penrose", G=None, drazin_index=0, alpha=0.0, tol=1e-12,
+                  stop="rel_fro", max_iter=0, prec="fp64", variant="plain", switch_tol=0.0,
+                  finish=None, check=False, host=False, profile=False) -> Desc:
+        if host:
+            import numpy as np
+            for M in (A, X) + ((G,) if G is not None else ()):
+                if not (isinstance(M, np.ndarray) and M.dtype == np.float64 and M.flags.c_contiguous):
+                    raise TypeError("host buffers must be C-contiguous float64 numpy arrays")
+            a_ptr, x_ptr = A.ctypes.data, X.ctypes.data
+            g_ptr = G.ctypes.data if G is not None else None
+            lda, ldx, ldg = A.shape[1], X.shape[1], (G.shape[1] if G is not None else 0)
+        else:
+            a_ptr, x_ptr = _dev_ptr(A), _dev_ptr(X)
+            g_ptr = _dev_ptr(G) if G is not None else None
+            lda, ldx = A.stride(0), X.stride(0)
+            ldg = G.stride(0) if G is not None else 0
+        m, n = A.shape
+        if tuple(X.shape) != (n, m):
+            raise ValueError("X must be n x m")
+        return Desc(m=m, n=n, A=a_ptr, lda=lda, X=x_ptr, ldx=ldx, G=g_ptr, ldg=ldg,
+                    kind=KIND[kind], drazin_index=drazin_index, alpha=alpha, tol=tol,
+                    stop=STOP[stop], max_iter=max_iter, prec=PREC[prec], variant=VARIANT[variant],
+                    switch_tol=switch_tol, finish=FINISH[finish], host_buffers=1 if host else 0,
+                    check=1 if check else 0, profile=1 if profile else 0)
+
+    # ------------------------------------------------------------ entry points
+    def solve(self, A, X=None, *, stream=None, raise_on_error=True, **kw):
+        """pinv_solve.  A: CUDA float64 tensor (or numpy with host=True).
+        Returns (X, info dict)."""
+        host = kw.get("host", False)
+        if X is None:
+            if host:
+                import numpy as np
+                X = np.empty((A.shape[1], A.shape[0]), dtype=np.float64)
+            else:
+                import torch
+                X = torch.empty((A.shape[1], A.shape[0]), dtype=torch.float64, device=A.device)
+        d = self.make_desc(A, X, **kw)
+        info = Info()
+        st = 0 if host and stream is None else _stream_ptr(stream)
+        rc = self._lib.pinv_solve(self._h, C.byref(d), C.c_void_p(st), C.byref(info))
+        if rc != PINV_OK and raise_on_error:
+            raise PinvError(rc, "pinv_solve")
+        return X, info.to_dict()
+
+    def solve_batched(self, As, Xs=None, *, stream=None, **kw):
+        import torch
+        if Xs is None:
+            Xs = [torch.empty((A.shape[1], A.shape[0]), dtype=torch.float64, device=A.device) for A in As]
+        descs = (Desc * len(As))(*[self.make_desc(A, X, **kw) for A, X in zip(As, Xs)])
+        infos = (Info * len(As))()
+        rc = self._lib.pinv_solve_batched(self._h, len(As), descs, C.c_void_p(_stream_ptr(stream)), infos)
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_solve_batched")
+        return Xs, [i.to_dict() for i in infos]
+
+    def submit(self, A, X, **kw) -> int:
+        d = self.make_desc(A, X, **kw)
+        rid = C.c_uint64()
+        rc = self._lib.pinv_submit(self._h, C.byref(d), C.byref(rid))
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_submit")
+        return rid.value
+
+    def poll(self, rid: int):
+        """Returns None while pending, else (status, info dict)."""
+        info = Info()
+        rc = self._lib.pinv_poll(self._h, C.c_uint64(rid), C.byref(info))
+        if rc == PINV_PENDING:
+            return None
+        return rc, info.to_dict()
+
+    def alpha_estimate(self, A, *, stream=None) -> float:
+        import torch
+        X = torch.empty((1, 1), dtype=torch.float64, device=A.device)
+        d = Desc(m=A.shape[0], n=A.shape[1], A=_dev_ptr(A), lda=A.stride(0), X=X.data_ptr(), ldx=1)
+        out = C.c_double()
+        rc = self._lib.pinv_alpha_estimate(self._h, C.byref(d), C.c_void_p(_stream_ptr(stream)), C.byref(out))
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_alpha_estimate")
+        return out.value
+
+    def step(self, A, X_in, X_out=None, *, prec="fp64", stabilized=False, stream=None):
+        """pinv_step: one loop of Eq. PM (or PM-modified).  Returns (X_out, rel_step)."""
+        import torch
+        if X_out is None:
+            X_out = torch.empty_like(X_in)
+        m, n = A.shape
+        rel = C.c_double()
+        rc = self._lib.pinv_step(self._h, m, n, C.c_void_p(_dev_ptr(A)), A.stride(0),
+                                 C.c_void_p(_dev_ptr(X_in)), C.c_void_p(_dev_ptr(X_out)),
+                                 X_in.stride(0), PREC[prec], 1 if stabilized else 0,
+                                 C.c_void_p(_stream_ptr(stream)), C.byref(rel))
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_step")
+        return X_out, rel.value

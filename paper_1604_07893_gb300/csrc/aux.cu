@@ -1,0 +1,187 @@
+// Small FP64 kernels around the GEMMs: initial values (Section 4), the
+// deterministic reduction of stop-norm partials, and residual norms.
+//
+// All reductions are two-level with a fixed CTA count and a fixed order, so a
+// result is bitwise reproducible from run to run.
+
+#include "common.h"
+
+namespace pinv {
+namespace {
+
+constexpr int RED_CTAS = 256;     // fixed first-level width of every reduction
+constexpr int RED_THREADS = 256;
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sh[w];
+    __syncthreads();
+    return s;  // valid in thread 0
+}
+
+__device__ __forceinline__ double block_max(double v, double* sh) {
+#pragma unroll
+    for (int off = 16; off; off >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, off));
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, sh[w]);
+    __syncthreads();
+    return s;
+}
+
+__global__ void reduce_pairs_kernel(const double* p, int count, double* out) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        a += p[2 * i];
+        b += p[2 * i + 1];
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) { out[0] = a; out[1] = b; }
+}
+
+__global__ void transpose_scale_kernel(int m, int n, const double* A, int lda, double alpha,
+                                       double* Y, int ldy) {
+    __shared__ double t[32][33];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;  // bx over n (cols of A), by over m
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int i = by + r, j = bx + threadIdx.x;
+        if (i < m && j < n) t[r][threadIdx.x] = A[(size_t)i * lda + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int j = bx + r, i = by + threadIdx.x;   // Y[j][i] = alpha * A[i][j]
+        if (i < m && j < n) Y[(size_t)j * ldy + i] = alpha * t[threadIdx.x][r];
+    }
+}
+
+__global__ void scale_copy_kernel(int rows, int cols, const double* X, int ldx, double alpha,
+                                  double* Y, int ldy) {
+    size_t total = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / cols, j = e % cols;
+        Y[i * ldy + j] = alpha * X[i * ldx + j];
+    }
+}
+
+// Partial column sums (block handles a strip of columns over all rows) and row sums.
+__global__ void row_abs_max_kernel(int m, int n, const double* A, int lda, double* part) {
+    __shared__ double sh[32];
+    double best = 0.0;
+    for (int i = blockIdx.x; i < m; i += gridDim.x) {
+        double s = 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) s += fabs(A[(size_t)i * lda + j]);
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) best = fmax(best, s);
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
+}
+
+__global__ void col_abs_max_kernel(int m, int n, const double* A, int lda, double* part) {
+    __shared__ double sh[32];
+    double best = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += fabs(A[(size_t)i * lda + j]);
+        best = fmax(best, s);
+    }
+    best = block_max(best, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
+}
+
+__global__ void max_kernel(const double* part, int count, double* out) {
+    __shared__ double sh[32];
+    double v = 0.0;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) v = fmax(v, part[i]);
+    v = block_max(v, sh);
+    if (threadIdx.x == 0) *out = v;
+}
+
+__global__ void trace_product_kernel(int n, const double* P, int ldp, const double* Q, int ldq,
+                                     double* part) {
+    __shared__ double sh[32];
+    double s = 0.0;
+    size_t total = (size_t)n * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / n, j = e % n;
+        s += P[i * ldp + j] * Q[j * ldq + i];
+    }
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = s, part[2 * blockIdx.x + 1] = 0.0;
+}
+
+__global__ void diff_norms_kernel(int rows, int cols, const double* P, int ldp, const double* Q,
+                                  int ldq, int transQ, double* part) {
+    __shared__ double sh[32];
+    double a = 0.0, b = 0.0;
+    size_t total = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total;
+         e += (size_t)gridDim.x * blockDim.x) {
+        size_t i = e / cols, j = e % cols;
+        double p = P[i * ldp + j];
+        double q = transQ ? Q[j * ldq + i] : Q[i * ldq + j];
+        a += (p - q) * (p - q);
+        b += p * p;
+    }
+    a = block_sum(a, sh);
+    b = block_sum(b, sh);
+    if (threadIdx.x == 0) part[2 * blockIdx.x] = a, part[2 * blockIdx.x + 1] = b;
+}
+
+}  // namespace
+
+void reduce_pairs(const double* partials, int count, double* out, cudaStream_t st) {
+    reduce_pairs_kernel<<<1, RED_THREADS, 0, st>>>(partials, count, out);
+}
+
+void transpose_scale(int m, int n, const double* A, int lda, double alpha, double* Y, int ldy,
+                     cudaStream_t st) {
+    dim3 grid((n + 31) / 32, (m + 31) / 32), block(32, 8);
+    transpose_scale_kernel<<<grid, block, 0, st>>>(m, n, A, lda, alpha, Y, ldy);
+}
+
+void scale_copy(int rows, int cols, const double* X, int ldx, double alpha, double* Y, int ldy,
+                cudaStream_t st) {
+    size_t total = (size_t)rows * cols;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    if (blocks < 1) blocks = 1;
+    scale_copy_kernel<<<blocks, 256, 0, st>>>(rows, cols, X, ldx, alpha, Y, ldy);
+}
+
+void norms_1_inf(int m, int n, const double* A, int lda, double* out, double* scratch,
+                 cudaStream_t st) {
+    col_abs_max_kernel<<<RED_CTAS, RED_THREADS, 0, st>>>(m, n, A, lda, scratch);
+    max_kernel<<<1, RED_THREADS, 0, st>>>(scratch, RED_CTAS, out);
+    row_abs_max_kernel<<<RED_CTAS, RED_THREADS, 0, st>>>(m, n, A, lda, scratch + RED_CTAS);
+    max_kernel<<<1, RED_THREADS, 0, st>>>(scratch + RED_CTAS, RED_CTAS, out + 1);
+}
+
+void trace_of_product(int n, const double* P, int ldp, const double* Q, int ldq, double* out,
+                      double* scratch, cudaStream_t st) {
+    trace_product_kernel<<<RED_CTAS, RED_THREADS, 0, st>>>(n, P, ldp, Q, ldq, scratch);
+    reduce_pairs_kernel<<<1, RED_THREADS, 0, st>>>(scratch, RED_CTAS, out);
+}
+
+void diff_norms(int rows, int cols, const double* P, int ldp, const double* Q, int ldq,
+                bool transQ, double* out, double* scratch, cudaStream_t st) {
+    diff_norms_kernel<<<RED_CTAS, RED_THREADS, 0, st>>>(rows, cols, P, ldp, Q, ldq,
+                                                        transQ ? 1 : 0, scratch);
+    reduce_pairs_kernel<<<1, RED_THREADS, 0, st>>>(scratch, RED_CTAS, out);
+}
+
+int diff_norms_scratch_pairs() { return RED_CTAS; }
+
+}  // namespace pinv

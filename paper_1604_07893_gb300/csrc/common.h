@@ -1,0 +1,65 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+namespace pinv {
+
+// One output of a fused GEMM epilogue:
+//   out[i][j] = a_acc * acc[i][j] + a_s1 * s1[i][j] + a_s2 * s2[i][j] + (i == j ? a_id : 0)
+// `out` may be null (nothing stored; useful when only the norms are wanted).
+struct EpiTerm {
+    double* out;
+    int ld;
+    double a_acc, a_s1, a_s2, a_id;
+};
+
+// Fused epilogue of a GEMM C = op(A) op(B): up to three outputs built from the
+// accumulator, two side inputs of C's shape and the identity.  When `partials`
+// is set, every CTA writes two FP64 partial sums in CTA order:
+//   partials[2*cta]   = sum (out0 - s1)^2      (||X_{k+1} - X_k||_F^2 when s1 = X_k)
+//   partials[2*cta+1] = sum s1^2               (||X_k||_F^2)
+struct Epilogue {
+    const double* s1; int ld1;
+    const double* s2; int ld2;
+    EpiTerm o[3];
+    int nout;
+    double* partials;
+};
+
+inline Epilogue epi_none() {
+    Epilogue e{};
+    e.nout = 0;
+    return e;
+}
+
+// C (M x N) = op(A) (M x K) * op(B) (K x N), all row-major FP64.
+// transA: A is stored K x M (element (i,k) at A[k*lda + i]); likewise transB.
+// Returns the number of CTAs launched (the partials count) or -1 on a launch error.
+int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
+             const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st);
+int gemm_f64_ctas(int M, int N);
+
+// Deterministic sum of `count` (pair) partials into out[0..1] (device).
+void reduce_pairs(const double* partials, int count, double* out, cudaStream_t st);
+
+// Y (n x m, ldy) = alpha * A^T, A m x n (lda).
+void transpose_scale(int m, int n, const double* A, int lda, double alpha, double* Y, int ldy,
+                     cudaStream_t st);
+// Y = alpha * X (rows x cols).
+void scale_copy(int rows, int cols, const double* X, int ldx, double alpha, double* Y, int ldy,
+                cudaStream_t st);
+// out[0] = max column abs sum (||A||_1), out[1] = max row abs sum (||A||_inf).
+void norms_1_inf(int m, int n, const double* A, int lda, double* out, double* scratch,
+                 cudaStream_t st);
+// out[0] = sum_ij P[i][j] * Q[j][i]  (trace of P Q), n x n.
+void trace_of_product(int n, const double* P, int ldp, const double* Q, int ldq, double* out,
+                      double* scratch, cudaStream_t st);
+// out[0] = sum (P - Q)^2, out[1] = sum P^2 (Q may be P^T when `transQ`).
+void diff_norms(int rows, int cols, const double* P, int ldp, const double* Q, int ldq,
+                bool transQ, double* out, double* scratch, cudaStream_t st);
+int diff_norms_scratch_pairs();
+
+}  // namespace pinv

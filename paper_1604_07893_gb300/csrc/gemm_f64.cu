@@ -1,0 +1,177 @@
+// FP64 GEMM with the fused epilogue used by every product of the iteration.
+//
+// tcgen05 has no FP64 kind, so FP64 products run on the FP64 tensor path
+// through mma.sync m8n8k4 (DMMA).  A 64x64 CTA tile, four warps of 32x32,
+// BK = 16; the next K-slab is fetched into registers while the current one is
+// multiplied from shared memory.  Ragged edges are zero-filled on load and
+// masked on store, so any M, N, K >= 1 works.
+//
+// The epilogue forms the linear combinations of Eq. PM directly from the
+// accumulator (identity subtraction for R = I - AX, the I + c R2 + R4 factors,
+// T, S, the TS + mu R2 + psi R4 sum, the update X + D X) and, optionally, the
+// two Frobenius partial sums of the stop test (Eq. stopreliable / relative
+// step).
+
+#include "common.h"
+
+namespace pinv {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int APAD = 4;   // As row stride BK + APAD doubles: conflict-free fragment reads
+constexpr int BPAD = 4;   // Bs row stride BN + BPAD
+constexpr int THREADS = 128;
+
+__device__ __forceinline__ void dmma(double& c0, double& c1, double a, double b) {
+    asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0,%1}, {%2}, {%3}, {%0,%1};\n"
+                 : "+d"(c0), "+d"(c1)
+                 : "d"(a), "d"(b));
+}
+
+struct GemmArgs {
+    int M, N, K;
+    const double* A; int lda; int transA;
+    const double* B; int ldb; int transB;
+};
+
+__device__ __forceinline__ double loadA(const GemmArgs& g, int i, int k) {
+    if (i >= g.M || k >= g.K) return 0.0;
+    return g.transA ? g.A[(size_t)k * g.lda + i] : g.A[(size_t)i * g.lda + k];
+}
+__device__ __forceinline__ double loadB(const GemmArgs& g, int k, int j) {
+    if (k >= g.K || j >= g.N) return 0.0;
+    return g.transB ? g.B[(size_t)j * g.ldb + k] : g.B[(size_t)k * g.ldb + j];
+}
+
+__global__ void __launch_bounds__(THREADS)
+gemm_f64_kernel(GemmArgs g, Epilogue epi) {
+    __shared__ double As[BM][BK + APAD];
+    __shared__ double Bs[BK][BN + BPAD];
+    __shared__ double red[2][THREADS / 32];
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int wm = warp >> 1, wn = warp & 1;
+    const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+    // Register staging of one K-slab: 1024 A elements and 1024 B elements, 8 each.
+    double ra[8], rb[8];
+    auto fetch = [&](int k0) {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int idx = tid + t * THREADS;
+            int r, k;
+            if (g.transA) { r = idx % BM; k = idx / BM; }   // consecutive threads: consecutive i
+            else          { k = idx % BK; r = idx / BK; }   // consecutive threads: consecutive k
+            ra[t] = loadA(g, m0 + r, k0 + k);
+            int kb, c;
+            if (g.transB) { kb = idx % BK; c = idx / BK; }
+            else          { c = idx % BN; kb = idx / BN; }
+            rb[t] = loadB(g, k0 + kb, n0 + c);
+        }
+    };
+    auto stash = [&]() {
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            int idx = tid + t * THREADS;
+            int r, k;
+            if (g.transA) { r = idx % BM; k = idx / BM; }
+            else          { k = idx % BK; r = idx / BK; }
+            As[r][k] = ra[t];
+            int kb, c;
+            if (g.transB) { kb = idx % BK; c = idx / BK; }
+            else          { c = idx % BN; kb = idx / BN; }
+            Bs[kb][c] = rb[t];
+        }
+    };
+
+    double acc[4][4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+
+    const int ktiles = (g.K + BK - 1) / BK;
+    fetch(0);
+    for (int kt = 0; kt < ktiles; ++kt) {
+        __syncthreads();
+        stash();
+        __syncthreads();
+        if (kt + 1 < ktiles) fetch((kt + 1) * BK);
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 4) {
+            double af[4], bf[4];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) af[i] = As[wm * 32 + i * 8 + (lane >> 2)][kk + (lane & 3)];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) bf[j] = Bs[kk + (lane & 3)][wn * 32 + j * 8 + (lane >> 2)];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) dmma(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
+        }
+    }
+
+    // ---- fused epilogue
+    double sd = 0.0, sx = 0.0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const int row = m0 + wm * 32 + i * 8 + (lane >> 2);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int col = n0 + wn * 32 + j * 8 + 2 * (lane & 3) + h;
+                if (row < g.M && col < g.N) {
+                    const double a = acc[i][j][h];
+                    const double v1 = epi.s1 ? epi.s1[(size_t)row * epi.ld1 + col] : 0.0;
+                    const double v2 = epi.s2 ? epi.s2[(size_t)row * epi.ld2 + col] : 0.0;
+                    const double id = (row == col) ? 1.0 : 0.0;
+#pragma unroll
+                    for (int o = 0; o < 3; ++o) {
+                        if (o < epi.nout) {
+                            const EpiTerm& t = epi.o[o];
+                            double v = t.a_acc * a + t.a_s1 * v1 + t.a_s2 * v2 + t.a_id * id;
+                            if (t.out) t.out[(size_t)row * t.ld + col] = v;
+                            if (o == 0 && epi.partials) {
+                                const double d = v - v1;
+                                sd += d * d;
+                                sx += v1 * v1;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (epi.partials) {
+#pragma unroll
+        for (int off = 16; off; off >>= 1) {
+            sd += __shfl_xor_sync(0xffffffffu, sd, off);
+            sx += __shfl_xor_sync(0xffffffffu, sx, off);
+        }
+        if (lane == 0) { red[0][warp] = sd; red[1][warp] = sx; }
+        __syncthreads();
+        if (tid == 0) {
+            double a = 0.0, b = 0.0;
+            for (int w = 0; w < THREADS / 32; ++w) { a += red[0][w]; b += red[1][w]; }
+            const int cta = blockIdx.y * gridDim.x + blockIdx.x;
+            epi.partials[2 * cta] = a;
+            epi.partials[2 * cta + 1] = b;
+        }
+    }
+}
+
+}  // namespace
+
+int gemm_f64_ctas(int M, int N) { return ((N + BN - 1) / BN) * ((M + BM - 1) / BM); }
+
+int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
+             const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st) {
+    GemmArgs g{M, N, K, A, lda, transA ? 1 : 0, B, ldb, transB ? 1 : 0};
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+    gemm_f64_kernel<<<grid, THREADS, 0, st>>>(g, epi);
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    return grid.x * grid.y;
+}
+
+}  // namespace pinv

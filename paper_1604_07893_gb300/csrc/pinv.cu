@@ -1,0 +1,732 @@
+// Host driver of the C ABI declared in include/pinv.h.
+//
+// One solve = X0 (Section 4) followed by loops of the factorised step of
+// Eq. PM, each a fixed chain of seven fused-epilogue GEMM launches on the
+// caller's stream:
+//   1  R  = I - X A         (left, n x n)      or  I - A X   (right, m x m)
+//   2  R2 = R R
+//   3  R4 = R2 R2,   L1 = I + c1 R2 + R4,   L2 = I + c2 R2 + R4
+//   4  M  = L1 L2 ->  T = M + c3 R2,   S = M + d1 R2 + d2 R4
+//   5  Z  = T S + mu R2 + psi R4
+//   6  D  = R Z + Z - I                    ((I + R) Z = I + D)
+//   7  X' = X + D X         (left)          or  X + X D     (right)
+//      + Frobenius partials of X' - X and X for the stop test.
+// The stabilised loop (Eq. PM-modified) adds X' <- X' A X' as two more GEMMs,
+// ordered so the middle product is the smaller square.  Only the two stop
+// norms come back to the host per loop.
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "../../include/pinv.h"
+#include "common.h"
+#include "mixed.h"
+
+using namespace pinv;
+
+namespace {
+
+// Closed forms of Section 2 for the parameters of Eq. simplify1/simplify2 and
+// Eq. hyper18-33 (c1, c2, c3, d1, d2, mu, psi).
+struct Coef {
+    double c1, c2, c3, d1, d2, mu, psi;
+};
+Coef pm_coefficients() {
+    const double r93 = std::sqrt(93.0);
+    const double q = std::sqrt(27.0 - 2.0 * r93);
+    Coef c;
+    c.c1 = 0.25 * (1.0 + q);
+    c.c2 = 0.25 * (1.0 - q);
+    c.c3 = (5.0 * r93 - 93.0) / 496.0;
+    c.d1 = (-93.0 - 5.0 * r93) / 496.0;
+    c.d2 = -0.25 * r93;
+    c.mu = 3.0 / 8.0;
+    c.psi = 321.0 / 1984.0;
+    return c;
+}
+
+EpiTerm term(double* out, int ld, double a_acc, double a_s1 = 0, double a_s2 = 0, double a_id = 0) {
+    EpiTerm t;
+    t.out = out; t.ld = ld; t.a_acc = a_acc; t.a_s1 = a_s1; t.a_s2 = a_s2; t.a_id = a_id;
+    return t;
+}
+Epilogue epi1(EpiTerm t0, const double* s1 = nullptr, int ld1 = 0, const double* s2 = nullptr,
+              int ld2 = 0) {
+    Epilogue e{};
+    e.s1 = s1; e.ld1 = ld1; e.s2 = s2; e.ld2 = ld2;
+    e.o[0] = t0; e.nout = 1; e.partials = nullptr;
+    return e;
+}
+
+}  // namespace
+
+struct pinv_handle {
+    int device = 0;
+    size_t budget = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    double* pinned = nullptr;  // host pinned readback block
+    double* dsmall = nullptr;  // device: reduction outputs
+    MixedEngine* mixed = nullptr;
+    std::vector<cudaEvent_t> events;  // profiling pool (pairs), created on demand
+    // serving
+    std::mutex mu;
+    uint64_t next_id = 1;
+    struct Request {
+        pinv_desc desc;
+        int status = PINV_PENDING;
+        pinv_info info{};
+    };
+    std::deque<uint64_t> queue;
+    std::map<uint64_t, Request> requests;
+};
+
+namespace {
+
+#define CK(call)                                                                       \
+    do {                                                                               \
+        cudaError_t e_ = (call);                                                       \
+        if (e_ != cudaSuccess) {                                                       \
+            std::fprintf(stderr, "pinv: %s failed: %s (%s:%d)\n", #call,               \
+                         cudaGetErrorString(e_), __FILE__, __LINE__);                  \
+            return PINV_ERR_CUDA;                                                      \
+        }                                                                              \
+    } while (0)
+
+size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Everything one solve needs on the device.
+struct Ctx {
+    pinv_handle* h;
+    cudaStream_t st;
+    int m, n;         // A is m x n
+    int s;            // residual dimension
+    bool left;        // left residual I - XA
+    const double* A; int lda;
+    double* X[3];     // ping, pong, half-step; each n x m, ld = m
+    double* sq[7];    // R R2 R4 L1 L2 T S; s x s, ld = s
+    double* Al;       // A^l (Drazin), n x n
+    double* Ad;       // device copy of A (host_buffers)
+    double* Gd;       // device copy of G (host_buffers)
+    double* big[2];   // max(m,n)^2 scratch for residual checks
+    double* partials; // pair partials
+    double* red;      // reduction scratch (2 * 256 pairs)
+    int gemms = 0;
+    int kernels = 0;
+    bool profile = false;
+    int ev_used = 0;        // event pairs recorded since the last harvest
+    double gemm_flops = 0;
+    float gemm_ms = 0;
+    Coef c;
+};
+
+// Time GEMMs with CUDA events on the launch stream; harvested at sync points.
+int prof_begin(Ctx& c) {
+    if (!c.profile) return -1;
+    auto& ev = c.h->events;
+    if ((int)ev.size() < 2 * (c.ev_used + 1)) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return -1;
+            ev.push_back(e);
+        }
+    }
+    const int slot = c.ev_used++;
+    cudaEventRecord(ev[2 * slot], c.st);
+    return slot;
+}
+void prof_end(Ctx& c, int slot) {
+    if (slot >= 0) cudaEventRecord(c.h->events[2 * slot + 1], c.st);
+}
+void prof_harvest(Ctx& c) {  // stream already synchronised
+    for (int i = 0; i < c.ev_used; ++i) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, c.h->events[2 * i], c.h->events[2 * i + 1]) == cudaSuccess)
+            c.gemm_ms += ms;
+    }
+    c.ev_used = 0;
+}
+
+size_t workspace_bytes(int m, int n, bool drazin, bool host, bool check) {
+    const size_t s = std::min(m, n), big = std::max(m, n);
+    size_t b = 0;
+    b += 3 * align_up(sizeof(double) * n * (size_t)m);
+    b += 7 * align_up(sizeof(double) * s * s);
+    if (drazin) b += align_up(sizeof(double) * n * (size_t)n);
+    if (host) b += 2 * align_up(sizeof(double) * n * (size_t)m);
+    if (check) b += 2 * align_up(sizeof(double) * big * big);
+    const size_t tiles = (size_t)((big + 63) / 64) * ((big + 63) / 64);
+    b += align_up(sizeof(double) * 2 * tiles);
+    b += align_up(sizeof(double) * 2 * 2 * 256);
+    return b;
+}
+
+int ensure_workspace(pinv_handle* h, size_t bytes) {
+    if (h->budget && bytes > h->budget) return PINV_ERR_BUDGET;
+    if (bytes <= h->ws_bytes) return PINV_OK;
+    if (h->ws) {
+        CK(cudaDeviceSynchronize());
+        CK(cudaFree(h->ws));
+        h->ws = nullptr;
+        h->ws_bytes = 0;
+    }
+    CK(cudaMalloc(&h->ws, bytes));
+    h->ws_bytes = bytes;
+    return PINV_OK;
+}
+
+void carve(Ctx& c, bool drazin, bool host, bool check) {
+    char* p = c.h->ws;
+    auto take = [&](size_t bytes) { char* q = p; p += align_up(bytes); return (double*)q; };
+    const size_t s = c.s, big = std::max(c.m, c.n);
+    for (int i = 0; i < 3; ++i) c.X[i] = take(sizeof(double) * c.n * (size_t)c.m);
+    for (int i = 0; i < 7; ++i) c.sq[i] = take(sizeof(double) * s * s);
+    c.Al = drazin ? take(sizeof(double) * c.n * (size_t)c.n) : nullptr;
+    c.Ad = host ? take(sizeof(double) * c.n * (size_t)c.m) : nullptr;
+    c.Gd = host ? take(sizeof(double) * c.n * (size_t)c.m) : nullptr;
+    c.big[0] = check ? take(sizeof(double) * big * big) : nullptr;
+    c.big[1] = check ? take(sizeof(double) * big * big) : nullptr;
+    const size_t tiles = (size_t)((big + 63) / 64) * ((big + 63) / 64);
+    c.partials = take(sizeof(double) * 2 * tiles);
+    c.red = take(sizeof(double) * 2 * 2 * 256);
+}
+
+int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const double* B, int ldb,
+         bool tB, const Epilogue& e) {
+    ++c.gemms;
+    ++c.kernels;
+    c.gemm_flops += 2.0 * M * N * K;
+    const int slot = prof_begin(c);
+    const int r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st);
+    prof_end(c, slot);
+    return r;
+}
+
+// Read the two stop norms (sum of squares) reduced from `count` pair partials.
+int read_norms(Ctx& c, int count, double* dx2, double* x2) {
+    reduce_pairs(c.partials, count, c.h->dsmall, c.st);
+    ++c.kernels;
+    CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    prof_harvest(c);
+    *dx2 = c.h->pinned[0];
+    *x2 = c.h->pinned[1];
+    return PINV_OK;
+}
+
+// One loop of Eq. PM in FP64: Xout = Xin (I + R)(T S + mu R2 + psi R4).
+// Returns the number of pair partials written for ||Xout - Xin||, ||Xin||, or < 0.
+int pm_loop_f64(Ctx& c, const double* Xin, double* Xout) {
+    const int s = c.s, m = c.m, n = c.n;
+    double *R = c.sq[0], *R2 = c.sq[1], *R4 = c.sq[2], *L1 = c.sq[3], *L2 = c.sq[4], *T = c.sq[5],
+           *S = c.sq[6];
+    double *Z = L1, *D = L2;  // L1/L2 are dead once M is formed
+    const Coef& k = c.c;
+    // 1: R = I - X A  |  I - A X
+    if (c.left) gemm(c, s, s, m, Xin, m, false, c.A, c.lda, false, epi1(term(R, s, -1, 0, 0, 1)));
+    else        gemm(c, s, s, n, c.A, c.lda, false, Xin, m, false, epi1(term(R, s, -1, 0, 0, 1)));
+    // 2: R2
+    gemm(c, s, s, s, R, s, false, R, s, false, epi1(term(R2, s, 1)));
+    // 3: R4, L1, L2
+    {
+        Epilogue e = epi1(term(R4, s, 1), R2, s);
+        e.o[1] = term(L1, s, 1, k.c1, 0, 1);
+        e.o[2] = term(L2, s, 1, k.c2, 0, 1);
+        e.nout = 3;
+        gemm(c, s, s, s, R2, s, false, R2, s, false, e);
+    }
+    // 4: M = L1 L2 -> T, S
+    {
+        Epilogue e = epi1(term(T, s, 1, k.c3), R2, s, R4, s);
+        e.o[1] = term(S, s, 1, k.d1, k.d2);
+        e.nout = 2;
+        gemm(c, s, s, s, L1, s, false, L2, s, false, e);
+    }
+    // 5: Z = T S + mu R2 + psi R4
+    gemm(c, s, s, s, T, s, false, S, s, false, epi1(term(Z, s, 1, k.mu, k.psi), R2, s, R4, s));
+    // 6: D = R Z + Z - I
+    gemm(c, s, s, s, R, s, false, Z, s, false, epi1(term(D, s, 1, 1, 0, -1), Z, s));
+    // 7: X' = X + D X | X + X D, with stop partials
+    Epilogue e = epi1(term(Xout, m, 1, 1), Xin, m);
+    e.partials = c.partials;
+    int ctas;
+    if (c.left) ctas = gemm(c, n, m, s, D, s, false, Xin, m, false, e);
+    else        ctas = gemm(c, n, m, s, Xin, m, false, D, s, false, e);
+    return ctas;
+}
+
+// X A X with the smaller square in the middle; partials against Xprev.
+int stabilise_f64(Ctx& c, const double* Xh, const double* Xprev, double* Xout) {
+    const int s = c.s, m = c.m, n = c.n;
+    double* P = c.sq[5];
+    Epilogue e = epi1(term(Xout, m, 1), Xprev, m);
+    e.partials = c.partials;
+    if (c.left) {  // P = Xh A (n x n); X' = P Xh
+        gemm(c, s, s, m, Xh, m, false, c.A, c.lda, false, epi1(term(P, s, 1)));
+        return gemm(c, n, m, s, P, s, false, Xh, m, false, e);
+    }
+    // Q = A Xh (m x m); X' = Xh Q
+    gemm(c, s, s, n, c.A, c.lda, false, Xh, m, false, epi1(term(P, s, 1)));
+    return gemm(c, n, m, s, Xh, m, false, P, s, false, e);
+}
+
+// Projection of the finish step: (XA)^T X (AX)^T (Moore-Penrose) or
+// A^l X^{2l+1} A^l (Drazin).  Xin -> Xout.
+void cleanup_f64(Ctx& c, const pinv_desc* d, const double* X, double* Xout) {
+    const int s = c.s, m = c.m, n = c.n;
+    if (d->kind == PINV_DRAZIN) {
+        const int l = d->drazin_index;
+        double* V[2] = {c.sq[0], c.sq[1]};
+        scale_copy(n, n, X, m, 1.0, V[0], n, c.st);
+        ++c.kernels;
+        int cur = 0;
+        for (int i = 0; i < 2 * l; ++i) {
+            gemm(c, n, n, n, V[cur], n, false, X, m, false, epi1(term(V[cur ^ 1], n, 1)));
+            cur ^= 1;
+        }
+        gemm(c, n, n, n, c.Al, n, false, V[cur], n, false, epi1(term(V[cur ^ 1], n, 1)));
+        gemm(c, n, n, n, V[cur ^ 1], n, false, c.Al, n, false, epi1(term(Xout, m, 1)));
+        return;
+    }
+    double *P = c.sq[0], *W = c.sq[1], *Y = c.X[2];
+    if (c.left) {
+        // P = X A (n x n); Y = P^T X (n x m); W = Y X^T (n x n); X' = W A^T
+        gemm(c, s, s, m, X, m, false, c.A, c.lda, false, epi1(term(P, s, 1)));
+        gemm(c, n, m, n, P, s, true, X, m, false, epi1(term(Y, m, 1)));
+        gemm(c, n, n, m, Y, m, false, X, m, true, epi1(term(W, s, 1)));
+        gemm(c, n, m, n, W, s, false, c.A, c.lda, true, epi1(term(Xout, m, 1)));
+    } else {
+        // P = A X (m x m); Y = X P^T (n x m); W = X^T Y (m x m); X' = A^T W
+        gemm(c, s, s, n, c.A, c.lda, false, X, m, false, epi1(term(P, s, 1)));
+        gemm(c, n, m, m, X, m, false, P, s, true, epi1(term(Y, m, 1)));
+        gemm(c, m, m, n, X, m, true, Y, m, false, epi1(term(W, s, 1)));
+        gemm(c, n, m, m, c.A, c.lda, true, W, s, false, epi1(term(Xout, m, 1)));
+    }
+}
+
+// Relative residual norms of the Penrose (Moore-Penrose / general) or Drazin
+// equations for the final X.
+int residual_checks(Ctx& c, const pinv_desc* d, const double* X, pinv_info* info) {
+    const int m = c.m, n = c.n;
+    double* AX = c.big[0];   // m x m
+    double* XA = c.big[1];   // n x n
+    double v[2];
+    auto norms = [&](int count) -> int {
+        double a, b;
+        int rc = read_norms(c, count, &a, &b);
+        v[0] = a; v[1] = b;
+        return rc;
+    };
+    gemm(c, m, m, n, c.A, c.lda, false, X, m, false, epi1(term(AX, m, 1)));
+    gemm(c, n, n, m, X, m, false, c.A, c.lda, false, epi1(term(XA, n, 1)));
+    if (d->kind == PINV_DRAZIN) {
+        const int l = d->drazin_index;
+        // ||XAX - X|| / ||X||
+        Epilogue e = epi1(term(nullptr, 0, 1), X, m);
+        e.partials = c.partials;
+        int k = gemm(c, n, m, n, XA, n, false, X, m, false, e);
+        if (norms(k)) return PINV_ERR_CUDA;
+        info->drazin[0] = std::sqrt(v[0] / v[1]);
+        // ||AX - XA|| / ||AX||
+        diff_norms(n, n, AX, m, XA, n, false, c.h->dsmall, c.red, c.st);
+        c.kernels += 2;
+        CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+        CK(cudaStreamSynchronize(c.st));
+        info->drazin[1] = std::sqrt(c.h->pinned[0] / c.h->pinned[1]);
+        // ||A^l (AX) - A^l|| / ||A^l||
+        e = epi1(term(nullptr, 0, 1), c.Al, n);
+        e.partials = c.partials;
+        k = gemm(c, n, n, n, c.Al, n, false, AX, m, false, e);
+        if (norms(k)) return PINV_ERR_CUDA;
+        info->drazin[2] = std::sqrt(v[0] / v[1]);
+        (void)l;
+        return PINV_OK;
+    }
+    // ||AXA - A|| / ||A||
+    Epilogue e = epi1(term(nullptr, 0, 1), c.A, c.lda);
+    e.partials = c.partials;
+    int k = gemm(c, m, n, m, AX, m, false, c.A, c.lda, false, e);
+    if (norms(k)) return PINV_ERR_CUDA;
+    info->penrose[0] = std::sqrt(v[0] / v[1]);
+    // ||X AX - X|| / ||X||
+    e = epi1(term(nullptr, 0, 1), X, m);
+    e.partials = c.partials;
+    k = gemm(c, n, m, m, X, m, false, AX, m, false, e);
+    if (norms(k)) return PINV_ERR_CUDA;
+    info->penrose[1] = std::sqrt(v[0] / v[1]);
+    // ||AX - (AX)^T|| / ||AX||, ||XA - (XA)^T|| / ||XA||
+    diff_norms(m, m, AX, m, AX, m, true, c.h->dsmall, c.red, c.st);
+    c.kernels += 2;
+    CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    info->penrose[2] = std::sqrt(c.h->pinned[0] / c.h->pinned[1]);
+    diff_norms(n, n, XA, n, XA, n, true, c.h->dsmall, c.red, c.st);
+    c.kernels += 2;
+    CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    info->penrose[3] = std::sqrt(c.h->pinned[0] / c.h->pinned[1]);
+    return PINV_OK;
+}
+
+int validate(const pinv_desc* d) {
+    if (!d) return PINV_ERR_ARG;
+    if (d->m < 1 || d->n < 1) return PINV_ERR_ARG;
+    if (!d->A || !d->X) return PINV_ERR_ARG;
+    if (d->lda < d->n || d->ldx < d->m) return PINV_ERR_ARG;
+    if (d->kind == PINV_DRAZIN && (d->m != d->n || d->drazin_index < 1)) return PINV_ERR_ARG;
+    if (d->kind == PINV_OUTER_G && (!d->G || d->ldg < d->m)) return PINV_ERR_ARG;
+    if (d->kind < PINV_MOORE_PENROSE || d->kind > PINV_OUTER_G) return PINV_ERR_ARG;
+    if (!(d->alpha >= 0.0) || !std::isfinite(d->alpha)) return PINV_ERR_ARG;
+    if (!(d->tol >= 0.0)) return PINV_ERR_ARG;
+    if (d->stop != PINV_STOP_REL_FRO && d->stop != PINV_STOP_PAPER) return PINV_ERR_ARG;
+    if (d->max_iter < 0 || d->max_iter > PINV_HISTORY) return PINV_ERR_ARG;
+    if (d->prec != PINV_PREC_FP64 && d->prec != PINV_PREC_MIXED_BF16 && d->prec != PINV_PREC_FP32)
+        return PINV_ERR_ARG;
+    if (d->variant != PINV_VARIANT_PLAIN && d->variant != PINV_VARIANT_STABILIZED) return PINV_ERR_ARG;
+    if (d->finish != PINV_FINISH_NONE && d->finish != PINV_FINISH_CLEAN) return PINV_ERR_ARG;
+    return PINV_OK;
+}
+
+int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
+    c.h = h;
+    c.st = st;
+    c.m = d->m;
+    c.n = d->n;
+    c.left = d->m > d->n;  // residual on the smaller side; the paper's right form when m <= n
+    c.s = c.left ? d->n : d->m;
+    c.c = pm_coefficients();
+    const bool drazin = d->kind == PINV_DRAZIN;
+    const bool host = d->host_buffers != 0;
+    const bool check = d->check != 0;
+    size_t bytes = workspace_bytes(d->m, d->n, drazin, host, check);
+    if (d->prec != PINV_PREC_FP64) bytes += mixed_workspace_bytes(d->m, d->n);
+    int rc = ensure_workspace(h, bytes);
+    if (rc) return rc;
+    carve(c, drazin, host, check);
+    if (host) {
+        CK(cudaMemcpy2DAsync(c.Ad, sizeof(double) * d->n, d->A, sizeof(double) * d->lda,
+                             sizeof(double) * d->n, d->m, cudaMemcpyHostToDevice, st));
+        c.A = c.Ad;
+        c.lda = d->n;
+        if (d->kind == PINV_OUTER_G) {
+            CK(cudaMemcpy2DAsync(c.Gd, sizeof(double) * d->m, d->G, sizeof(double) * d->ldg,
+                                 sizeof(double) * d->m, d->n, cudaMemcpyHostToDevice, st));
+        }
+    } else {
+        c.A = d->A;
+        c.lda = d->lda;
+    }
+    return PINV_OK;
+}
+
+// X0 = alpha G (Section 4) into c.X[0]; returns alpha used via *alpha.
+int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
+    const int m = c.m, n = c.n;
+    double a = d->alpha;
+    if (d->kind == PINV_DRAZIN) {
+        const int l = d->drazin_index;
+        // A^l by l - 1 products
+        scale_copy(n, n, c.A, c.lda, 1.0, c.Al, n, c.st);
+        ++c.kernels;
+        for (int i = 1; i < l; ++i) {
+            gemm(c, n, n, n, c.Al, n, false, c.A, c.lda, false, epi1(term(c.sq[0], n, 1)));
+            scale_copy(n, n, c.sq[0], n, 1.0, c.Al, n, c.st);
+            ++c.kernels;
+        }
+        if (a == 0.0) {  // alpha = 1 / Tr(A^{l+1}) = 1 / sum_ij (A^l)_ij A_ji
+            trace_of_product(n, c.Al, n, c.A, c.lda, c.h->dsmall, c.red, c.st);
+            c.kernels += 2;
+            CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, sizeof(double), cudaMemcpyDeviceToHost, c.st));
+            CK(cudaStreamSynchronize(c.st));
+            const double tr = c.h->pinned[0];
+            if (!(tr > 0.0) || !std::isfinite(tr)) return PINV_ERR_ARG;
+            a = 1.0 / tr;
+        }
+        scale_copy(n, n, c.Al, n, a, c.X[0], m, c.st);
+        ++c.kernels;
+    } else {
+        if (a == 0.0) {  // 1 / (||A||_1 ||A||_inf)
+            norms_1_inf(m, n, c.A, c.lda, c.h->dsmall, c.red, c.st);
+            c.kernels += 4;
+            CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+            CK(cudaStreamSynchronize(c.st));
+            const double p = c.h->pinned[0] * c.h->pinned[1];
+            if (!(p > 0.0) || !std::isfinite(p)) return PINV_ERR_NONFINITE;
+            a = 1.0 / p;
+        }
+        if (d->kind == PINV_MOORE_PENROSE) {
+            transpose_scale(m, n, c.A, c.lda, a, c.X[0], m, c.st);
+            ++c.kernels;
+        } else {
+            const double* G = d->host_buffers ? c.Gd : d->G;
+            const int ldg = d->host_buffers ? m : d->ldg;
+            scale_copy(n, m, G, ldg, a, c.X[0], m, c.st);
+            ++c.kernels;
+        }
+    }
+    *alpha = a;
+    return PINV_OK;
+}
+
+double stop_measure(const pinv_desc* d, double dx2, double x2, int k, double alpha) {
+    const double dx = std::sqrt(dx2);
+    if (d->stop == PINV_STOP_PAPER) return dx / (std::pow(18.0, k) * alpha);
+    return x2 > 0 ? dx / std::sqrt(x2) : INFINITY;
+}
+
+int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* info) {
+    auto t0 = std::chrono::steady_clock::now();
+    std::memset(info, 0, sizeof(*info));
+    int rc = validate(d);
+    if (rc) return info->status = rc;
+    Ctx c{};
+    c.profile = d->profile != 0;
+    rc = setup_context(h, d, st, c);
+    if (rc) return info->status = rc;
+    info->side = c.left ? 1 : 0;
+    double alpha = 0.0;
+    rc = initial_value(c, d, &alpha);
+    if (rc) return info->status = rc;
+    info->alpha = alpha;
+
+    const int max_iter = d->max_iter ? d->max_iter : 100;
+    const double switch_tol = d->switch_tol > 0 ? d->switch_tol : 1e-3;
+    const double floor_guard = 1e-3;
+    int cur = 0;              // X[cur] = X_k
+    double prev = INFINITY;
+    bool stabilise = false;
+    int status = PINV_ERR_MAXITER, reason = 2;
+    MixedSchedule sched;
+    const bool mixed = d->prec != PINV_PREC_FP64;
+    if (mixed) {
+        if (!h->mixed) h->mixed = mixed_create();
+        rc = mixed_begin(h->mixed, c.m, c.n, c.left, c.A, c.lda, d->prec, c.st, &sched);
+        if (rc) return info->status = rc;
+    }
+    for (int k = 0; k < max_iter; ++k) {
+        const bool stab_now = stabilise;
+        const double* Xk = c.X[cur];
+        double* Xn = c.X[cur ^ 1];
+        int parts;
+        int prec_k = 0;
+        if (mixed) {
+            prec_k = mixed_loop_precision(&sched, k, prev);
+        }
+        double* target = stab_now ? c.X[2] : Xn;
+        if (prec_k == 0) {
+            parts = pm_loop_f64(c, Xk, target);
+        } else {
+            parts = mixed_pm_loop(h->mixed, &sched, prec_k, Xk, target, c.partials, c.st);
+            c.gemms += 7;
+            c.kernels += mixed_last_kernels(h->mixed);
+        }
+        if (stab_now) {
+            parts = stabilise_f64(c, c.X[2], Xk, Xn);
+            ++info->stabilized_loops;
+        }
+        if (parts < 0) return info->status = PINV_ERR_CUDA;
+        double dx2, x2;
+        rc = read_norms(c, parts, &dx2, &x2);
+        if (rc) return info->status = rc;
+        const double e = stop_measure(d, dx2, x2, k, alpha);
+        info->loops_run = k + 1;
+        if (k < PINV_HISTORY) {
+            info->history[k] = e;
+            info->precision[k] = (signed char)prec_k;
+        }
+        if (!std::isfinite(e)) { status = PINV_ERR_NONFINITE; info->iters = k; break; }
+        if (e < d->tol) { status = PINV_OK; reason = 0; cur ^= 1; info->iters = k + 1; info->rel_step = e; break; }
+        const bool stalled = stab_now ? (e >= prev) : (prev < floor_guard && e >= prev * prev);
+        if (stalled && prec_k != 1) { status = PINV_OK; reason = 1; info->iters = k; info->rel_step = prev; break; }
+        // divergence guard on the relative step: a convergent loop grows X by at
+        // most a factor 18 (|p(r)| <= 18 for |r| <= 1)
+        const double rel = x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY;
+        if (rel > 1e3 && k > 0) { status = PINV_ERR_DIVERGED; info->iters = k; break; }
+        if (d->variant == PINV_VARIANT_STABILIZED && e < switch_tol && prec_k != 1) stabilise = true;
+        prev = e;
+        info->rel_step = e;
+        cur ^= 1;
+        info->iters = k + 1;
+    }
+    info->stop_reason = reason;
+    if (status == PINV_OK && d->finish == PINV_FINISH_CLEAN) {
+        // projection, then one FP64 loop (Theorems 6.2 / 7.1: the blocks the
+        // loop does not contract are removed, the range block is re-contracted)
+        cleanup_f64(c, d, c.X[cur], c.X[cur ^ 1]);
+        int parts = pm_loop_f64(c, c.X[cur ^ 1], c.X[cur]);
+        if (parts < 0) return info->status = PINV_ERR_CUDA;
+    }
+    const double* Xfinal = c.X[cur];
+    if (status == PINV_OK && d->check) {
+        rc = residual_checks(c, d, Xfinal, info);
+        if (rc) return info->status = rc;
+    }
+    if (d->host_buffers) {
+        CK(cudaMemcpy2DAsync(d->X, sizeof(double) * d->ldx, Xfinal, sizeof(double) * c.m,
+                             sizeof(double) * c.m, c.n, cudaMemcpyDeviceToHost, st));
+    } else {
+        CK(cudaMemcpy2DAsync(d->X, sizeof(double) * d->ldx, Xfinal, sizeof(double) * c.m,
+                             sizeof(double) * c.m, c.n, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    prof_harvest(c);
+    info->gemms = c.gemms;
+    info->kernels = c.kernels;
+    info->gemm_ms = c.gemm_ms;
+    info->gemm_flops = c.gemm_flops;
+    info->ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return info->status = status;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pinv_init(pinv_handle** out, const pinv_config* cfg) {
+    if (!out) return PINV_ERR_ARG;
+    *out = nullptr;
+    pinv_handle* h = new pinv_handle();
+    h->device = cfg ? cfg->device : 0;
+    h->budget = cfg ? cfg->hbm_budget_bytes : 0;
+    cudaError_t e = cudaSetDevice(h->device);
+    if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->dsmall, 64 * sizeof(double));
+    if (e != cudaSuccess) {
+        std::fprintf(stderr, "pinv_init: %s\n", cudaGetErrorString(e));
+        if (h->pinned) cudaFreeHost(h->pinned);
+        delete h;
+        return PINV_ERR_CUDA;
+    }
+    *out = h;
+    return PINV_OK;
+}
+
+void pinv_destroy(pinv_handle* h) {
+    if (!h) return;
+    cudaSetDevice(h->device);
+    cudaDeviceSynchronize();
+    if (h->mixed) mixed_destroy(h->mixed);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    if (h->ws) cudaFree(h->ws);
+    if (h->dsmall) cudaFree(h->dsmall);
+    if (h->pinned) cudaFreeHost(h->pinned);
+    delete h;
+}
+
+int pinv_solve(pinv_handle* h, const pinv_desc* desc, void* stream, pinv_info* info) {
+    if (!h) return PINV_ERR_ARG;
+    pinv_info local;
+    pinv_info* out = info ? info : &local;
+    if (cudaSetDevice(h->device) != cudaSuccess) return out->status = PINV_ERR_CUDA;
+    return solve_one(h, desc, (cudaStream_t)stream, out);
+}
+
+int pinv_solve_batched(pinv_handle* h, int count, const pinv_desc* descs, void* stream,
+                       pinv_info* infos) {
+    if (!h || count < 0 || (count && !descs)) return PINV_ERR_ARG;
+    int worst = PINV_OK;
+    for (int i = 0; i < count; ++i) {
+        pinv_info local;
+        int rc = pinv_solve(h, &descs[i], stream, infos ? &infos[i] : &local);
+        if (rc != PINV_OK && worst == PINV_OK) worst = rc;
+    }
+    return worst;
+}
+
+int pinv_submit(pinv_handle* h, const pinv_desc* desc, uint64_t* id) {
+    if (!h || !desc || !id) return PINV_ERR_ARG;
+    int rc = validate(desc);
+    if (rc) return rc;
+    const size_t need = workspace_bytes(desc->m, desc->n, desc->kind == PINV_DRAZIN,
+                                        desc->host_buffers != 0, desc->check != 0);
+    if (h->budget && need > h->budget) return PINV_ERR_BUDGET;
+    std::lock_guard<std::mutex> lk(h->mu);
+    *id = h->next_id++;
+    pinv_handle::Request r;
+    r.desc = *desc;
+    h->requests[*id] = r;
+    h->queue.push_back(*id);
+    return PINV_OK;
+}
+
+int pinv_poll(pinv_handle* h, uint64_t id, pinv_info* info) {
+    if (!h) return PINV_ERR_ARG;
+    std::lock_guard<std::mutex> lk(h->mu);
+    auto it = h->requests.find(id);
+    if (it == h->requests.end()) return PINV_ERR_UNKNOWN_ID;
+    // drive one request per poll (FIFO)
+    if (!h->queue.empty()) {
+        uint64_t next = h->queue.front();
+        h->queue.pop_front();
+        auto& r = h->requests[next];
+        cudaSetDevice(h->device);
+        r.status = solve_one(h, &r.desc, nullptr, &r.info);
+    }
+    if (it->second.status == PINV_PENDING) return PINV_PENDING;
+    int st = it->second.status;
+    if (info) *info = it->second.info;
+    h->requests.erase(it);
+    return st;
+}
+
+int pinv_alpha_estimate(pinv_handle* h, const pinv_desc* d, void* stream, double* alpha) {
+    if (!h || !d || !alpha || !d->A || d->m < 1 || d->n < 1 || d->lda < d->n) return PINV_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = ensure_workspace(h, std::max(h->ws_bytes, (size_t)(2 * 2 * 256 * sizeof(double))));
+    if (rc) return rc;
+    double* scratch = (double*)h->ws;
+    norms_1_inf(d->m, d->n, d->A, d->lda, h->dsmall, scratch, st);
+    CK(cudaMemcpyAsync(h->pinned, h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    const double p = h->pinned[0] * h->pinned[1];
+    if (!(p > 0.0) || !std::isfinite(p)) return PINV_ERR_NONFINITE;
+    *alpha = 1.0 / p;
+    return PINV_OK;
+}
+
+int pinv_step(pinv_handle* h, int m, int n, const double* A, int lda, const double* X_in,
+              double* X_out, int ldx, pinv_prec prec, int stabilized, void* stream,
+              double* rel_step) {
+    if (!h || m < 1 || n < 1 || !A || !X_in || !X_out || lda < n || ldx != m || X_in == X_out)
+        return PINV_ERR_ARG;
+    if (prec != PINV_PREC_FP64 && prec != PINV_PREC_MIXED_BF16 && prec != PINV_PREC_FP32)
+        return PINV_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
+    pinv_desc d{};
+    d.m = m; d.n = n; d.A = A; d.lda = lda; d.X = X_out; d.ldx = ldx;
+    d.kind = PINV_MOORE_PENROSE; d.prec = prec;
+    Ctx c{};
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = setup_context(h, &d, st, c);
+    if (rc) return rc;
+    int parts;
+    if (prec == PINV_PREC_FP64) {
+        parts = pm_loop_f64(c, X_in, stabilized ? c.X[2] : X_out);
+    } else {
+        MixedSchedule sched;
+        if (!h->mixed) h->mixed = mixed_create();
+        rc = mixed_begin(h->mixed, m, n, c.left, A, lda, prec, st, &sched);
+        if (rc) return rc;
+        const int pk = prec == PINV_PREC_MIXED_BF16 ? 1 : 3;
+        parts = mixed_pm_loop(h->mixed, &sched, pk, X_in, stabilized ? c.X[2] : X_out, c.partials, st);
+    }
+    if (stabilized) parts = stabilise_f64(c, c.X[2], X_in, X_out);
+    if (parts < 0) return PINV_ERR_CUDA;
+    double dx2, x2;
+    rc = read_norms(c, parts, &dx2, &x2);
+    if (rc) return rc;
+    if (rel_step) *rel_step = x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY;
+    CK(cudaGetLastError());
+    return PINV_OK;
+}
+
+}  // extern "C"

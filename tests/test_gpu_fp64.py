@@ -1,0 +1,279 @@
+"""GPU parity of the FP64 path against the oracle (through the C ABI).
+
+Tolerances (FP64 products on both sides):
+* one loop: the factorised seven-product step against the naive 17-product
+  oracle step -- both exact up to rounding, relative Frobenius difference and
+  per-element difference <= 1e-12 of the largest entry;
+* whole solves: relative Frobenius difference <= 1e-9 (the FP64-finished bar
+  at kappa <= 1e4) and <= 1e-12 where the oracle itself reaches 1e-14.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import hyperpower as H
+from paper_1604_07893_gb300 import workloads as W
+from tests.helpers import drazin_closed_form, example1, pinv_closed_form, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_07893_gb300 import Handle
+    h = Handle(0)
+    yield h
+    h.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy()
+
+
+def assert_close(got, ref, tol):
+    scale = np.abs(ref).max()
+    assert np.abs(got - ref).max() <= tol * scale, np.abs(got - ref).max() / scale
+    assert rel(got, ref) <= tol
+
+
+# -------------------------------------------------------------------------- one loop
+
+@pytest.mark.parametrize("m,n", [(64, 48), (48, 64), (1, 1), (200, 136), (136, 200), (130, 130),
+                                 (17, 129), (257, 65)])
+def test_one_pm_loop_matches_naive_order18_step(handle, m, n):
+    w = W.rectangular(m, n, None, 1.0, 1e-2, seed=m * 7 + n)
+    A = w.A
+    X = H.x0_moore_penrose(A, H.alpha_pan_schreiber(w.s[0], w.s[-1]))
+    for _ in range(2):
+        ref = H.hyperpower_step(A, X, side=H.choose_side(m, n))
+        got, step = handle.step(dev(A), dev(X))
+        assert_close(host(got), ref, 1e-12)
+        assert step == pytest.approx(float(np.linalg.norm(ref - X) / np.linalg.norm(X)), rel=1e-10)
+        X = ref
+
+
+@pytest.mark.parametrize("m,n", [(96, 72), (72, 96)])
+def test_one_stabilised_loop_matches_oracle(handle, m, n):
+    w = W.rectangular(m, n, 54, 1.0, 1e-1, seed=3)
+    X = H.x0_moore_penrose(w.A, 1.0)
+    for _ in range(3):
+        X = H.hyperpower_step(w.A, X)
+    ref = H.stabilised_step(w.A, X, side=H.choose_side(m, n))
+    got, _ = handle.step(dev(w.A), dev(X), stabilized=True)
+    assert_close(host(got), ref, 1e-12)
+
+
+# -------------------------------------------------------------------------- solves
+
+def test_solve_64x48_matches_oracle_and_closed_form(handle):
+    """The small Moore-Penrose case: 64 x 48, s log-spaced in [1e-2, 1]."""
+    w = W.rectangular(64, 48, None, 1.0, 1e-2, seed=0)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    ref, oinfo = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, check=True)
+    assert info["status"] == 0 and info["iters"] == oinfo.iters
+    assert_close(host(X), ref, 1e-12)
+    assert rel(host(X), pinv_closed_form(w)) < 1e-12
+    assert max(info["penrose"]) < 1e-12
+
+
+def test_solve_literal_boundary_alpha_fails_like_the_oracle(handle):
+    """alpha = 2/s_max^2 (the edge of Theorem 3.1's condition) reaches another
+    outer inverse on both sides."""
+    w = W.rectangular(64, 48, None, 1.0, 1e-2, seed=0)
+    X, info = handle.solve(dev(w.A), alpha=2.0, tol=1e-12)
+    assert rel(host(X), pinv_closed_form(w)) > 1e-6
+
+
+@pytest.mark.parametrize("variant", ["plain", "stabilized"])
+def test_solve_rank_deficient_kappa_1e4(handle, variant):
+    """Reduced form of the 4096 x 3072 rank-2304 workload (rank 3n/4,
+    s log-spaced in [1e-4, 1]), with the cleanup-and-one-loop finish."""
+    w = W.rectangular(512, 384, 288, 1.0, 1e-4, seed=1)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha,
+                     variant="stabilised" if variant == "stabilized" else "plain",
+                     finish="moore_penrose")
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, variant=variant, finish="clean",
+                           check=True)
+    assert info["status"] == 0
+    assert rel(host(X), ref) <= 1e-9
+    assert rel(host(X), pinv_closed_form(w)) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9
+
+
+def test_solve_wide_matrix_right_side(handle):
+    w = W.rectangular(70, 150, 60, 1.0, 1e-2, seed=9)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-13, alpha=alpha, finish="moore_penrose")
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-13, finish="clean")
+    assert info["side"] == "right"
+    assert rel(host(X), ref) < 1e-11
+
+
+def test_solve_drazin_family(handle):
+    d = W.drazin_index2(256, 64, seed=2)
+    ref, _ = H.solve(d.A, H.x0_drazin(d.A, 2), tol=1e-13, alpha=1.0)
+    X, info = handle.solve(dev(d.A), kind="drazin", drazin_index=2, tol=1e-13, check=True)
+    assert info["status"] == 0
+    assert rel(host(X), ref) < 1e-10
+    assert rel(host(X), drazin_closed_form(d)) < 1e-10
+    assert max(info["drazin"]) < 1e-10
+    tr = np.trace(np.linalg.matrix_power(d.A, 3))
+    assert info["alpha"] == pytest.approx(1.0 / tr, rel=1e-12)
+
+
+def test_solve_example1_drazin(handle):
+    """Section 8, Example 1 in FP64: the printed index-3 matrix."""
+    A = example1()
+    ref, _ = H.solve(A, H.x0_drazin(A, 3), tol=1e-14, alpha=1.0)
+    X, info = handle.solve(dev(A), kind="drazin", drazin_index=3, tol=1e-14)
+    assert rel(host(X), ref) < 1e-10
+    assert abs(host(X)[0, 0] - 0.25) < 1e-10 and abs(host(X)[0, 1] + 0.25) < 1e-10
+
+
+def test_solve_outer_inverse_with_G(handle):
+    w = W.rectangular(30, 20, 20, 1.0, 1e-1, seed=5)
+    rng = np.random.default_rng(9)
+    Vs = np.linalg.qr(rng.standard_normal((20, 6)))[0]
+    G = np.ascontiguousarray(Vs @ Vs.T @ w.A.T)
+    lam = np.linalg.eigvalsh(Vs.T @ w.A.T @ w.A @ Vs)
+    alpha = 2.0 / (lam.max() + lam.min())
+    ref, _ = H.solve(w.A, H.x0_general(G, alpha), tol=1e-13, alpha=alpha)
+    X, info = handle.solve(dev(w.A), kind="outer_g", G=dev(G), alpha=alpha, tol=1e-13)
+    assert rel(host(X), ref) < 1e-11
+
+
+def test_solve_spd_nonsingular(handle):
+    s = W.spd(300, 1e-3, 1.0, seed=5)
+    alpha = 2.0 / (s.lam.max() + s.lam.min())
+    ref, _ = H.solve(s.A, H.x0_general(np.eye(300), alpha), tol=1e-13, alpha=alpha)
+    X, info = handle.solve(dev(s.A), kind="outer_g", G=dev(np.eye(300)), alpha=alpha, tol=1e-13)
+    assert rel(host(X), ref) < 1e-11
+
+
+def test_paper_stop_rule(handle):
+    """Eq. stopreliable with the Frobenius norm (Section 8, Example 2) on a
+    Hilbert matrix H_{100x90}, X0 = 2/(s1^2 + sr^2) H^T."""
+    A = W.hilbert(100, 90)
+    s = np.linalg.svd(A, compute_uv=False)
+    s_r = s[s > 1e-15 * s[0]][-1]          # numerically nonzero: sigma_r of Section 4
+    alpha = 2.0 / (s[0] ** 2 + s_r ** 2)
+    ref, oinfo = H.solve(A, H.x0_moore_penrose(A, alpha), tol=1e-5, stop=H.STOP_PAPER, alpha=alpha)
+    X, info = handle.solve(dev(A), alpha=alpha, tol=1e-5, stop="paper")
+    assert info["iters"] == oinfo.iters
+    assert rel(host(X), ref) < 1e-6
+
+
+def test_alpha_estimate(handle):
+    w = W.rectangular(123, 77, None, 2.0, 1e-2, seed=4)
+    assert handle.alpha_estimate(dev(w.A)) == pytest.approx(H.alpha_rectangular(w.A), rel=1e-12)
+    X, info = handle.solve(dev(w.A), alpha=0.0, tol=1e-12)
+    assert info["alpha"] == pytest.approx(H.alpha_rectangular(w.A), rel=1e-12)
+
+
+def test_host_buffers_equal_device_buffers(handle):
+    w = W.rectangular(100, 60, None, 1.0, 1e-2, seed=6)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    Xd, _ = handle.solve(dev(w.A), alpha=alpha, tol=1e-12)
+    Xh, info = handle.solve(np.ascontiguousarray(w.A), alpha=alpha, tol=1e-12, host=True)
+    assert info["status"] == 0
+    assert np.array_equal(Xh, host(Xd))
+
+
+def test_deterministic(handle):
+    w = W.rectangular(200, 150, 120, 1.0, 1e-3, seed=8)
+    a = handle.solve(dev(w.A), alpha=1.0, tol=1e-12)[0]
+    b = handle.solve(dev(w.A), alpha=1.0, tol=1e-12)[0]
+    assert torch.equal(a, b)
+
+
+def test_batched_equals_single(handle):
+    ws = W.uneven_batch(6, seed=3, m_hi=200)
+    As = [dev(w.A) for w in ws]
+    Xs, infos = handle.solve_batched(As, alpha=0.0, tol=1e-12)
+    for A, X, info in zip(As, Xs, infos):
+        X1, _ = handle.solve(A, alpha=0.0, tol=1e-12)
+        assert torch.equal(X, X1)
+
+
+def test_submit_poll_equals_solve(handle):
+    ws = [W.rectangular(80 + 10 * i, 50, None, 1.0, 1e-2, seed=i) for i in range(3)]
+    As = [dev(w.A) for w in ws]
+    Xs = [torch.empty(50, A.shape[0], dtype=torch.float64, device="cuda") for A in As]
+    ids = [handle.submit(A, X, alpha=0.0, tol=1e-12) for A, X in zip(As, Xs)]
+    done = {}
+    for _ in range(100):
+        for i in ids:
+            if i not in done:
+                r = handle.poll(i)
+                if r is not None:
+                    done[i] = r
+        if len(done) == len(ids):
+            break
+    assert len(done) == len(ids)
+    for A, X, i in zip(As, Xs, ids):
+        assert done[i][0] == 0
+        X1, _ = handle.solve(A, alpha=0.0, tol=1e-12)
+        assert torch.equal(X, X1)
+
+
+# -------------------------------------------------------------------------- errors
+
+def test_argument_errors(handle):
+    from paper_1604_07893_gb300 import PinvError
+    A = dev(np.ones((4, 3)))
+    with pytest.raises(PinvError) as e:
+        handle.solve(A, kind="drazin", drazin_index=1)      # Drazin needs a square A
+    assert e.value.code == -1
+    with pytest.raises(PinvError) as e:
+        handle.solve(A, alpha=-1.0)
+    assert e.value.code == -1
+    with pytest.raises(PinvError) as e:
+        handle.solve(dev(np.eye(3)), kind="drazin", drazin_index=0)
+    assert e.value.code == -1
+
+
+def test_nonfinite_input_reported(handle):
+    A = np.ones((6, 4))
+    A[2, 1] = np.nan
+    X, info = handle.solve(dev(A), alpha=0.1, raise_on_error=False)
+    assert info["status"] == -3
+
+
+def test_budget_error():
+    from paper_1604_07893_gb300 import Handle, PinvError
+    h = Handle(0, hbm_budget_bytes=1 << 20)
+    A = dev(np.ones((512, 512)))
+    with pytest.raises(PinvError) as e:
+        h.solve(A, alpha=1e-3)
+    assert e.value.code == -2
+    h.close()
+
+
+# -------------------------------------------------------------------------- full size
+
+@pytest.mark.slow
+def test_full_size_rank_deficient_sampled_rows(handle):
+    """The 4096 x 3072 rank-2304 workload in FP64, as timed by the benchmark:
+    sampled rows of X against the closed form V diag(1/s) U^T, and the
+    Penrose residuals computed on the device."""
+    w = W.rectangular(4096, 3072, 2304, 1.0, 1e-4, seed=1)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, variant="stabilized", finish="clean",
+                           check=True)
+    assert info["status"] == 0
+    Xh = host(X)
+    rows = np.random.default_rng(0).choice(3072, 24, replace=False)
+    ref_rows = (w.V[rows] / w.s) @ w.U.T
+    assert rel(Xh[rows], ref_rows) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9
