@@ -155,6 +155,7 @@ void prof_harvest(Ctx& c) {  // stream already synchronised
 }
 
 size_t workspace_bytes(int m, int n, bool drazin, bool host, bool check) {
+    // `check` also covers the finish step: both need the two max(m,n)^2 squares
     const size_t s = std::min(m, n), big = std::max(m, n);
     size_t b = 0;
     b += 3 * align_up(sizeof(double) * n * (size_t)m);
@@ -295,20 +296,14 @@ void cleanup_f64(Ctx& c, const pinv_desc* d, const double* X, double* Xout) {
         gemm(c, n, n, n, V[cur ^ 1], n, false, c.Al, n, false, epi1(term(Xout, m, 1)));
         return;
     }
-    double *P = c.sq[0], *W = c.sq[1], *Y = c.X[2];
-    if (c.left) {
-        // P = X A (n x n); Y = P^T X (n x m); W = Y X^T (n x n); X' = W A^T
-        gemm(c, s, s, m, X, m, false, c.A, c.lda, false, epi1(term(P, s, 1)));
-        gemm(c, n, m, n, P, s, true, X, m, false, epi1(term(Y, m, 1)));
-        gemm(c, n, n, m, Y, m, false, X, m, true, epi1(term(W, s, 1)));
-        gemm(c, n, m, n, W, s, false, c.A, c.lda, true, epi1(term(Xout, m, 1)));
-    } else {
-        // P = A X (m x m); Y = X P^T (n x m); W = X^T Y (m x m); X' = A^T W
-        gemm(c, s, s, n, c.A, c.lda, false, X, m, false, epi1(term(P, s, 1)));
-        gemm(c, n, m, m, X, m, false, P, s, true, epi1(term(Y, m, 1)));
-        gemm(c, m, m, n, X, m, true, Y, m, false, epi1(term(W, s, 1)));
-        gemm(c, n, m, m, c.A, c.lda, true, W, s, false, epi1(term(Xout, m, 1)));
-    }
+    // X' = P^T X Q^T with P = XA (n x n) and Q = AX (m x m): both factors are
+    // near-projectors (entries O(1)), so no intermediate grows like ||X||^2.
+    double *P = c.big[0], *Q = c.big[1], *Y = c.X[2];
+    gemm(c, n, n, m, X, m, false, c.A, c.lda, false, epi1(term(P, n, 1)));
+    gemm(c, m, m, n, c.A, c.lda, false, X, m, false, epi1(term(Q, m, 1)));
+    gemm(c, n, m, n, P, n, true, X, m, false, epi1(term(Y, m, 1)));
+    gemm(c, n, m, m, Y, m, false, Q, m, true, epi1(term(Xout, m, 1)));
+    (void)s;
 }
 
 // Relative residual norms of the Penrose (Moore-Penrose / general) or Drazin
@@ -404,7 +399,7 @@ int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
     c.c = pm_coefficients();
     const bool drazin = d->kind == PINV_DRAZIN;
     const bool host = d->host_buffers != 0;
-    const bool check = d->check != 0;
+    const bool check = d->check != 0 || d->finish == PINV_FINISH_CLEAN;
     size_t bytes = workspace_bytes(d->m, d->n, drazin, host, check);
     if (d->prec != PINV_PREC_FP64) bytes += mixed_workspace_bytes(d->m, d->n);
     int rc = ensure_workspace(h, bytes);
@@ -646,7 +641,8 @@ int pinv_submit(pinv_handle* h, const pinv_desc* desc, uint64_t* id) {
     int rc = validate(desc);
     if (rc) return rc;
     const size_t need = workspace_bytes(desc->m, desc->n, desc->kind == PINV_DRAZIN,
-                                        desc->host_buffers != 0, desc->check != 0);
+                                        desc->host_buffers != 0,
+                                        desc->check != 0 || desc->finish == PINV_FINISH_CLEAN);
     if (h->budget && need > h->budget) return PINV_ERR_BUDGET;
     std::lock_guard<std::mutex> lk(h->mu);
     *id = h->next_id++;
