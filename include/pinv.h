@@ -194,6 +194,27 @@ int  pinv_step(pinv_handle *h, int m, int n, const double *A, int lda,
                const double *X_in, double *X_out, int ldx,
                pinv_prec prec, int stabilized, void *stream, double *rel_step);
 
+/* For callers that cannot allocate device memory (a plugin whose host
+ * framework owns the allocator, code under a pool that forbids cudaMalloc,
+ * code that must not trigger the implicit synchronisation of cudaMalloc or
+ * cudaFree): the same FP64 loop as pinv_step, with every intermediate taken
+ * from one fixed-size static device array inside the library, so the call
+ * allocates nothing (no cudaMalloc/cudaFree/cudaMallocHost, no allocating
+ * library routine).  The paper has no counterpart; this is a deployment aid.
+ *   - No handle: runs on the current device; the caller passes A, X_in, X_out
+ *     (device, n x m with ldx == m, X_in != X_out) and receives *rel_step.
+ *   - m and n must be <= PINV_NOALLOC_MAX_DIM, else PINV_ERR_BUDGET with no
+ *     device work.  The static array (about 1 MiB) lives on every GPU that
+ *     loads the library until the process exits.
+ *   - The first call on each device looks up the array's device address
+ *     (cudaGetSymbolAddress); make that first call before any stream capture.
+ *   - All calls on a device share the array and it keeps the last call's
+ *     contents: calls that overlap on the GPU race, so serialise them. */
+#define PINV_NOALLOC_MAX_DIM 128
+int  pinv_step_noalloc(int m, int n, const double *A, int lda, const double *X_in,
+                       double *X_out, int ldx, int stabilized, void *stream,
+                       double *rel_step);
+
 #ifdef __cplusplus
 }
 #endif

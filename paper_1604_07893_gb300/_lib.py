@@ -25,7 +25,8 @@ FINISH = {None: 0, "none": 0, "clean": 1}
 HISTORY = 128
 
 EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_batched", "pinv_submit",
-           "pinv_poll", "pinv_alpha_estimate", "pinv_step")
+           "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_step_noalloc")
+NOALLOC_MAX_DIM = 128
 
 
 class Config(C.Structure):
@@ -86,6 +87,8 @@ def load() -> C.CDLL:
     lib.pinv_alpha_estimate.argtypes = [C.c_void_p, P(Desc), C.c_void_p, P(C.c_double)]
     lib.pinv_step.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                               C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
+    lib.pinv_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
+                                      C.c_void_p, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
     for name in EXPORTS:
         if name != "pinv_destroy":
             getattr(lib, name).restype = C.c_int
@@ -236,3 +239,20 @@ class Handle:
         if rc != PINV_OK:
             raise PinvError(rc, "pinv_step")
         return X_out, rel.value
+
+
+def step_noalloc(A, X_in, X_out=None, *, stabilized=False, stream=None):
+    """pinv_step_noalloc: one FP64 loop using the library's static scratch
+    (no allocation inside the call; m, n <= 128).  Returns (X_out, rel_step)."""
+    import torch
+    lib = load()
+    if X_out is None:
+        X_out = torch.empty_like(X_in)
+    m, n = A.shape
+    rel = C.c_double()
+    rc = lib.pinv_step_noalloc(m, n, C.c_void_p(_dev_ptr(A)), A.stride(0), C.c_void_p(_dev_ptr(X_in)),
+                               C.c_void_p(_dev_ptr(X_out)), X_in.stride(0), 1 if stabilized else 0,
+                               C.c_void_p(_stream_ptr(stream)), C.byref(rel))
+    if rc != PINV_OK:
+        raise PinvError(rc, "pinv_step_noalloc")
+    return X_out, rel.value
