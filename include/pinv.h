@@ -68,10 +68,18 @@ typedef enum {
 } pinv_stop;
 
 typedef enum {
-    PINV_PREC_FP64       = 0, /* every product in FP64                             */
-    PINV_PREC_MIXED_BF16 = 1, /* early loops BF16 tensor cores, FP32-class finish, FP64 final */
+    PINV_PREC_FP64       = 0, /* every product in native FP64 (DMMA)               */
+    PINV_PREC_MIXED_BF16 = 1, /* loops in BF16 while the step is > 0.5 (growth phase),
+                                 FP32-class until it is < 1e-4 or stops falling, then
+                                 FP64-class (tensor cores).  For problems without a
+                                 null block (full column rank, nonsingular); needs
+                                 alpha <= 1/sigma_max^2 (e.g. the alpha = 0 recipe) */
     PINV_PREC_MIXED_FP8  = 2, /* reserved: FP8 early loops (returns PINV_ERR_ARG)  */
-    PINV_PREC_FP32       = 3  /* FP32-class (split TF32 tensor-core) loops, FP64 final */
+    PINV_PREC_FP32       = 3, /* FP32-class loops (4 exact BF16 slices, 10 slice
+                                 products) until the step is < 1e-4 or stops falling,
+                                 then FP64-class                                   */
+    PINV_PREC_FP64_TC    = 4  /* every product FP64-accurate on the BF16 tensor
+                                 cores: 9 exact slices per operand, 45 products    */
 } pinv_prec;
 
 typedef enum {
@@ -138,6 +146,7 @@ typedef struct {
     int    kernels;          /* all kernel launches issued (GEMMs included)          */
     float  gemm_ms;          /* desc->profile: summed CUDA-event time of the GEMMs   */
     double gemm_flops;       /* algorithmic flops of those GEMMs (2 M N K each)       */
+    double tensor_flops;     /* BF16 tensor-core flops issued: 2 M N K per slice product */
     double history[PINV_HISTORY];  /* stop measure per loop                          */
     signed char precision[PINV_HISTORY]; /* per loop: 0 FP64, 1 BF16, 3 FP32-class  */
 } pinv_info;
@@ -193,6 +202,15 @@ int  pinv_alpha_estimate(pinv_handle *h, const pinv_desc *desc, void *stream, do
 int  pinv_step(pinv_handle *h, int m, int n, const double *A, int lda,
                const double *X_in, double *X_out, int ldx,
                pinv_prec prec, int stabilized, void *stream, double *rel_step);
+
+/* C = op(A) op(B) (row-major, C is M x N) with the product engine of `prec`
+ * (FP64: DMMA; FP64_TC/FP32/MIXED_BF16: the tcgen05 slice engine at FP64-,
+ * FP32- or BF16-class accuracy), the building block of every loop above.
+ * trans_a: A is stored K x M; trans_b: B is stored N x K.  Device pointers;
+ * uses the handle's workspace. */
+int  pinv_gemm(pinv_handle *h, int M, int N, int K, const double *A, int lda, int trans_a,
+               const double *B, int ldb, int trans_b, double *C, int ldc, pinv_prec prec,
+               void *stream);
 
 /* For callers that cannot allocate device memory (a plugin whose host
  * framework owns the allocator, code under a pool that forbids cudaMalloc,

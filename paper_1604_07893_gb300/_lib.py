@@ -19,13 +19,13 @@ ERRORS = {-1: "PINV_ERR_ARG", -2: "PINV_ERR_BUDGET", -3: "PINV_ERR_NONFINITE", -
           -5: "PINV_ERR_MAXITER", -6: "PINV_ERR_TIMEOUT", -7: "PINV_ERR_CUDA", -8: "PINV_ERR_UNKNOWN_ID"}
 KIND = {"moore_penrose": 0, "drazin": 1, "outer_g": 2}
 STOP = {"rel_fro": 0, "paper": 1}
-PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3}
+PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3, "fp64_tc": 4}
 VARIANT = {"plain": 0, "stabilized": 1}
 FINISH = {None: 0, "none": 0, "clean": 1}
 HISTORY = 128
 
 EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_batched", "pinv_submit",
-           "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_step_noalloc")
+           "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_step_noalloc")
 NOALLOC_MAX_DIM = 128
 
 
@@ -51,7 +51,8 @@ class Info(C.Structure):
                 ("rel_step", C.c_double), ("alpha", C.c_double),
                 ("penrose", C.c_double * 4), ("drazin", C.c_double * 3), ("ms", C.c_float),
                 ("gemms", C.c_int), ("kernels", C.c_int), ("gemm_ms", C.c_float),
-                ("gemm_flops", C.c_double), ("history", C.c_double * HISTORY),
+                ("gemm_flops", C.c_double), ("tensor_flops", C.c_double),
+                ("history", C.c_double * HISTORY),
                 ("precision", C.c_byte * HISTORY)]
 
     def to_dict(self) -> dict:
@@ -61,7 +62,8 @@ class Info(C.Structure):
                     side="left" if self.side else "right", rel_step=self.rel_step, alpha=self.alpha,
                     penrose=list(self.penrose), drazin=list(self.drazin), ms=self.ms,
                     gemms=self.gemms, kernels=self.kernels, gemm_ms=self.gemm_ms,
-                    gemm_flops=self.gemm_flops, history=list(self.history[:n]),
+                    gemm_flops=self.gemm_flops, tensor_flops=self.tensor_flops,
+                    history=list(self.history[:n]),
                     precision=list(self.precision[:n]))
 
 
@@ -87,6 +89,8 @@ def load() -> C.CDLL:
     lib.pinv_alpha_estimate.argtypes = [C.c_void_p, P(Desc), C.c_void_p, P(C.c_double)]
     lib.pinv_step.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                               C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
+    lib.pinv_gemm.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                              C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
     lib.pinv_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
     for name in EXPORTS:
@@ -224,6 +228,24 @@ class Handle:
         if rc != PINV_OK:
             raise PinvError(rc, "pinv_alpha_estimate")
         return out.value
+
+    def gemm(self, A, B, *, trans_a=False, trans_b=False, prec="fp64", C=None, stream=None):
+        """pinv_gemm: C = op(A) op(B) with the product engine of `prec`."""
+        import torch
+        M = A.shape[1] if trans_a else A.shape[0]
+        K = A.shape[0] if trans_a else A.shape[1]
+        N = B.shape[0] if trans_b else B.shape[1]
+        if (B.shape[1] if trans_b else B.shape[0]) != K:
+            raise ValueError("inner dimensions differ")
+        if C is None:
+            C = torch.empty((M, N), dtype=torch.float64, device=A.device)
+        rc = self._lib.pinv_gemm(self._h, M, N, K, _dev_ptr(A),
+                                 A.stride(0), 1 if trans_a else 0, _dev_ptr(B), B.stride(0),
+                                 1 if trans_b else 0, _dev_ptr(C), C.stride(0), PREC[prec],
+                                 _stream_ptr(stream))
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_gemm")
+        return C
 
     def step(self, A, X_in, X_out=None, *, prec="fp64", stabilized=False, stream=None):
         """pinv_step: one loop of Eq. PM (or PM-modified).  Returns (X_out, rel_step)."""

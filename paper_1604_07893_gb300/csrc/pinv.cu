@@ -27,7 +27,7 @@
 
 #include "../../include/pinv.h"
 #include "common.h"
-#include "mixed.h"
+#include "tc_gemm.h"
 
 using namespace pinv;
 
@@ -74,7 +74,7 @@ struct pinv_handle {
     size_t ws_bytes = 0;
     double* pinned = nullptr;  // host pinned readback block
     double* dsmall = nullptr;  // device: reduction outputs
-    MixedEngine* mixed = nullptr;
+    int* derr = nullptr;       // device error word of the tensor-core kernels
     std::vector<cudaEvent_t> events;  // profiling pool (pairs), created on demand
     // serving
     std::mutex mu;
@@ -118,11 +118,15 @@ struct Ctx {
     double* big[2];   // max(m,n)^2 scratch for residual checks
     double* partials; // pair partials
     double* red;      // reduction scratch (2 * 256 pairs)
+    int prec_k = 0;         // product precision of the GEMMs being issued (0 = DMMA FP64)
+    void* tcws = nullptr;   // slice workspace of the tensor-core engine
+    size_t tcws_bytes = 0;
     int gemms = 0;
     int kernels = 0;
     bool profile = false;
     int ev_used = 0;        // event pairs recorded since the last harvest
     double gemm_flops = 0;
+    double tensor_flops = 0;
     float gemm_ms = 0;
     Coef c;
 };
@@ -154,7 +158,12 @@ void prof_harvest(Ctx& c) {  // stream already synchronised
     c.ev_used = 0;
 }
 
-size_t workspace_bytes(int m, int n, bool drazin, bool host, bool check) {
+size_t tc_bytes(int m, int n, int prec) {
+    const int big = std::max(m, n);
+    return prec == PINV_PREC_FP64 ? 0 : tc_workspace_bytes(big, big, big, tc_mode(TC_FP64));
+}
+
+size_t workspace_bytes(int m, int n, bool drazin, bool host, bool check, int prec) {
     // `check` also covers the finish step: both need the two max(m,n)^2 squares
     const size_t s = std::min(m, n), big = std::max(m, n);
     size_t b = 0;
@@ -164,8 +173,9 @@ size_t workspace_bytes(int m, int n, bool drazin, bool host, bool check) {
     if (host) b += 2 * align_up(sizeof(double) * n * (size_t)m);
     if (check) b += 2 * align_up(sizeof(double) * big * big);
     const size_t tiles = (size_t)((big + 63) / 64) * ((big + 63) / 64);
-    b += align_up(sizeof(double) * 2 * tiles);
+    b += align_up(sizeof(double) * 2 * 4 * tiles);   // pair partials (4 per tensor-core tile)
     b += align_up(sizeof(double) * 2 * 2 * 256);
+    b += align_up(tc_bytes(m, n, prec));
     return b;
 }
 
@@ -183,7 +193,7 @@ int ensure_workspace(pinv_handle* h, size_t bytes) {
     return PINV_OK;
 }
 
-void carve(Ctx& c, bool drazin, bool host, bool check) {
+void carve(Ctx& c, bool drazin, bool host, bool check, int prec) {
     char* p = c.h->ws;
     auto take = [&](size_t bytes) { char* q = p; p += align_up(bytes); return (double*)q; };
     const size_t s = c.s, big = std::max(c.m, c.n);
@@ -195,8 +205,10 @@ void carve(Ctx& c, bool drazin, bool host, bool check) {
     c.big[0] = check ? take(sizeof(double) * big * big) : nullptr;
     c.big[1] = check ? take(sizeof(double) * big * big) : nullptr;
     const size_t tiles = (size_t)((big + 63) / 64) * ((big + 63) / 64);
-    c.partials = take(sizeof(double) * 2 * tiles);
+    c.partials = take(sizeof(double) * 2 * 4 * tiles);
     c.red = take(sizeof(double) * 2 * 2 * 256);
+    c.tcws_bytes = tc_bytes(c.m, c.n, prec);
+    c.tcws = c.tcws_bytes ? (void*)take(c.tcws_bytes) : nullptr;
 }
 
 int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const double* B, int ldb,
@@ -205,7 +217,15 @@ int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const d
     ++c.kernels;
     c.gemm_flops += 2.0 * M * N * K;
     const int slot = prof_begin(c);
-    const int r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st);
+    int r;
+    if (c.prec_k == 0) {
+        r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st);
+    } else {
+        --c.kernels;  // tc_gemm counts its own launches (slicing + GEMM)
+        c.tensor_flops += 2.0 * M * N * K * tc_pairs(tc_mode(c.prec_k));
+        r = tc_gemm(M, N, K, A, lda, tA, B, ldb, tB, e, tc_mode(c.prec_k), c.tcws, c.tcws_bytes,
+                    c.h->derr, c.st, &c.kernels);
+    }
     prof_end(c, slot);
     return r;
 }
@@ -215,10 +235,18 @@ int read_norms(Ctx& c, int count, double* dx2, double* x2) {
     reduce_pairs(c.partials, count, c.h->dsmall, c.st);
     ++c.kernels;
     CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaMemcpyAsync(c.h->pinned + 2, c.h->derr, sizeof(int), cudaMemcpyDeviceToHost, c.st));
     CK(cudaStreamSynchronize(c.st));
     prof_harvest(c);
     *dx2 = c.h->pinned[0];
     *x2 = c.h->pinned[1];
+    int derr;
+    std::memcpy(&derr, c.h->pinned + 2, sizeof(int));
+    if (derr) {
+        std::fprintf(stderr, "pinv: tensor-core kernel wait timed out (code %d)\n", derr);
+        cudaMemsetAsync(c.h->derr, 0, sizeof(int), c.st);
+        return PINV_ERR_TIMEOUT;
+    }
     return PINV_OK;
 }
 
@@ -382,7 +410,8 @@ int validate(const pinv_desc* d) {
     if (!(d->tol >= 0.0)) return PINV_ERR_ARG;
     if (d->stop != PINV_STOP_REL_FRO && d->stop != PINV_STOP_PAPER) return PINV_ERR_ARG;
     if (d->max_iter < 0 || d->max_iter > PINV_HISTORY) return PINV_ERR_ARG;
-    if (d->prec != PINV_PREC_FP64 && d->prec != PINV_PREC_MIXED_BF16 && d->prec != PINV_PREC_FP32)
+    if (d->prec != PINV_PREC_FP64 && d->prec != PINV_PREC_MIXED_BF16 && d->prec != PINV_PREC_FP32 &&
+        d->prec != PINV_PREC_FP64_TC)
         return PINV_ERR_ARG;
     if (d->variant != PINV_VARIANT_PLAIN && d->variant != PINV_VARIANT_STABILIZED) return PINV_ERR_ARG;
     if (d->finish != PINV_FINISH_NONE && d->finish != PINV_FINISH_CLEAN) return PINV_ERR_ARG;
@@ -400,11 +429,11 @@ int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
     const bool drazin = d->kind == PINV_DRAZIN;
     const bool host = d->host_buffers != 0;
     const bool check = d->check != 0 || d->finish == PINV_FINISH_CLEAN;
-    size_t bytes = workspace_bytes(d->m, d->n, drazin, host, check);
-    if (d->prec != PINV_PREC_FP64) bytes += mixed_workspace_bytes(d->m, d->n);
+    size_t bytes = workspace_bytes(d->m, d->n, drazin, host, check, d->prec);
     int rc = ensure_workspace(h, bytes);
     if (rc) return rc;
-    carve(c, drazin, host, check);
+    carve(c, drazin, host, check, d->prec);
+    c.prec_k = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;
     if (host) {
         CK(cudaMemcpy2DAsync(c.Ad, sizeof(double) * d->n, d->A, sizeof(double) * d->lda,
                              sizeof(double) * d->n, d->m, cudaMemcpyHostToDevice, st));
@@ -498,30 +527,30 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
     double prev = INFINITY;
     bool stabilise = false;
     int status = PINV_ERR_MAXITER, reason = 2;
-    MixedSchedule sched;
-    const bool mixed = d->prec != PINV_PREC_FP64;
-    if (mixed) {
-        if (!h->mixed) h->mixed = mixed_create();
-        rc = mixed_begin(h->mixed, c.m, c.n, c.left, c.A, c.lda, d->prec, c.st, &sched);
-        if (rc) return info->status = rc;
-    }
+    // precision of the final (FP64-class) products: native FP64 or the tensor-core engine
+    const int fp64_class = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;
+    // Precision schedule: the level only rises.  BF16 serves the growth phase
+    // (step > 0.5: the iterate is still being scaled up and any error is
+    // corrected later -- for problems without a null block); FP32-class
+    // products then run until the step falls below 1e-4 or stops falling
+    // (their noise floor); every later loop, the stop rule and the switch to
+    // the stabilised loop use FP64-class products.
+    int level = d->prec == PINV_PREC_MIXED_BF16 ? TC_BF16 : (d->prec == PINV_PREC_FP32 ? TC_FP32 : fp64_class);
+    int prev_prec = -1;
+    double prev2 = INFINITY;
     for (int k = 0; k < max_iter; ++k) {
         const bool stab_now = stabilise;
         const double* Xk = c.X[cur];
         double* Xn = c.X[cur ^ 1];
         int parts;
-        int prec_k = 0;
-        if (mixed) {
-            prec_k = mixed_loop_precision(&sched, k, prev);
-        }
+        // product precision of loop k (the step of loop k-1 says how far from
+        // convergence the iterate is; low precision only far from it)
+        if (level == TC_BF16 && prev <= 0.5) level = TC_FP32;
+        if (level == TC_FP32 && (prev <= 1e-4 || (prev < 1e-2 && prev >= 0.25 * prev2))) level = fp64_class;
+        const int prec_k = level;
+        c.prec_k = prec_k;
         double* target = stab_now ? c.X[2] : Xn;
-        if (prec_k == 0) {
-            parts = pm_loop_f64(c, Xk, target);
-        } else {
-            parts = mixed_pm_loop(h->mixed, &sched, prec_k, Xk, target, c.partials, c.st);
-            c.gemms += 7;
-            c.kernels += mixed_last_kernels(h->mixed);
-        }
+        parts = pm_loop_f64(c, Xk, target);
         if (stab_now) {
             parts = stabilise_f64(c, c.X[2], Xk, Xn);
             ++info->stabilized_loops;
@@ -534,23 +563,29 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         info->loops_run = k + 1;
         if (k < PINV_HISTORY) {
             info->history[k] = e;
-            info->precision[k] = (signed char)prec_k;
+            info->precision[k] = (signed char)(prec_k == 0 ? 0 : prec_k);
         }
         if (!std::isfinite(e)) { status = PINV_ERR_NONFINITE; info->iters = k; break; }
         if (e < d->tol) { status = PINV_OK; reason = 0; cur ^= 1; info->iters = k + 1; info->rel_step = e; break; }
+        // the stop rule compares two consecutive FP64-class loops only: the first
+        // FP64-class step after lower-precision loops removes their noise
+        const bool final_class = prec_k == fp64_class && prev_prec == fp64_class;
         const bool stalled = stab_now ? (e >= prev) : (prev < floor_guard && e >= prev * prev);
-        if (stalled && prec_k != 1) { status = PINV_OK; reason = 1; info->iters = k; info->rel_step = prev; break; }
+        if (stalled && final_class) { status = PINV_OK; reason = 1; info->iters = k; info->rel_step = prev; break; }
         // divergence guard on the relative step: a convergent loop grows X by at
         // most a factor 18 (|p(r)| <= 18 for |r| <= 1)
         const double rel = x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY;
         if (rel > 1e3 && k > 0) { status = PINV_ERR_DIVERGED; info->iters = k; break; }
-        if (d->variant == PINV_VARIANT_STABILIZED && e < switch_tol && prec_k != 1) stabilise = true;
+        if (d->variant == PINV_VARIANT_STABILIZED && e < switch_tol && prec_k == fp64_class) stabilise = true;
+        prev2 = prev;
         prev = e;
+        prev_prec = prec_k;
         info->rel_step = e;
         cur ^= 1;
         info->iters = k + 1;
     }
     info->stop_reason = reason;
+    c.prec_k = fp64_class;
     if (status == PINV_OK && d->finish == PINV_FINISH_CLEAN) {
         // projection, then one FP64 loop (Theorems 6.2 / 7.1: the blocks the
         // loop does not contract are removed, the range block is re-contracted)
@@ -577,6 +612,7 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
     info->kernels = c.kernels;
     info->gemm_ms = c.gemm_ms;
     info->gemm_flops = c.gemm_flops;
+    info->tensor_flops = c.tensor_flops;
     info->ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return info->status = status;
 }
@@ -594,6 +630,8 @@ int pinv_init(pinv_handle** out, const pinv_config* cfg) {
     cudaError_t e = cudaSetDevice(h->device);
     if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 64 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->dsmall, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&h->derr, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(h->derr, 0, sizeof(int));
     if (e != cudaSuccess) {
         std::fprintf(stderr, "pinv_init: %s\n", cudaGetErrorString(e));
         if (h->pinned) cudaFreeHost(h->pinned);
@@ -608,7 +646,7 @@ void pinv_destroy(pinv_handle* h) {
     if (!h) return;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
-    if (h->mixed) mixed_destroy(h->mixed);
+    if (h->derr) cudaFree(h->derr);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     if (h->ws) cudaFree(h->ws);
     if (h->dsmall) cudaFree(h->dsmall);
@@ -642,7 +680,7 @@ int pinv_submit(pinv_handle* h, const pinv_desc* desc, uint64_t* id) {
     if (rc) return rc;
     const size_t need = workspace_bytes(desc->m, desc->n, desc->kind == PINV_DRAZIN,
                                         desc->host_buffers != 0,
-                                        desc->check != 0 || desc->finish == PINV_FINISH_CLEAN);
+                                        desc->check != 0 || desc->finish == PINV_FINISH_CLEAN, desc->prec);
     if (h->budget && need > h->budget) return PINV_ERR_BUDGET;
     std::lock_guard<std::mutex> lk(h->mu);
     *id = h->next_id++;
@@ -694,7 +732,8 @@ int pinv_step(pinv_handle* h, int m, int n, const double* A, int lda, const doub
               double* rel_step) {
     if (!h || m < 1 || n < 1 || !A || !X_in || !X_out || lda < n || ldx != m || X_in == X_out)
         return PINV_ERR_ARG;
-    if (prec != PINV_PREC_FP64 && prec != PINV_PREC_MIXED_BF16 && prec != PINV_PREC_FP32)
+    if (prec != PINV_PREC_FP64 && prec != PINV_PREC_MIXED_BF16 && prec != PINV_PREC_FP32 &&
+        prec != PINV_PREC_FP64_TC)
         return PINV_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
     pinv_desc d{};
@@ -704,23 +743,49 @@ int pinv_step(pinv_handle* h, int m, int n, const double* A, int lda, const doub
     cudaStream_t st = (cudaStream_t)stream;
     int rc = setup_context(h, &d, st, c);
     if (rc) return rc;
-    int parts;
-    if (prec == PINV_PREC_FP64) {
-        parts = pm_loop_f64(c, X_in, stabilized ? c.X[2] : X_out);
-    } else {
-        MixedSchedule sched;
-        if (!h->mixed) h->mixed = mixed_create();
-        rc = mixed_begin(h->mixed, m, n, c.left, A, lda, prec, st, &sched);
-        if (rc) return rc;
-        const int pk = prec == PINV_PREC_MIXED_BF16 ? 1 : 3;
-        parts = mixed_pm_loop(h->mixed, &sched, pk, X_in, stabilized ? c.X[2] : X_out, c.partials, st);
-    }
+    c.prec_k = prec == PINV_PREC_FP64 ? 0 : (prec == PINV_PREC_MIXED_BF16 ? TC_BF16 : (prec == PINV_PREC_FP32 ? TC_FP32 : TC_FP64));
+    int parts = pm_loop_f64(c, X_in, stabilized ? c.X[2] : X_out);
     if (stabilized) parts = stabilise_f64(c, c.X[2], X_in, X_out);
     if (parts < 0) return PINV_ERR_CUDA;
     double dx2, x2;
     rc = read_norms(c, parts, &dx2, &x2);
     if (rc) return rc;
     if (rel_step) *rel_step = x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY;
+    CK(cudaGetLastError());
+    return PINV_OK;
+}
+
+int pinv_gemm(pinv_handle* h, int M, int N, int K, const double* A, int lda, int trans_a,
+              const double* B, int ldb, int trans_b, double* C, int ldc, pinv_prec prec,
+              void* stream) {
+    if (!h || M < 1 || N < 1 || K < 1 || !A || !B || !C || ldc < N) return PINV_ERR_ARG;
+    if (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N)) return PINV_ERR_ARG;
+    if (prec != PINV_PREC_FP64 && prec != PINV_PREC_MIXED_BF16 && prec != PINV_PREC_FP32 &&
+        prec != PINV_PREC_FP64_TC)
+        return PINV_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int pk = prec == PINV_PREC_FP64 ? 0 : (prec == PINV_PREC_MIXED_BF16 ? TC_BF16 : (prec == PINV_PREC_FP32 ? TC_FP32 : TC_FP64));
+    Epilogue e = epi1(term(C, ldc, 1));
+    if (pk == 0) {
+        if (gemm_f64(M, N, K, A, lda, trans_a != 0, B, ldb, trans_b != 0, e, st) < 0) return PINV_ERR_CUDA;
+    } else {
+        const size_t need = tc_workspace_bytes(M, N, K, tc_mode(pk));
+        int rc = ensure_workspace(h, std::max(need, h->ws_bytes));
+        if (rc) return rc;
+        int kernels = 0;
+        if (tc_gemm(M, N, K, A, lda, trans_a != 0, B, ldb, trans_b != 0, e, tc_mode(pk), h->ws, h->ws_bytes,
+                    h->derr, st, &kernels) < 0)
+            return PINV_ERR_CUDA;
+    }
+    CK(cudaMemcpyAsync(h->pinned + 2, h->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    int derr;
+    std::memcpy(&derr, h->pinned + 2, sizeof(int));
+    if (derr) {
+        cudaMemset(h->derr, 0, sizeof(int));
+        return PINV_ERR_TIMEOUT;
+    }
     CK(cudaGetLastError());
     return PINV_OK;
 }

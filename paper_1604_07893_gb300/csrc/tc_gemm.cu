@@ -1,0 +1,521 @@
+// Tensor-core GEMM for every product of the iteration on sm_103a.
+//
+// C (M x N, FP64) = op(A) op(B) evaluated as a sum of BF16 slice products:
+//   op(A) = sum_s A_s,  op(B) = sum_t B_t,   C = sum_{s + t <= L} A_s B_t.
+// Slices are BF16 matrices.  In the exact modes (FP64-class, FP32-class) each
+// row of op(A) (column of op(B)) is cut on a power-of-two grid with 6 bits per
+// slice, so every slice entry is q * 2^e with |q| <= 64: bf16 holds it exactly,
+// every product q q' 2^(e+e') is exact, and a K-chunk of <= 2048 products sums
+// to an integer multiple of one power of two below 2^23 -- the FP32 tensor-core
+// accumulation is exact.  Each (pair, chunk) accumulator is drained from TMEM
+// and added in FP64 in the epilogue, so the only rounding is the FP64 sum of
+// the slice products and the truncation of slices beyond s + t > L.
+//   FP64-class: 9 slices per operand, s + t <= 8 (45 products)
+//   FP32-class: 4 slices, s + t <= 3 (10 products)
+//   BF16:       1 slice rounded to nearest (no grid), one product
+//
+// Kernel layout (one persistent CTA per SM, 6 warps):
+//   warp 0      TMA producer: 3-D tensor maps [slice][row][k], 128B swizzle,
+//               ragged edges zero-filled by the TMA unit
+//   warp 1      TMEM allocator + single-thread tcgen05.mma issuer
+//               (M = 128, N = BN, K = 16 per instruction, kind::f16, BF16 in,
+//               FP32 accumulate), two TMEM accumulators so the epilogue drains
+//               one while the next (pair, chunk) accumulates
+//   warps 2..5  epilogue: tcgen05.ld 32x32b, FP64 accumulation in registers,
+//               then the fused combination of Eq. PM (identity, side inputs,
+//               up to three outputs) and the stop-norm partials
+// Every mbarrier wait is bounded; on timeout the kernel records an error code,
+// releases its TMEM and returns.
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+#include <mutex>
+
+#include "common.h"
+#include "tc_gemm.h"
+
+namespace pinv {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 64;
+constexpr int BK = 64;          // 64 bf16 = one 128-byte swizzle row
+constexpr int STAGES = 8;
+constexpr int THREADS = 192;
+constexpr int A_TILE_BYTES = BM * BK * 2;   // 16 KiB
+constexpr int B_TILE_BYTES = BN * BK * 2;   //  8 KiB
+constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
+constexpr int TMEM_COLS = 2 * BN;           // two accumulators
+constexpr unsigned WAIT_LIMIT = 1u << 22;   // polls before a wait gives up (about a second)
+
+struct TcParams {
+    int M, N, K;          // K = logical length (the tensor maps are zero-padded beyond it)
+    int npairs;
+    int pair_s[64], pair_t[64];
+    int chunk;            // K elements per exact accumulation
+    int tiles_m, tiles_n;
+    Epilogue epi;
+    int* err;             // device error word (0 = ok)
+};
+
+// ------------------------------------------------------------------ PTX helpers
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// Bounded wait for the phase with parity `parity` to complete.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const uint32_t addr = smem_u32(bar);
+    for (unsigned i = 0; i < WAIT_LIMIT; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(addr), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1, int c2) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%3, %4, %5}], [%2];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
+        : "memory");
+}
+// Shared-memory matrix descriptor: K-major tile, rows of 128 bytes, 128B swizzle,
+// 8-row core-matrix groups 1024 bytes apart.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((addr >> 4) & 0x3FFF);
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused for SW128 K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+// Instruction descriptor, kind::f16: BF16 A/B, FP32 D, both K-major, M = 128, N = BN.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                     smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+    uint32_t r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void record_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// ------------------------------------------------------------------ the kernel
+__global__ void __launch_bounds__(THREADS, 1)
+tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
+               const __grid_constant__ TcParams P) {
+    extern __shared__ __align__(1024) uint8_t smem_raw[];
+    uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+    uint64_t* empty = full + STAGES;
+    uint64_t* accf = empty + STAGES;
+    uint64_t* acce = accf + 2;
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acce + 2);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntiles = P.tiles_m * P.tiles_n;
+    const int kchunks = (P.K + P.chunk - 1) / P.chunk;
+    const int units = P.npairs * kchunks;
+
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 128); }
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tmem_holder)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_holder;
+
+    if (warp == 0) {
+        // ---------------------------------------------------------- TMA producer
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+                const int m0 = (tile % P.tiles_m) * BM, n0 = (tile / P.tiles_m) * BN;
+                for (int u = 0; u < units && !*abort_flag; ++u) {
+                    const int pr = u / kchunks, ch = u % kchunks;
+                    const int k_begin = ch * P.chunk;
+                    const int k_end = min(P.K, k_begin + P.chunk);
+                    for (int k = k_begin; k < k_end; k += BK) {
+                        if (!mbar_wait(&empty[stage], phase ^ 1)) {
+                            record_error(P.err, 1); *abort_flag = 1; break;
+                        }
+                        uint8_t* sa = smem + stage * STAGE_BYTES;
+                        mbar_expect_tx(&full[stage], STAGE_BYTES);
+                        tma_load_3d(sa, &mapA, &full[stage], k, m0, P.pair_s[pr]);
+                        tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, P.pair_t[pr]);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                    }
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------------- MMA issuer
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_bf16(BM, BN);
+            int stage = 0;
+            uint32_t phase = 0;
+            int buf = 0;
+            uint32_t accphase[2] = {0, 0};
+            for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+                for (int u = 0; u < units && !*abort_flag; ++u) {
+                    const int ch = u % kchunks;
+                    const int k_begin = ch * P.chunk;
+                    const int k_end = min(P.K, k_begin + P.chunk);
+                    if (!mbar_wait(&acce[buf], accphase[buf] ^ 1)) {
+                        record_error(P.err, 2); *abort_flag = 1; break;
+                    }
+                    tc_fence_after();
+                    const uint32_t d = tmem + buf * BN;
+                    uint32_t acc = 0;
+                    for (int k = k_begin; k < k_end; k += BK) {
+                        if (!mbar_wait(&full[stage], phase)) {
+                            record_error(P.err, 3); *abort_flag = 1; break;
+                        }
+                        tc_fence_after();
+                        const uint32_t a0 = smem_u32(smem + stage * STAGE_BYTES);
+                        const uint32_t b0 = a0 + A_TILE_BYTES;
+#pragma unroll
+                        for (int kk = 0; kk < BK / 16; ++kk) {
+                            mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc, acc);
+                            acc = 1;
+                        }
+                        mma_commit(&empty[stage]);
+                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                    }
+                    mma_commit(&accf[buf]);
+                    accphase[buf] ^= 1;
+                    buf ^= 1;
+                }
+            }
+        }
+    } else {
+        // ---------------------------------------------------------- epilogue (warps 2..5)
+        const int lg = warp & 3;                 // TMEM lane group of this warp
+        const int row_in_tile = lg * 32 + lane;
+        int buf = 0;
+        uint32_t accphase[2] = {0, 0};
+        const Epilogue& E = P.epi;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            const int m0 = (tile % P.tiles_m) * BM, n0 = (tile / P.tiles_m) * BN;
+            double acc[BN];
+#pragma unroll
+            for (int j = 0; j < BN; ++j) acc[j] = 0.0;
+            bool ok = true;
+            for (int u = 0; u < units; ++u) {
+                if (*abort_flag || !mbar_wait(&accf[buf], accphase[buf])) {
+                    record_error(P.err, 4); *abort_flag = 1; ok = false; break;
+                }
+                tc_fence_after();
+                const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + buf * BN;
+#pragma unroll
+                for (int c = 0; c < BN; c += 32) {
+                    float v[32];
+                    tmem_ld32(taddr + c, v);
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) acc[c + j] += (double)v[j];
+                }
+                tc_fence_before();
+                mbar_arrive(&acce[buf]);
+                accphase[buf] ^= 1;
+                buf ^= 1;
+            }
+            if (!ok) break;
+            // fused FP64 epilogue for this row of the tile
+            const int row = m0 + row_in_tile;
+            double sd = 0.0, sx = 0.0;
+            if (row < P.M) {
+                const double* s1 = E.s1 ? E.s1 + (size_t)row * E.ld1 : nullptr;
+                const double* s2 = E.s2 ? E.s2 + (size_t)row * E.ld2 : nullptr;
+#pragma unroll
+                for (int j = 0; j < BN; ++j) {
+                    const int col = n0 + j;
+                    if (col < P.N) {
+                        const double a = acc[j];
+                        const double v1 = s1 ? s1[col] : 0.0;
+                        const double v2 = s2 ? s2[col] : 0.0;
+                        const double id = (row == col) ? 1.0 : 0.0;
+#pragma unroll
+                        for (int o = 0; o < 3; ++o) {
+                            if (o < E.nout) {
+                                const EpiTerm& t = E.o[o];
+                                const double v = t.a_acc * a + t.a_s1 * v1 + t.a_s2 * v2 + t.a_id * id;
+                                if (t.out) t.out[(size_t)row * t.ld + col] = v;
+                                if (o == 0) { const double dd = v - v1; sd += dd * dd; sx += v1 * v1; }
+                            }
+                        }
+                    }
+                }
+            }
+            if (E.partials) {  // one pair per (tile, epilogue warp): no barrier between warps
+#pragma unroll
+                for (int off = 16; off; off >>= 1) {
+                    sd += __shfl_xor_sync(0xffffffffu, sd, off);
+                    sx += __shfl_xor_sync(0xffffffffu, sx, off);
+                }
+                if (lane == 0) {
+                    E.partials[2 * (4 * tile + lg)] = sd;
+                    E.partials[2 * (4 * tile + lg) + 1] = sx;
+                }
+            }
+        }
+    }
+
+    __syncwarp();
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
+    }
+}
+
+// ------------------------------------------------------------------ slicing
+// Rows of op(X) (op(X)[i][k] = trans ? X[k][i] : X[i][k]); one exponent per row:
+// e_i with 2^e_i > max_k |op(X)[i][k]|.
+__global__ void row_exponent_kernel(int rows, int K, const double* X, int ld, int trans, int* e) {
+    if (!trans) {
+        const int warps = blockDim.x >> 5;
+        const int i = blockIdx.x * warps + (threadIdx.x >> 5);
+        const int lane = threadIdx.x & 31;
+        if (i >= rows) return;
+        double mx = 0.0;
+        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[(size_t)i * ld + k]));
+        for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        if (lane == 0) { int ex = 0; if (mx > 0) frexp(mx, &ex); e[i] = ex; }
+    } else {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= rows) return;
+        double mx = 0.0;
+        for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(X[(size_t)k * ld + i]));
+        int ex = 0;
+        if (mx > 0) frexp(mx, &ex);
+        e[i] = ex;
+    }
+}
+
+// out[s][i][k] (bf16, row length Kp) for 32 x 32 tiles of op(X); zero beyond K.
+// exact = 1: slices on the per-row grid 2^(e_i - 6(s+1)); exact = 0: one
+// round-to-nearest slice.
+__global__ void slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans, const int* e,
+                             int S, int exact, __nv_bfloat16* out) {
+    __shared__ double t[32][33];
+    const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        double v = 0.0;
+        if (trans) {  // X is K x rows: read along i (contiguous)
+            const int k = k0 + r, i = i0 + tx;
+            if (k < K && i < rows) v = X[(size_t)k * ld + i];
+            t[tx][r] = v;      // t[i_local][k_local]
+        } else {
+            const int i = i0 + r, k = k0 + tx;
+            if (k < K && i < rows) v = X[(size_t)i * ld + k];
+            t[r][tx] = v;
+        }
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + r, k = k0 + tx;
+        if (i >= rows || k >= Kp) continue;
+        double x = (k < K) ? t[r][tx] : 0.0;
+        const size_t plane = (size_t)rows * Kp;
+        if (!exact) {
+            out[(size_t)i * Kp + k] = __double2bfloat16(x);
+            for (int s = 1; s < S; ++s) out[s * plane + (size_t)i * Kp + k] = __double2bfloat16(0.0);
+            continue;
+        }
+        const int ei = e[i];
+        for (int s = 0; s < S; ++s) {
+            const int sh = ei - 6 * (s + 1);
+            const double q = rint(ldexp(x, -sh));     // |q| <= 64
+            const double piece = ldexp(q, sh);
+            out[s * plane + (size_t)i * Kp + k] = __float2bfloat16_rn((float)piece);
+            x -= piece;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ host side
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled get_encode() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int S, int rows, int Kp, int box_rows) {
+    EncodeTiled enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t dims[3] = {(cuuint64_t)Kp, (cuuint64_t)rows, (cuuint64_t)S};
+    cuuint64_t strides[2] = {(cuuint64_t)Kp * 2, (cuuint64_t)rows * Kp * 2};
+    cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+    cuuint32_t elem[3] = {1, 1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, (void*)base, dims, strides, box, elem,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+int num_sms() {
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 1;
+    }
+    return sms;
+}
+
+}  // namespace
+
+TcMode tc_mode(int prec) {
+    TcMode m;
+    if (prec == TC_BF16) { m.S = 1; m.L = 0; m.exact = 0; }
+    else if (prec == TC_FP32) { m.S = 4; m.L = 3; m.exact = 1; }
+    else { m.S = 9; m.L = 8; m.exact = 1; }
+    return m;
+}
+
+int tc_pairs(const TcMode& m) {
+    int n = 0;
+    for (int s = 0; s < m.S; ++s)
+        for (int t = 0; t < m.S; ++t)
+            if (s + t <= m.L) ++n;
+    return n;
+}
+
+size_t tc_workspace_bytes(int M, int N, int K, const TcMode& m) {
+    const size_t Kp = (size_t)((K + 7) / 8) * 8;
+    auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
+    return al((size_t)m.S * M * Kp * 2) + al((size_t)m.S * N * Kp * 2) + al(sizeof(int) * (M + N)) + 1024;
+}
+
+size_t tc_smem_bytes() { return STAGES * STAGE_BYTES + 1024 + 256; }
+
+int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb, bool transB,
+            const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err, cudaStream_t st,
+            int* kernels) {
+    const int Kp = ((K + 7) / 8) * 8;
+    if (tc_workspace_bytes(M, N, K, mode) > ws_bytes) return -1;
+    auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
+    char* p = static_cast<char*>(ws);
+    __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(p);
+    p += al((size_t)mode.S * M * Kp * 2);
+    __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(p);
+    p += al((size_t)mode.S * N * Kp * 2);
+    int* ea = reinterpret_cast<int*>(p);
+    int* eb = ea + M;
+
+    // slices of op(A) (rows i, length K) and of op(B)^T (rows j, length K)
+    if (mode.exact) {
+        if (!transA) row_exponent_kernel<<<(M + 7) / 8, 256, 0, st>>>(M, K, A, lda, 0, ea);
+        else         row_exponent_kernel<<<(M + 127) / 128, 128, 0, st>>>(M, K, A, lda, 1, ea);
+        // op(B)^T row j = column j of op(B): B stored K x N (trans=1 view) unless transB
+        if (transB) row_exponent_kernel<<<(N + 7) / 8, 256, 0, st>>>(N, K, B, ldb, 0, eb);
+        else        row_exponent_kernel<<<(N + 127) / 128, 128, 0, st>>>(N, K, B, ldb, 1, eb);
+        *kernels += 2;
+    }
+    {
+        dim3 blk(32, 8);
+        dim3 ga((Kp + 31) / 32, (M + 31) / 32), gb((Kp + 31) / 32, (N + 31) / 32);
+        slice_kernel<<<ga, blk, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, ea, mode.S, mode.exact, sa);
+        slice_kernel<<<gb, blk, 0, st>>>(N, K, Kp, B, ldb, transB ? 0 : 1, eb, mode.S, mode.exact, sb);
+        *kernels += 2;
+    }
+    CUtensorMap ma, mb;
+    if (!make_map(&ma, sa, mode.S, M, Kp, BM) || !make_map(&mb, sb, mode.S, N, Kp, BN)) return -1;
+
+    TcParams P;
+    P.M = M; P.N = N; P.K = K;
+    P.npairs = 0;
+    for (int s = 0; s < mode.S; ++s)
+        for (int t = 0; t < mode.S; ++t)
+            if (s + t <= mode.L) { P.pair_s[P.npairs] = s; P.pair_t[P.npairs] = t; ++P.npairs; }
+    P.chunk = mode.exact ? 2048 : ((K + BK - 1) / BK) * BK;
+    P.tiles_m = (M + BM - 1) / BM;
+    P.tiles_n = (N + BN - 1) / BN;
+    P.epi = epi;
+    P.err = err;
+    const int tiles = P.tiles_m * P.tiles_n;
+    const int grid = tiles < num_sms() ? tiles : num_sms();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+        attr = true;
+    }
+    tc_gemm_kernel<<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+    *kernels += 1;
+    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    return 4 * tiles;   // pair partials: one per (tile, epilogue warp)
+}
+
+}  // namespace pinv

@@ -1,0 +1,32 @@
+// Tensor-core GEMM engine (tcgen05 + TMA + TMEM) for sm_103a.
+#pragma once
+
+#include <cstddef>
+
+#include "common.h"
+
+namespace pinv {
+
+// Product precisions of the engine (values match pinv_prec where they overlap).
+enum { TC_BF16 = 1, TC_FP32 = 3, TC_FP64 = 4 };
+
+// S slices per operand, slice pairs with s + t <= L, exact = power-of-two grid
+// slices (FP64/FP32-class) instead of one round-to-nearest BF16 slice.
+struct TcMode {
+    int S, L, exact;
+};
+
+TcMode tc_mode(int prec);
+int tc_pairs(const TcMode& m);
+size_t tc_workspace_bytes(int M, int N, int K, const TcMode& m);
+size_t tc_smem_bytes();
+
+// C = op(A) op(B) with the fused FP64 epilogue `epi`.  `ws` holds the slices.
+// `err` is a device int that records a timed-out wait (0 = ok).  Adds the
+// number of kernels launched to *kernels.  Returns the count of pair partials
+// written when epi.partials is set (4 per 128 x 64 output tile) or -1.
+int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb,
+            bool transB, const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err,
+            cudaStream_t st, int* kernels);
+
+}  // namespace pinv

@@ -1,0 +1,124 @@
+"""GPU checks of the tcgen05 slice engine (through pinv_gemm / pinv_step /
+pinv_solve) against extended-precision references and the oracle.
+
+Error bounds, per element, relative to (|op(A)| |op(B)|)_ij:
+* FP64-class (9 exact slices, 45 products): 4e-16 (native FP64 rounding is
+  about K u / sqrt(K) ~ 1e-16 here; the dropped slice products are 2^-60);
+* FP32-class (4 slices, 10 products): 2e-7 (the first dropped products are
+  2^-30 of the row/column maxima);
+* BF16 (one round-to-nearest slice, FP32 accumulation): 2^-7.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import hyperpower as H
+from paper_1604_07893_gb300 import workloads as W
+from tests.helpers import pinv_closed_form, rel
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+BOUND = {"fp64_tc": 4e-16, "fp32": 2e-7, "mixed_bf16": 2.0 ** -7}
+
+
+@pytest.fixture(scope="module")
+def handle():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_07893_gb300 import Handle
+    h = Handle(0)
+    yield h
+    h.close()
+
+
+def dev(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).cuda()
+
+
+def check_gemm(h, A, B, ta, tb, prec):
+    opA = A.T if ta else A
+    opB = B.T if tb else B
+    ref = opA.astype(np.longdouble) @ opB.astype(np.longdouble)
+    scale = np.abs(opA) @ np.abs(opB)
+    C = h.gemm(dev(A), dev(B), trans_a=ta, trans_b=tb, prec=prec)
+    torch.cuda.synchronize()
+    err = (np.abs(C.cpu().numpy() - ref) / np.maximum(scale, 1e-300)).astype(np.float64)
+    return float(err.max())
+
+
+@pytest.mark.parametrize("prec", ["fp64_tc", "fp32", "mixed_bf16"])
+@pytest.mark.parametrize("M,N,K", [(128, 64, 64), (1, 1, 1), (200, 136, 300), (130, 70, 2100),
+                                   (257, 129, 4101)])
+def test_gemm_against_extended_precision(handle, prec, M, N, K):
+    rng = np.random.default_rng(M * 31 + N * 7 + K)
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-4, 4, (M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-4, 4, (1, N)))
+    assert check_gemm(handle, A, B, False, False, prec) <= BOUND[prec]
+
+
+@pytest.mark.parametrize("ta,tb", [(True, False), (False, True), (True, True)])
+def test_gemm_transposes(handle, ta, tb):
+    rng = np.random.default_rng(5)
+    M, N, K = 150, 90, 333
+    A = rng.standard_normal((K, M) if ta else (M, K))
+    B = rng.standard_normal((N, K) if tb else (K, N))
+    assert check_gemm(handle, A, B, ta, tb, "fp64_tc") <= BOUND["fp64_tc"]
+
+
+def test_gemm_fp64_tc_matches_dmma(handle):
+    rng = np.random.default_rng(6)
+    A = dev(rng.standard_normal((384, 512)))
+    B = dev(rng.standard_normal((512, 256)))
+    c1 = handle.gemm(A, B, prec="fp64_tc")
+    c2 = handle.gemm(A, B, prec="fp64")
+    assert float((c1 - c2).abs().max() / c2.abs().max()) < 1e-14
+
+
+@pytest.mark.parametrize("m,n", [(64, 48), (48, 64), (200, 136), (257, 65)])
+def test_one_loop_fp64_tc_matches_naive_step(handle, m, n):
+    w = W.rectangular(m, n, None, 1.0, 1e-2, seed=m * 7 + n)
+    X = H.x0_moore_penrose(w.A, H.alpha_pan_schreiber(w.s[0], w.s[-1]))
+    for _ in range(2):
+        ref = H.hyperpower_step(w.A, X, side=H.choose_side(m, n))
+        got, _ = handle.step(dev(w.A), dev(X), prec="fp64_tc")
+        got = got.cpu().numpy()
+        assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+        X = ref
+
+
+@pytest.mark.parametrize("variant", ["plain", "stabilized"])
+def test_solve_fp64_tc_rank_deficient(handle, variant):
+    w = W.rectangular(512, 384, 288, 1.0, 1e-4, seed=1)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha,
+                     variant="stabilised" if variant == "stabilized" else "plain", finish="moore_penrose")
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, variant=variant, finish="clean",
+                           prec="fp64_tc", check=True)
+    assert info["status"] == 0
+    assert rel(X.cpu().numpy(), ref) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["mixed_bf16", "fp32"])
+def test_mixed_solve_full_rank(handle, prec):
+    """Full column rank (no null block to grow): low-precision early loops are
+    corrected by the FP64-class loops that follow."""
+    w = W.rectangular(300, 200, None, 1.0, 1e-3, seed=4)
+    alpha = 1.0 / w.s[0] ** 2
+    ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, prec=prec, finish="clean", check=True)
+    assert info["status"] == 0
+    assert 1 in info["precision"] or prec == "fp32"
+    assert rel(X.cpu().numpy(), ref) <= 1e-9
+    assert rel(X.cpu().numpy(), pinv_closed_form(w)) <= 1e-9
+
+
+def test_mixed_solve_spd(handle):
+    s = W.spd(512, 1e-3, 1.0, seed=5)
+    alpha = 1.0 / s.lam.max()          # BF16 loops need alpha <= 1/lambda_max
+    X, info = handle.solve(dev(s.A), kind="outer_g", G=dev(np.eye(512)), alpha=alpha, tol=1e-12,
+                           prec="mixed_bf16")
+    inv = (s.Q / s.lam) @ s.Q.T
+    assert info["status"] == 0
+    assert rel(X.cpu().numpy(), inv) <= 1e-9
