@@ -131,8 +131,10 @@ struct Ctx {
     Coef c;
 };
 
-// Time GEMMs with CUDA events on the launch stream; harvested at sync points.
-int prof_begin(Ctx& c) {
+// Time GEMM kernels with CUDA events on the launch stream; harvested at sync
+// points.  For the tensor-core engine the events bracket the tcgen05 kernel
+// alone (not the slicing kernels before it).
+int prof_slot(Ctx& c) {
     if (!c.profile) return -1;
     auto& ev = c.h->events;
     if ((int)ev.size() < 2 * (c.ev_used + 1)) {
@@ -142,12 +144,10 @@ int prof_begin(Ctx& c) {
             ev.push_back(e);
         }
     }
-    const int slot = c.ev_used++;
-    cudaEventRecord(ev[2 * slot], c.st);
-    return slot;
+    return c.ev_used++;
 }
-void prof_end(Ctx& c, int slot) {
-    if (slot >= 0) cudaEventRecord(c.h->events[2 * slot + 1], c.st);
+cudaEvent_t prof_ev(Ctx& c, int slot, int which) {
+    return slot >= 0 ? c.h->events[2 * slot + which] : nullptr;
 }
 void prof_harvest(Ctx& c) {  // stream already synchronised
     for (int i = 0; i < c.ev_used; ++i) {
@@ -216,17 +216,18 @@ int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const d
     ++c.gemms;
     ++c.kernels;
     c.gemm_flops += 2.0 * M * N * K;
-    const int slot = prof_begin(c);
+    const int slot = prof_slot(c);
     int r;
     if (c.prec_k == 0) {
+        if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 0), c.st);
         r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st);
+        if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 1), c.st);
     } else {
         --c.kernels;  // tc_gemm counts its own launches (slicing + GEMM)
         c.tensor_flops += 2.0 * M * N * K * tc_pairs(tc_mode(c.prec_k));
         r = tc_gemm(M, N, K, A, lda, tA, B, ldb, tB, e, tc_mode(c.prec_k), c.tcws, c.tcws_bytes,
-                    c.h->derr, c.st, &c.kernels);
+                    c.h->derr, c.st, &c.kernels, prof_ev(c, slot, 0), prof_ev(c, slot, 1));
     }
-    prof_end(c, slot);
     return r;
 }
 

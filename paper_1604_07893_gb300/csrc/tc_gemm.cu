@@ -463,7 +463,7 @@ size_t tc_smem_bytes() { return STAGES * STAGE_BYTES + 1024 + 256; }
 
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb, bool transB,
             const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err, cudaStream_t st,
-            int* kernels) {
+            int* kernels, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
     const int Kp = ((K + 7) / 8) * 8;
     if (tc_workspace_bytes(M, N, K, mode) > ws_bytes) return -1;
     auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
@@ -512,7 +512,9 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
         cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
         attr = true;
     }
+    if (ev_begin) cudaEventRecord(ev_begin, st);
     tc_gemm_kernel<<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+    if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return 4 * tiles;   // pair partials: one per (tile, epilogue warp)
