@@ -3,13 +3,15 @@
 // C (M x N, FP64) = op(A) op(B) evaluated as a sum of BF16 slice products:
 //   op(A) = sum_s A_s,  op(B) = sum_t B_t,   C = sum_{s + t <= L} A_s B_t.
 // Slices are BF16 matrices.  In the exact modes (FP64-class, FP32-class) each
-// row of op(A) (column of op(B)) is cut on a power-of-two grid with 6 bits per
-// slice, so every slice entry is q * 2^e with |q| <= 64: bf16 holds it exactly,
+// row of op(A) (column of op(B)) is scaled by its power of two 2^-e (so its
+// largest entry lies in [1/2, 1)) and cut on a grid with 6 bits per slice:
+// every slice entry is q * 2^-6(s+1) with |q| <= 64, bf16 holds it exactly,
 // every product q q' 2^(e+e') is exact, and a K-chunk of <= 2048 products sums
 // to an integer multiple of one power of two below 2^23 -- the FP32 tensor-core
 // accumulation is exact.  Each (pair, chunk) accumulator is drained from TMEM
-// and added in FP64 in the epilogue, so the only rounding is the FP64 sum of
-// the slice products and the truncation of slices beyond s + t > L.
+// and added in FP64 in the epilogue, which finally applies 2^(e_i + f_j); the
+// only rounding is the FP64 sum of the slice products and the truncation of
+// slices beyond s + t > L.
 //   FP64-class: 9 slices per operand, s + t <= 8 (45 products)
 //   FP32-class: 4 slices, s + t <= 3 (10 products)
 //   BF16:       1 slice rounded to nearest (no grid), one product
@@ -58,7 +60,18 @@ struct TcParams {
     int tiles_m, tiles_n;
     Epilogue epi;
     int* err;             // device error word (0 = ok)
+    // bit patterns of the row maxima of op(A) and of the column maxima of op(B)
+    // (exact modes): the epilogue scales each entry by 2^(e_i + f_j)
+    const unsigned long long* rmax;
+    const unsigned long long* cmax;
 };
+
+__device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i) {
+    int e = 0;
+    const double v = __longlong_as_double((long long)mx[i]);
+    if (v > 0.0) frexp(v, &e);
+    return e;
+}
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -281,6 +294,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             // fused FP64 epilogue for this row of the tile
             const int row = m0 + row_in_tile;
             double sd = 0.0, sx = 0.0;
+            if (row < P.M && P.rmax) {   // undo the row/column normalisation of the slices
+                const int ei = grid_exponent(P.rmax, row);
+#pragma unroll
+                for (int j = 0; j < BN; ++j) {
+                    const int col = min(n0 + j, P.N - 1);
+                    acc[j] = ldexp(acc[j], ei + grid_exponent(P.cmax, col));
+                }
+            }
             if (row < P.M) {
                 const double* s1 = E.s1 ? E.s1 + (size_t)row * E.ld1 : nullptr;
                 const double* s2 = E.s2 ? E.s2 + (size_t)row * E.ld2 : nullptr;
@@ -328,34 +349,43 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 }
 
 // ------------------------------------------------------------------ slicing
-// Rows of op(X) (op(X)[i][k] = trans ? X[k][i] : X[i][k]); one exponent per row:
-// e_i with 2^e_i > max_k |op(X)[i][k]|.
-__global__ void row_exponent_kernel(int rows, int K, const double* X, int ld, int trans, int* e) {
-    if (!trans) {
-        const int warps = blockDim.x >> 5;
-        const int i = blockIdx.x * warps + (threadIdx.x >> 5);
-        const int lane = threadIdx.x & 31;
-        if (i >= rows) return;
-        double mx = 0.0;
-        for (int k = lane; k < K; k += 32) mx = fmax(mx, fabs(X[(size_t)i * ld + k]));
-        for (int off = 16; off; off >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-        if (lane == 0) { int ex = 0; if (mx > 0) frexp(mx, &ex); e[i] = ex; }
-    } else {
-        const int i = blockIdx.x * blockDim.x + threadIdx.x;
-        if (i >= rows) return;
-        double mx = 0.0;
-        for (int k = 0; k < K; ++k) mx = fmax(mx, fabs(X[(size_t)k * ld + i]));
-        int ex = 0;
-        if (mx > 0) frexp(mx, &ex);
-        e[i] = ex;
+// Rows of op(X) (op(X)[i][k] = trans ? X[k][i] : X[i][k]): mx[i] receives the
+// bit pattern of max_k |op(X)[i][k]| (non-negative doubles order like their
+// bits, so integer max is the floating max).  mx must be zeroed first.
+__global__ void row_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx) {
+    const int warps = blockDim.x >> 5;
+    const int i = blockIdx.x * warps + (threadIdx.x >> 5);
+    const int lane = threadIdx.x & 31;
+    if (i >= rows) return;
+    double m = 0.0;
+    for (int k = lane; k < K; k += 32) m = fmax(m, fabs(X[(size_t)i * ld + k]));
+    for (int off = 16; off; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) mx[i] = (unsigned long long)__double_as_longlong(m);
+}
+// Transposed view: X is K x rows; a (32 columns) x (256 rows of X) patch per
+// block, coalesced along the columns, combined with atomicMax.
+__global__ void col_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx) {
+    __shared__ double sh[8][33];
+    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
+    const int i = blockIdx.x * 32 + tx;
+    const int k0 = blockIdx.y * 256;
+    const int k1 = min(K, k0 + 256);
+    double m = 0.0;
+    if (i < rows)
+        for (int k = k0 + ty; k < k1; k += 8) m = fmax(m, fabs(X[(size_t)k * ld + i]));
+    sh[ty][tx] = m;
+    __syncthreads();
+    if (ty == 0 && i < rows) {
+        for (int j = 1; j < 8; ++j) m = fmax(m, sh[j][tx]);
+        atomicMax(&mx[i], (unsigned long long)__double_as_longlong(m));
     }
 }
 
 // out[s][i][k] (bf16, row length Kp) for 32 x 32 tiles of op(X); zero beyond K.
 // exact = 1: slices on the per-row grid 2^(e_i - 6(s+1)); exact = 0: one
 // round-to-nearest slice.
-__global__ void slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans, const int* e,
-                             int S, int exact, __nv_bfloat16* out) {
+__global__ void slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans,
+                             const unsigned long long* mx, int S, int exact, __nv_bfloat16* out) {
     __shared__ double t[32][33];
     const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
@@ -382,13 +412,35 @@ __global__ void slice_kernel(int rows, int K, int Kp, const double* X, int ld, i
             for (int s = 1; s < S; ++s) out[s * plane + (size_t)i * Kp + k] = __double2bfloat16(0.0);
             continue;
         }
-        const int ei = e[i];
+        int ei = 0;   // 2^ei > max |row i| (frexp: max = f 2^ei, 0.5 <= f < 1)
+        const double rmax = __longlong_as_double((long long)mx[i]);
+        if (rmax > 0.0) frexp(rmax, &ei);
+        // Integer digit extraction (GB300's FP64 pipe is narrow): x = m 2^E with
+        // a 53-bit integer m; F = round(x / 2^(ei - 6S)) is a signed fixed-point
+        // integer with |F| < 2^(6S); slice s is the balanced 6-bit digit
+        // q_s = round(F / 2^(6(S-1-s))) taken from the top, F -= q_s 2^(...).
+        const long long bits = __double_as_longlong(x);
+        const int bexp = (int)((bits >> 52) & 0x7FF);
+        if (bexp == 0x7FF) {   // NaN/Inf: poison every slice so the product reports it
+            for (int s = 0; s < S; ++s) out[s * plane + (size_t)i * Kp + k] = __float2bfloat16_rn(NAN);
+            continue;
+        }
+        long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (bexp ? (1LL << 52) : 0LL);
+        const int E = (bexp ? bexp : 1) - 1075;             // x = mant * 2^E
+        const int shift = E - (ei - 6 * S);                 // F = mant * 2^shift
+        long long F;
+        if (shift >= 0) F = mant << shift;                  // < 2^(6S) <= 2^54 since |x| < 2^ei
+        else if (shift > -62) F = (mant + (1LL << (-shift - 1))) >> (-shift);
+        else F = 0;
+        if (bits < 0) F = -F;
         for (int s = 0; s < S; ++s) {
-            const int sh = ei - 6 * (s + 1);
-            const double q = rint(ldexp(x, -sh));     // |q| <= 64
-            const double piece = ldexp(q, sh);
-            out[s * plane + (size_t)i * Kp + k] = __float2bfloat16_rn((float)piece);
-            x -= piece;
+            const int w = 6 * (S - 1 - s);
+            const long long q = w ? ((F + (1LL << (w - 1))) >> w) : F;   // |q| <= 64
+            F -= q << w;
+            // row-normalised: the slice holds q 2^(-6(s+1)); 2^ei is applied in the
+            // GEMM epilogue, so no product leaves the FP32 range whatever the row scale
+            const float piece = ldexpf((float)q, w - 6 * S);                  // exact: q has <= 7 bits
+            out[s * plane + (size_t)i * Kp + k] = __float2bfloat16_rn(piece);
         }
     }
 }
@@ -456,7 +508,7 @@ int tc_pairs(const TcMode& m) {
 size_t tc_workspace_bytes(int M, int N, int K, const TcMode& m) {
     const size_t Kp = (size_t)((K + 7) / 8) * 8;
     auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
-    return al((size_t)m.S * M * Kp * 2) + al((size_t)m.S * N * Kp * 2) + al(sizeof(int) * (M + N)) + 1024;
+    return al((size_t)m.S * M * Kp * 2) + al((size_t)m.S * N * Kp * 2) + al(8 * (size_t)(M + N)) + 1024;
 }
 
 size_t tc_smem_bytes() { return STAGES * STAGE_BYTES + 1024 + 256; }
@@ -472,16 +524,18 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     p += al((size_t)mode.S * M * Kp * 2);
     __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(p);
     p += al((size_t)mode.S * N * Kp * 2);
-    int* ea = reinterpret_cast<int*>(p);
-    int* eb = ea + M;
+    unsigned long long* ea = reinterpret_cast<unsigned long long*>(p);
+    unsigned long long* eb = ea + M;
 
     // slices of op(A) (rows i, length K) and of op(B)^T (rows j, length K)
     if (mode.exact) {
-        if (!transA) row_exponent_kernel<<<(M + 7) / 8, 256, 0, st>>>(M, K, A, lda, 0, ea);
-        else         row_exponent_kernel<<<(M + 127) / 128, 128, 0, st>>>(M, K, A, lda, 1, ea);
-        // op(B)^T row j = column j of op(B): B stored K x N (trans=1 view) unless transB
-        if (transB) row_exponent_kernel<<<(N + 7) / 8, 256, 0, st>>>(N, K, B, ldb, 0, eb);
-        else        row_exponent_kernel<<<(N + 127) / 128, 128, 0, st>>>(N, K, B, ldb, 1, eb);
+        // per-row maxima of op(A) and of op(B)^T (= columns of op(B))
+        if (cudaMemsetAsync(ea, 0, 8 * (size_t)(M + N), st) != cudaSuccess) return -1;
+        dim3 blk(32, 8);
+        if (!transA) row_absmax_kernel<<<(M + 7) / 8, 256, 0, st>>>(M, K, A, lda, ea);
+        else col_absmax_kernel<<<dim3((M + 31) / 32, (K + 255) / 256), blk, 0, st>>>(M, K, A, lda, ea);
+        if (transB) row_absmax_kernel<<<(N + 7) / 8, 256, 0, st>>>(N, K, B, ldb, eb);
+        else col_absmax_kernel<<<dim3((N + 31) / 32, (K + 255) / 256), blk, 0, st>>>(N, K, B, ldb, eb);
         *kernels += 2;
     }
     {
@@ -505,6 +559,8 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.tiles_n = (N + BN - 1) / BN;
     P.epi = epi;
     P.err = err;
+    P.rmax = mode.exact ? ea : nullptr;
+    P.cmax = mode.exact ? eb : nullptr;
     const int tiles = P.tiles_m * P.tiles_n;
     const int grid = tiles < num_sms() ? tiles : num_sms();
     static bool attr = false;
