@@ -173,7 +173,7 @@ size_t workspace_bytes(int m, int n, bool drazin, bool host, bool check, int pre
     if (host) b += 2 * align_up(sizeof(double) * n * (size_t)m);
     if (check) b += 2 * align_up(sizeof(double) * big * big);
     const size_t tiles = (size_t)((big + 63) / 64) * ((big + 63) / 64);
-    b += align_up(sizeof(double) * 2 * 4 * tiles);   // pair partials (4 per tensor-core tile)
+    b += align_up(sizeof(double) * 2 * 8 * tiles);   // pair partials (8 per 128 x 128 tensor-core tile)
     b += align_up(sizeof(double) * 2 * 2 * 256);
     b += align_up(tc_bytes(m, n, prec));
     return b;
@@ -205,7 +205,7 @@ void carve(Ctx& c, bool drazin, bool host, bool check, int prec) {
     c.big[0] = check ? take(sizeof(double) * big * big) : nullptr;
     c.big[1] = check ? take(sizeof(double) * big * big) : nullptr;
     const size_t tiles = (size_t)((big + 63) / 64) * ((big + 63) / 64);
-    c.partials = take(sizeof(double) * 2 * 4 * tiles);
+    c.partials = take(sizeof(double) * 2 * 8 * tiles);
     c.red = take(sizeof(double) * 2 * 2 * 256);
     c.tcws_bytes = tc_bytes(c.m, c.n, prec);
     c.tcws = c.tcws_bytes ? (void*)take(c.tcws_bytes) : nullptr;

@@ -42,14 +42,18 @@ namespace pinv {
 namespace {
 
 constexpr int BM = 128;
-constexpr int BN = 64;
+constexpr int BN = 128;
 constexpr int BK = 64;          // 64 bf16 = one 128-byte swizzle row
-constexpr int STAGES = 8;
-constexpr int THREADS = 192;
+constexpr int STAGES = 6;
+constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, each owning BN/2 columns
+constexpr int EPI_COLS = BN / 2;
+constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr int A_TILE_BYTES = BM * BK * 2;   // 16 KiB
-constexpr int B_TILE_BYTES = BN * BK * 2;   //  8 KiB
+constexpr int B_TILE_BYTES = BN * BK * 2;   // 16 KiB
 constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
-constexpr int TMEM_COLS = 2 * BN;           // two accumulators
+// TMEM columns: two FP32 MMA accumulators [0, 2BN) and the FP64 running sums of
+// the tile (two 32-bit columns per double) [2BN, 4BN).
+constexpr int TMEM_COLS = 4 * BN;
 constexpr unsigned WAIT_LIMIT = 1u << 22;   // polls before a wait gives up (about a second)
 
 struct TcParams {
@@ -57,6 +61,7 @@ struct TcParams {
     int npairs;
     int pair_s[64], pair_t[64];
     int chunk;            // K elements per exact accumulation
+    int exact;            // 1: slices on power-of-two grids (integer-valued products)
     int tiles_m, tiles_n;
     Epilogue epi;
     int* err;             // device error word (0 = ok)
@@ -156,6 +161,30 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld32_raw(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st32_raw(uint32_t taddr, const uint32_t* r) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+        "%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,%32};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]),
+        "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]), "r"(r[16]),
+        "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]), "r"(r[24]),
+        "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
 __device__ __forceinline__ void record_error(int* err, int code) {
     if (err) atomicCAS(err, 0, code);
 }
@@ -180,7 +209,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
-        for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 128); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 32 * EPI_WARPS); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -260,56 +289,95 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
         }
     } else {
-        // ---------------------------------------------------------- epilogue (warps 2..5)
+        // ---------------------------------------------------------- epilogue (warps 2..9)
+        // Drained accumulators of one slice diagonal d = s + t share the unit
+        // 2^-6(d+2) (the slices are integer digits times powers of two), so in
+        // the exact modes they are summed exactly as int32 (at most 18 drains of
+        // |value| <= 2^23 units: < 2^28).  Each diagonal is then added once, in
+        // FP64, to the running sums kept in TMEM columns [2BN, 4BN).
         const int lg = warp & 3;                 // TMEM lane group of this warp
+        const int half = (warp - 2) >> 2;        // which BN/2 columns of the tile
+        const int ew = warp - 2;                 // epilogue warp index
         const int row_in_tile = lg * 32 + lane;
+        const uint32_t lane_base = tmem + ((uint32_t)(lg * 32) << 16);
+        const uint32_t acc64 = lane_base + 2 * BN + 2 * half * EPI_COLS;
         int buf = 0;
         uint32_t accphase[2] = {0, 0};
         const Epilogue& E = P.epi;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const int m0 = (tile % P.tiles_m) * BM, n0 = (tile / P.tiles_m) * BN;
-            double acc[BN];
-#pragma unroll
-            for (int j = 0; j < BN; ++j) acc[j] = 0.0;
+            int iacc[EPI_COLS];
+            int dcur = -1;
+            bool have64 = false;
             bool ok = true;
             for (int u = 0; u < units; ++u) {
+                const int pr = u / kchunks;
+                const int d = P.pair_s[pr] + P.pair_t[pr];
+                if (d != dcur) {
+#pragma unroll
+                    for (int j = 0; j < EPI_COLS; ++j) iacc[j] = 0;
+                    dcur = d;
+                }
                 if (*abort_flag || !mbar_wait(&accf[buf], accphase[buf])) {
                     record_error(P.err, 4); *abort_flag = 1; ok = false; break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = tmem + ((uint32_t)(lg * 32) << 16) + buf * BN;
+                const uint32_t taddr = lane_base + buf * BN + half * EPI_COLS;
+                const float unit = P.exact ? ldexpf(1.0f, 6 * (d + 2)) : 1.0f;
 #pragma unroll
-                for (int c = 0; c < BN; c += 32) {
-                    float v[32];
-                    tmem_ld32(taddr + c, v);
+                for (int c = 0; c < EPI_COLS; c += 32) {
+                    uint32_t r[32];
+                    tmem_ld32_raw(taddr + c, r);
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) acc[c + j] += (double)v[j];
+                    for (int j = 0; j < 32; ++j) {
+                        if (P.exact) iacc[c + j] += __float2int_rn(__uint_as_float(r[j]) * unit);
+                        else iacc[c + j] = (int)r[j];   // one drain only: keep the FP32 bits
+                    }
                 }
                 tc_fence_before();
                 mbar_arrive(&acce[buf]);
                 accphase[buf] ^= 1;
                 buf ^= 1;
-            }
-            if (!ok) break;
-            // fused FP64 epilogue for this row of the tile
-            const int row = m0 + row_in_tile;
-            double sd = 0.0, sx = 0.0;
-            if (row < P.M && P.rmax) {   // undo the row/column normalisation of the slices
-                const int ei = grid_exponent(P.rmax, row);
+                const bool diag_done =
+                    (u + 1 == units) || (P.pair_s[(u + 1) / kchunks] + P.pair_t[(u + 1) / kchunks] != d);
+                if (diag_done) {   // add this diagonal to the FP64 sums in TMEM
+                    const double sc = P.exact ? ldexp(1.0, -6 * (d + 2)) : 1.0;
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const int col = min(n0 + j, P.N - 1);
-                    acc[j] = ldexp(acc[j], ei + grid_exponent(P.cmax, col));
+                    for (int c = 0; c < EPI_COLS; c += 16) {
+                        uint32_t r[32];
+                        if (have64) tmem_ld32_raw(acc64 + 2 * c, r);
+#pragma unroll
+                        for (int j = 0; j < 16; ++j) {
+                            const double v = P.exact ? (double)iacc[c + j] * sc
+                                                     : (double)__int_as_float(iacc[c + j]);
+                            const double o = have64 ? __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]) : 0.0;
+                            const double nw = o + v;
+                            r[2 * j] = (uint32_t)__double2loint(nw);
+                            r[2 * j + 1] = (uint32_t)__double2hiint(nw);
+                        }
+                        tmem_st32_raw(acc64 + 2 * c, r);
+                    }
+                    have64 = true;
                 }
             }
-            if (row < P.M) {
-                const double* s1 = E.s1 ? E.s1 + (size_t)row * E.ld1 : nullptr;
-                const double* s2 = E.s2 ? E.s2 + (size_t)row * E.ld2 : nullptr;
+            if (!ok) break;
+            // fused FP64 epilogue for this row of the tile, 16 columns at a time
+            const int row = m0 + row_in_tile;
+            const int ei = (P.rmax && row < P.M) ? grid_exponent(P.rmax, row) : 0;
+            double sd = 0.0, sx = 0.0;
+            const double* s1 = (E.s1 && row < P.M) ? E.s1 + (size_t)row * E.ld1 : nullptr;
+            const double* s2 = (E.s2 && row < P.M) ? E.s2 + (size_t)row * E.ld2 : nullptr;
+#pragma unroll 1
+            for (int c = 0; c < EPI_COLS; c += 16) {
+                uint32_t r[32];
+                tmem_ld32_raw(acc64 + 2 * c, r);
+                if (row >= P.M) continue;
 #pragma unroll
-                for (int j = 0; j < BN; ++j) {
-                    const int col = n0 + j;
+                for (int j = 0; j < 16; ++j) {
+                    const int col = n0 + half * EPI_COLS + c + j;
                     if (col < P.N) {
-                        const double a = acc[j];
+                        double a = __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]);
+                        if (P.rmax) a = ldexp(a, ei + grid_exponent(P.cmax, col));
                         const double v1 = s1 ? s1[col] : 0.0;
                         const double v2 = s2 ? s2[col] : 0.0;
                         const double id = (row == col) ? 1.0 : 0.0;
@@ -332,8 +400,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     sx += __shfl_xor_sync(0xffffffffu, sx, off);
                 }
                 if (lane == 0) {
-                    E.partials[2 * (4 * tile + lg)] = sd;
-                    E.partials[2 * (4 * tile + lg) + 1] = sx;
+                    E.partials[2 * (EPI_WARPS * tile + ew)] = sd;
+                    E.partials[2 * (EPI_WARPS * tile + ew) + 1] = sx;
                 }
             }
         }
@@ -550,10 +618,13 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
 
     TcParams P;
     P.M = M; P.N = N; P.K = K;
-    P.npairs = 0;
-    for (int s = 0; s < mode.S; ++s)
-        for (int t = 0; t < mode.S; ++t)
-            if (s + t <= mode.L) { P.pair_s[P.npairs] = s; P.pair_t[P.npairs] = t; ++P.npairs; }
+    P.npairs = 0;   // ordered by diagonal s + t (the epilogue sums a diagonal in int32)
+    for (int d = 0; d <= mode.L; ++d)
+        for (int s = 0; s < mode.S; ++s) {
+            const int t = d - s;
+            if (t >= 0 && t < mode.S) { P.pair_s[P.npairs] = s; P.pair_t[P.npairs] = t; ++P.npairs; }
+        }
+    P.exact = mode.exact;
     P.chunk = mode.exact ? 2048 : ((K + BK - 1) / BK) * BK;
     P.tiles_m = (M + BM - 1) / BM;
     P.tiles_n = (N + BN - 1) / BN;
@@ -573,7 +644,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
-    return 4 * tiles;   // pair partials: one per (tile, epilogue warp)
+    return EPI_WARPS * tiles;   // pair partials: one per (tile, epilogue warp)
 }
 
 }  // namespace pinv

@@ -25,7 +25,7 @@ size_t tc_smem_bytes();
 // ev_begin/ev_end (optional) are recorded around the tensor-core kernel alone.
 // `err` is a device int that records a timed-out wait (0 = ok).  Adds the
 // number of kernels launched to *kernels.  Returns the count of pair partials
-// written when epi.partials is set (4 per 128 x 64 output tile) or -1.
+// written when epi.partials is set (8 per 128 x 128 output tile) or -1.
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb,
             bool transB, const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err,
             cudaStream_t st, int* kernels, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
