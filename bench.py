@@ -47,7 +47,12 @@ WORKLOAD = "moore_penrose_rank_deficient_4096x3072_r2304"
 # dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
 # kernel from the committed ncu summary under profiles/ (None until captured
 # for the current kernel).
-TRAFFIC_BYTES = {"fp64": None, "fp64_tc": None, "fp32": None, "mixed_bf16": None}
+TRAFFIC_BYTES = {"fp64": None, "fp32": None, "mixed_bf16": None,
+                 # profiles/tc_gemm_kernel_fp64class_3072x3072x4096.md: 5.449 GB read + 75.8 MB
+                 # written for a 3072x3072x4096 launch; scaled to this workload's mean launch
+                 # by the FP64-equivalent flops it processes (see TRAFFIC_SCALE below)
+                 "fp64_tc": 5.449e9 + 75.8e6}
+TRAFFIC_REF_FLOPS = 2.0 * 3072 * 3072 * 4096   # the captured launch's 2MNK
 
 
 def env_rank():
@@ -290,6 +295,8 @@ def run_ours(args):
     achieved = work / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
     fp64_equiv = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
     traffic = TRAFFIC_BYTES.get(args.prec)
+    if traffic is not None and gemm_launches:
+        traffic = traffic * (gemm_flops / gemm_launches) / TRAFFIC_REF_FLOPS   # per mean launch
     value = world * args.steps / (total_ms * 1e-3)
     sorted_ms = sorted(per_step)
     p50 = statistics.median(per_step)
