@@ -196,6 +196,8 @@ class Handle:
         import torch
         if Xs is None:
             Xs = [torch.empty((A.shape[1], A.shape[0]), dtype=torch.float64, device=A.device) for A in As]
+        if not As:
+            return [], []
         descs = (Desc * len(As))(*[self.make_desc(A, X, **kw) for A, X in zip(As, Xs)])
         infos = (Info * len(As))()
         rc = self._lib.pinv_solve_batched(self._h, len(As), descs, C.c_void_p(_stream_ptr(stream)), infos)

@@ -40,6 +40,8 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
 
 __global__ void reduce_pairs_kernel(const double* p, int count, double* out) {
     __shared__ double sh[32];
+    p += 2LL * count * blockIdx.x;   // instance blockIdx.x of a batch
+    out += 2 * blockIdx.x;
     double a = 0.0, b = 0.0;
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
         a += p[2 * i];
@@ -140,10 +142,98 @@ __global__ void diff_norms_kernel(int rows, int cols, const double* P, int ldp, 
     if (threadIdx.x == 0) part[2 * blockIdx.x] = a, part[2 * blockIdx.x + 1] = b;
 }
 
+__global__ void gather_pad_kernel(const InstanceRef* table, int rows_pad, int cols_pad, double* slab0,
+                                  long long stride) {
+    const InstanceRef r = table[blockIdx.z];
+    double* dst = slab0 + (long long)blockIdx.z * stride;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols_pad; j += gridDim.x * blockDim.x) {
+        if (i < rows_pad)
+            dst[(size_t)i * cols_pad + j] = (i < r.rows && j < r.cols) ? r.src[(size_t)i * r.ld + j] : 0.0;
+    }
+}
+
+__global__ void scatter_kernel(const InstanceRef* table, const int* mask, int rows_pad, int cols_pad,
+                               double* slab0, int ld_slab, long long stride, int to_caller) {
+    if (mask && !mask[blockIdx.z]) return;
+    const InstanceRef r = table[blockIdx.z];
+    double* slab = slab0 + (long long)blockIdx.z * stride;
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= rows_pad) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols_pad; j += gridDim.x * blockDim.x) {
+        const bool inside = i < r.rows && j < r.cols;
+        if (to_caller) {
+            if (inside) r.dst[(size_t)i * r.ld + j] = slab[(size_t)i * ld_slab + j];
+        } else {
+            slab[(size_t)i * ld_slab + j] = inside ? r.dst[(size_t)i * r.ld + j] : 0.0;
+        }
+    }
+}
+
+__global__ void transpose_scale_batched_kernel(int m, int n, const double* A0, int lda, const double* alpha,
+                                               double* Y0, int ldy, long long stride) {
+    __shared__ double t[32][33];
+    const double* A = A0 + (long long)blockIdx.z * stride;
+    double* Y = Y0 + (long long)blockIdx.z * stride;
+    const double a = alpha[blockIdx.z];
+    const int bx = blockIdx.x * 32, by = blockIdx.y * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int i = by + r, j = bx + threadIdx.x;
+        if (i < m && j < n) t[r][threadIdx.x] = A[(size_t)i * lda + j];
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        int j = bx + r, i = by + threadIdx.x;
+        if (i < m && j < n) Y[(size_t)j * ldy + i] = a * t[threadIdx.x][r];
+    }
+}
+
+__global__ void scale_copy_batched_kernel(int rows, int cols, const double* X0, int ldx, const double* alpha,
+                                          double* Y0, int ldy, long long stride) {
+    const double* X = X0 + (long long)blockIdx.z * stride;
+    double* Y = Y0 + (long long)blockIdx.z * stride;
+    const double a = alpha[blockIdx.z];
+    const int i = blockIdx.y * blockDim.y + threadIdx.y;
+    if (i >= rows) return;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < cols; j += gridDim.x * blockDim.x)
+        Y[(size_t)i * ldy + j] = a * X[(size_t)i * ldx + j];
+}
+
 }  // namespace
 
-void reduce_pairs(const double* partials, int count, double* out, cudaStream_t st) {
-    reduce_pairs_kernel<<<1, RED_THREADS, 0, st>>>(partials, count, out);
+void gather_pad(const InstanceRef* table, int batch, int rows_pad, int cols_pad, double* slab0,
+                long long stride, cudaStream_t st) {
+    dim3 blk(32, 8), grid((cols_pad + 31) / 32 < 8 ? (cols_pad + 31) / 32 : 8, (rows_pad + 7) / 8, batch);
+    gather_pad_kernel<<<grid, blk, 0, st>>>(table, rows_pad, cols_pad, slab0, stride);
+}
+
+void scatter_out(const InstanceRef* table, const int* mask, int batch, int rows_pad, int cols_pad,
+                 const double* slab0, int ld_slab, long long stride, cudaStream_t st) {
+    dim3 blk(32, 8), grid((cols_pad + 31) / 32 < 8 ? (cols_pad + 31) / 32 : 8, (rows_pad + 7) / 8, batch);
+    scatter_kernel<<<grid, blk, 0, st>>>(table, mask, rows_pad, cols_pad, const_cast<double*>(slab0), ld_slab,
+                                         stride, 1);
+}
+
+void scatter_in(const InstanceRef* table, const int* mask, int batch, int rows_pad, int cols_pad,
+                double* slab0, int ld_slab, long long stride, cudaStream_t st) {
+    dim3 blk(32, 8), grid((cols_pad + 31) / 32 < 8 ? (cols_pad + 31) / 32 : 8, (rows_pad + 7) / 8, batch);
+    scatter_kernel<<<grid, blk, 0, st>>>(table, mask, rows_pad, cols_pad, slab0, ld_slab, stride, 0);
+}
+
+void transpose_scale_batched(int m, int n, const double* A0, int lda, const double* alpha, double* Y0,
+                             int ldy, long long stride, int batch, cudaStream_t st) {
+    dim3 grid((n + 31) / 32, (m + 31) / 32, batch), block(32, 8);
+    transpose_scale_batched_kernel<<<grid, block, 0, st>>>(m, n, A0, lda, alpha, Y0, ldy, stride);
+}
+
+void scale_copy_batched(int rows, int cols, const double* X0, int ldx, const double* alpha, double* Y0,
+                        int ldy, long long stride, int batch, cudaStream_t st) {
+    dim3 blk(32, 8), grid((cols + 31) / 32 < 8 ? (cols + 31) / 32 : 8, (rows + 7) / 8, batch);
+    scale_copy_batched_kernel<<<grid, blk, 0, st>>>(rows, cols, X0, ldx, alpha, Y0, ldy, stride);
+}
+
+void reduce_pairs(const double* partials, int count, double* out, cudaStream_t st, int batch) {
+    reduce_pairs_kernel<<<batch, RED_THREADS, 0, st>>>(partials, count, out);
 }
 
 void transpose_scale(int m, int n, const double* A, int lda, double alpha, double* Y, int ldy,

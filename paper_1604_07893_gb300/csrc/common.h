@@ -37,13 +37,17 @@ inline Epilogue epi_none() {
 
 // C (M x N) = op(A) (M x K) * op(B) (K x N), all row-major FP64.
 // transA: A is stored K x M (element (i,k) at A[k*lda + i]); likewise transB.
-// Returns the number of CTAs launched (the partials count) or -1 on a launch error.
+// batch > 1: instance b uses every matrix (operands, side inputs, outputs) at
+// +b*stride elements and writes its pair partials after those of instance b-1.
+// Returns the pair partials per instance (the CTA count) or -1 on a launch error.
 int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
-             const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st);
+             const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st,
+             int batch = 1, long long stride = 0);
 int gemm_f64_ctas(int M, int N);
 
-// Deterministic sum of `count` (pair) partials into out[0..1] (device).
-void reduce_pairs(const double* partials, int count, double* out, cudaStream_t st);
+// Deterministic sum of `count` (pair) partials into out[0..1] (device); with
+// batch > 1, instance b sums partials[2*count*b ...] into out[2b], out[2b+1].
+void reduce_pairs(const double* partials, int count, double* out, cudaStream_t st, int batch = 1);
 
 // Y (n x m, ldy) = alpha * A^T, A m x n (lda).
 void transpose_scale(int m, int n, const double* A, int lda, double alpha, double* Y, int ldy,
@@ -61,5 +65,30 @@ void trace_of_product(int n, const double* P, int ldp, const double* Q, int ldq,
 void diff_norms(int rows, int cols, const double* P, int ldp, const double* Q, int ldq,
                 bool transQ, double* out, double* scratch, cudaStream_t st);
 int diff_norms_scratch_pairs();
+
+// One instance of a batch: a caller matrix (rows x cols, leading dimension ld).
+struct InstanceRef {
+    const double* src;
+    double* dst;
+    int rows, cols, ld;
+    int pad;
+};
+// slab_b (rows_pad x cols_pad, ld cols_pad, at slab0 + b*stride) = the
+// instance's src, zero outside it; `table` is device memory.
+void gather_pad(const InstanceRef* table, int batch, int rows_pad, int cols_pad, double* slab0,
+                long long stride, cudaStream_t st);
+// dst_b (rows_b x cols_b, ld_b) = the top-left block of slab_b (ld ld_slab) for
+// every b with mask[b] != 0 (mask may be null: all); `table` is device memory.
+void scatter_out(const InstanceRef* table, const int* mask, int batch, int rows_pad, int cols_pad,
+                 const double* slab0, int ld_slab, long long stride, cudaStream_t st);
+// slab_b = dst_b (the reverse of scatter_out, zero outside), for mask[b] != 0.
+void scatter_in(const InstanceRef* table, const int* mask, int batch, int rows_pad, int cols_pad,
+                double* slab0, int ld_slab, long long stride, cudaStream_t st);
+// Y_b (n x m) = alpha[b] * A_b^T for every instance (alpha: device array).
+void transpose_scale_batched(int m, int n, const double* A0, int lda, const double* alpha, double* Y0,
+                             int ldy, long long stride, int batch, cudaStream_t st);
+// Y_b = alpha[b] * X_b.
+void scale_copy_batched(int rows, int cols, const double* X0, int ldx, const double* alpha, double* Y0,
+                        int ldy, long long stride, int batch, cudaStream_t st);
 
 }  // namespace pinv

@@ -32,6 +32,7 @@ struct GemmArgs {
     int M, N, K;
     const double* A; int lda; int transA;
     const double* B; int ldb; int transB;
+    long long stride;   // batch: instance b reads/writes every matrix at +b*stride
 };
 
 __device__ __forceinline__ double loadA(const GemmArgs& g, int i, int k) {
@@ -52,6 +53,15 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp >> 1, wn = warp & 1;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (blockIdx.z) {   // instance blockIdx.z of a batch: shift every matrix
+        const long long off = (long long)blockIdx.z * g.stride;
+        g.A += off; g.B += off;
+        if (epi.s1) epi.s1 += off;
+        if (epi.s2) epi.s2 += off;
+        for (int o = 0; o < 3; ++o)
+            if (epi.o[o].out) epi.o[o].out += off;
+        if (epi.partials) epi.partials += 2LL * blockIdx.z * gridDim.x * gridDim.y;
+    }
 
     // Register staging of one K-slab: 1024 A elements and 1024 B elements, 8 each.
     double ra[8], rb[8];
@@ -166,12 +176,13 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
 int gemm_f64_ctas(int M, int N) { return ((N + BN - 1) / BN) * ((M + BM - 1) / BM); }
 
 int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
-             const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st) {
-    GemmArgs g{M, N, K, A, lda, transA ? 1 : 0, B, ldb, transB ? 1 : 0};
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM);
+             const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st,
+             int batch, long long stride) {
+    GemmArgs g{M, N, K, A, lda, transA ? 1 : 0, B, ldb, transB ? 1 : 0, stride};
+    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     gemm_f64_kernel<<<grid, THREADS, 0, st>>>(g, epi);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
-    return grid.x * grid.y;
+    return grid.x * grid.y;   // pair partials per instance
 }
 
 }  // namespace pinv

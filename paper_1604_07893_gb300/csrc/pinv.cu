@@ -22,6 +22,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -119,6 +120,8 @@ struct Ctx {
     double* partials; // pair partials
     double* red;      // reduction scratch (2 * 256 pairs)
     int prec_k = 0;         // product precision of the GEMMs being issued (0 = DMMA FP64)
+    int batch = 1;          // instances processed together (all buffers at +b*stride)
+    long long stride = 0;
     void* tcws = nullptr;   // slice workspace of the tensor-core engine
     size_t tcws_bytes = 0;
     int gemms = 0;
@@ -215,18 +218,19 @@ int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const d
          bool tB, const Epilogue& e) {
     ++c.gemms;
     ++c.kernels;
-    c.gemm_flops += 2.0 * M * N * K;
+    c.gemm_flops += 2.0 * M * N * K * c.batch;
     const int slot = prof_slot(c);
     int r;
     if (c.prec_k == 0) {
         if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 0), c.st);
-        r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st);
+        r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st, c.batch, c.stride);
         if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 1), c.st);
     } else {
         --c.kernels;  // tc_gemm counts its own launches (slicing + GEMM)
-        c.tensor_flops += 2.0 * M * N * K * tc_pairs(tc_mode(c.prec_k));
+        c.tensor_flops += 2.0 * M * N * K * tc_pairs(tc_mode(c.prec_k)) * c.batch;
         r = tc_gemm(M, N, K, A, lda, tA, B, ldb, tB, e, tc_mode(c.prec_k), c.tcws, c.tcws_bytes,
-                    c.h->derr, c.st, &c.kernels, prof_ev(c, slot, 0), prof_ev(c, slot, 1));
+                    c.h->derr, c.st, &c.kernels, prof_ev(c, slot, 0), prof_ev(c, slot, 1), c.batch,
+                    c.stride);
     }
     return r;
 }
@@ -618,6 +622,298 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
     return info->status = status;
 }
 
+
+// ------------------------------------------------------------------ batched groups
+// A group is a bucket of independent problems padded to one shape (zero rows
+// and columns: the padded block of R is exactly I and the padded rows of X stay
+// exactly 0, so every instance's iterate is its own problem's iterate).  Each
+// instance owns one fixed-size slab of the workspace (A, three iterates, the
+// seven squares, the two large squares), so every batched launch addresses
+// instance b at +b*stride.  The group runs the chain of Eq. PM for all its
+// instances in lockstep on its own stream; the stop rule is applied per
+// instance on the host and an instance's kept iterate is copied to its caller
+// buffer the moment it stops.
+struct Group {
+    pinv_handle* h = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<pinv_desc> d;
+    std::vector<pinv_info> info;
+    int batch = 0, M = 0, N = 0, prec = 0, fp64_class = 0, level = 0, prev_prec = -1;
+    bool left = false, stabilise = false, finish = false;
+    int k = 0, cur = 0, max_iter = 100;
+    char* mem = nullptr;
+    double* pinned = nullptr;      // norms [2 batch] then masks
+    Ctx c{};
+    InstanceRef *tabA = nullptr, *tabX = nullptr, *tabG = nullptr;
+    int* dmask = nullptr;          // 2 x batch: copy from X[cur], copy from X[cur^1]
+    double* dalpha = nullptr;
+    double* dnorms = nullptr;
+    cudaEvent_t ev = nullptr;
+    std::vector<double> prev, prev2;
+    std::vector<char> done;
+    int parts = 0;
+    int err = PINV_OK;
+
+    ~Group() { release(); }
+    void release() {
+        if (st) cudaStreamSynchronize(st);
+        if (mem) cudaFree(mem);
+        if (pinned) cudaFreeHost(pinned);
+        if (ev) cudaEventDestroy(ev);
+        if (st) cudaStreamDestroy(st);
+        mem = nullptr; pinned = nullptr; ev = nullptr; st = nullptr;
+    }
+    bool active() const {
+        if (err) return false;
+        for (int b = 0; b < batch; ++b)
+            if (!done[b]) return true;
+        return false;
+    }
+};
+
+size_t slab_doubles(int M, int N, bool big2, bool g) {
+    auto al = [](size_t x) { return (x + 31) & ~size_t(31); };   // 256-byte multiples
+    const size_t s = std::min(M, N), big = std::max(M, N);
+    size_t t = al((size_t)M * N) + 3 * al((size_t)N * M) + 7 * al(s * s);
+    if (big2) t += 2 * al(big * big);
+    if (g) t += al((size_t)N * M);
+    return t;
+}
+
+size_t group_bytes(int batch, int M, int N, int prec, bool big2, bool g) {
+    const size_t big = std::max(M, N);
+    const size_t tiles = ((big + 63) / 64) * ((big + 63) / 64);
+    size_t b = sizeof(double) * slab_doubles(M, N, big2, g) * batch;
+    b += align_up(sizeof(double) * 2 * 8 * tiles * batch);            // partials
+    b += align_up(sizeof(double) * 2 * 2 * 256);                      // reduction scratch
+    b += 3 * align_up(sizeof(InstanceRef) * batch) + align_up(sizeof(int) * 2 * batch) +
+         2 * align_up(sizeof(double) * 2 * batch);
+    if (prec != PINV_PREC_FP64) b += align_up(tc_workspace_bytes((int)big, (int)big, (int)big, tc_mode(TC_FP64), batch));
+    return b + 4096;
+}
+
+int group_begin(Group& G) {
+    pinv_handle* h = G.h;
+    const pinv_desc& d0 = G.d[0];
+    G.batch = (int)G.d.size();
+    G.prec = d0.prec;
+    G.fp64_class = d0.prec == PINV_PREC_FP64 ? 0 : TC_FP64;
+    G.level = d0.prec == PINV_PREC_MIXED_BF16 ? TC_BF16 : (d0.prec == PINV_PREC_FP32 ? TC_FP32 : G.fp64_class);
+    G.left = G.M > G.N;
+    G.finish = d0.finish == PINV_FINISH_CLEAN;
+    G.max_iter = 0;
+    for (auto& x : G.d) G.max_iter = std::max(G.max_iter, x.max_iter ? x.max_iter : 100);
+    const bool gk = d0.kind == PINV_OUTER_G;
+    G.info.assign(G.batch, pinv_info{});
+    G.prev.assign(G.batch, INFINITY);
+    G.prev2.assign(G.batch, INFINITY);
+    G.done.assign(G.batch, 0);
+    CK(cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming));
+    const size_t bytes = group_bytes(G.batch, G.M, G.N, G.prec, G.finish, gk);
+    CK(cudaMalloc(&G.mem, bytes));
+    CK(cudaMallocHost(&G.pinned, sizeof(double) * 2 * G.batch + sizeof(int) * 2 * G.batch + 64));
+    // carve
+    char* p = G.mem;
+    auto take = [&](size_t n) { char* q = p; p += align_up(n); return q; };
+    const long long slab = (long long)slab_doubles(G.M, G.N, G.finish, gk);
+    double* slabs = (double*)take(sizeof(double) * slab * G.batch);
+    Ctx& c = G.c;
+    c.h = h; c.st = G.st; c.m = G.M; c.n = G.N; c.left = G.left; c.s = G.left ? G.N : G.M;
+    c.c = pm_coefficients();
+    c.batch = G.batch; c.stride = slab;
+    {
+        auto al = [](size_t x) { return (x + 31) & ~size_t(31); };
+        const size_t s2 = (size_t)c.s * c.s, big = std::max(G.M, G.N);
+        double* q = slabs;
+        c.Ad = q; q += al((size_t)G.M * G.N);
+        for (int i = 0; i < 3; ++i) { c.X[i] = q; q += al((size_t)G.N * G.M); }
+        for (int i = 0; i < 7; ++i) { c.sq[i] = q; q += al(s2); }
+        c.big[0] = c.big[1] = nullptr;
+        if (G.finish) { c.big[0] = q; q += al(big * big); c.big[1] = q; q += al(big * big); }
+        c.Gd = nullptr;
+        if (gk) { c.Gd = q; q += al((size_t)G.N * G.M); }
+        c.A = c.Ad; c.lda = G.N; c.Al = nullptr;
+    }
+    const size_t big = std::max(G.M, G.N);
+    const size_t tiles = ((big + 63) / 64) * ((big + 63) / 64);
+    c.partials = (double*)take(sizeof(double) * 2 * 8 * tiles * G.batch);
+    c.red = (double*)take(sizeof(double) * 2 * 2 * 256);
+    G.tabA = (InstanceRef*)take(sizeof(InstanceRef) * G.batch);
+    G.tabX = (InstanceRef*)take(sizeof(InstanceRef) * G.batch);
+    G.tabG = (InstanceRef*)take(sizeof(InstanceRef) * G.batch);
+    G.dmask = (int*)take(sizeof(int) * 2 * G.batch);
+    G.dalpha = (double*)take(sizeof(double) * 2 * G.batch);
+    G.dnorms = (double*)take(sizeof(double) * 2 * G.batch);
+    if (G.prec != PINV_PREC_FP64) {
+        c.tcws_bytes = tc_workspace_bytes((int)big, (int)big, (int)big, tc_mode(TC_FP64), G.batch);
+        c.tcws = take(c.tcws_bytes);
+    }
+    // instance tables and alphas
+    std::vector<InstanceRef> ta(G.batch), tx(G.batch), tg(G.batch);
+    std::vector<double> alpha(G.batch);
+    for (int b = 0; b < G.batch; ++b) {
+        const pinv_desc& x = G.d[b];
+        ta[b] = InstanceRef{x.A, nullptr, x.m, x.n, x.lda, 0};
+        tx[b] = InstanceRef{nullptr, x.X, x.n, x.m, x.ldx, 0};
+        tg[b] = InstanceRef{x.G, nullptr, x.n, x.m, x.ldg, 0};
+        alpha[b] = x.alpha;
+    }
+    CK(cudaMemcpyAsync(G.tabA, ta.data(), sizeof(InstanceRef) * G.batch, cudaMemcpyHostToDevice, G.st));
+    CK(cudaMemcpyAsync(G.tabX, tx.data(), sizeof(InstanceRef) * G.batch, cudaMemcpyHostToDevice, G.st));
+    CK(cudaMemcpyAsync(G.tabG, tg.data(), sizeof(InstanceRef) * G.batch, cudaMemcpyHostToDevice, G.st));
+    gather_pad(G.tabA, G.batch, G.M, G.N, c.Ad, slab, G.st);
+    if (gk) gather_pad(G.tabG, G.batch, G.N, G.M, c.Gd, slab, G.st);
+    // alpha = 0: the Section 4 recipe per instance (norms on the padded slab are the instance's)
+    for (int b = 0; b < G.batch; ++b) {
+        if (alpha[b] == 0.0) {
+            norms_1_inf(G.M, G.N, c.Ad + b * slab, G.N, h->dsmall, c.red, G.st);
+            CK(cudaMemcpyAsync(G.pinned, h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, G.st));
+            CK(cudaStreamSynchronize(G.st));
+            const double pr = G.pinned[0] * G.pinned[1];
+            alpha[b] = (pr > 0 && std::isfinite(pr)) ? 1.0 / pr : 1.0;
+        }
+        G.info[b].alpha = alpha[b];
+        G.info[b].side = G.left ? 1 : 0;
+    }
+    CK(cudaMemcpyAsync(G.dalpha, alpha.data(), sizeof(double) * G.batch, cudaMemcpyHostToDevice, G.st));
+    if (gk) scale_copy_batched(G.N, G.M, c.Gd, G.M, G.dalpha, c.X[0], G.M, slab, G.batch, G.st);
+    else transpose_scale_batched(G.M, G.N, c.Ad, G.N, G.dalpha, c.X[0], G.M, slab, G.batch, G.st);
+    CK(cudaStreamSynchronize(G.st));
+    return PINV_OK;
+}
+
+// Issue loop k for every instance (asynchronous; norms land in pinned memory).
+int group_issue(Group& G) {
+    Ctx& c = G.c;
+    double maxprev = 0.0, maxprev2 = 0.0;
+    for (int b = 0; b < G.batch; ++b)
+        if (!G.done[b]) { maxprev = std::max(maxprev, G.prev[b]); maxprev2 = std::max(maxprev2, G.prev2[b]); }
+    if (G.level == TC_BF16 && maxprev <= 0.5) G.level = TC_FP32;
+    if (G.level == TC_FP32 && (maxprev <= 1e-4 || (maxprev < 1e-2 && maxprev >= 0.25 * maxprev2))) G.level = G.fp64_class;
+    c.prec_k = G.level;
+    const double* Xk = c.X[G.cur];
+    double* Xn = c.X[G.cur ^ 1];
+    int parts = pm_loop_f64(c, Xk, G.stabilise ? c.X[2] : Xn);
+    if (G.stabilise) parts = stabilise_f64(c, c.X[2], Xk, Xn);
+    if (parts < 0) return G.err = PINV_ERR_CUDA;
+    G.parts = parts;
+    reduce_pairs(c.partials, parts, G.dnorms, G.st, G.batch);
+    CK(cudaMemcpyAsync(G.pinned, G.dnorms, sizeof(double) * 2 * G.batch, cudaMemcpyDeviceToHost, G.st));
+    CK(cudaMemcpyAsync(G.pinned + 2 * G.batch, G.h->derr, sizeof(int), cudaMemcpyDeviceToHost, G.st));
+    CK(cudaEventRecord(G.ev, G.st));
+    return PINV_OK;
+}
+
+// Wait for loop k, apply the stop rule per instance, copy out stopped instances.
+int group_complete(Group& G) {
+    CK(cudaEventSynchronize(G.ev));
+    int derr;
+    std::memcpy(&derr, G.pinned + 2 * G.batch, sizeof(int));
+    if (derr) return G.err = PINV_ERR_TIMEOUT;
+    Ctx& c = G.c;
+    const int k = G.k;
+    const int prec_k = G.level;
+    const bool final_class = prec_k == G.fp64_class && G.prev_prec == G.fp64_class;
+    std::vector<int> mask(2 * G.batch, 0);
+    bool any_copy = false, all_below_switch = true;
+    for (int b = 0; b < G.batch; ++b) {
+        if (G.done[b]) continue;
+        pinv_info& I = G.info[b];
+        const pinv_desc& x = G.d[b];
+        const double dx2 = G.pinned[2 * b], x2 = G.pinned[2 * b + 1];
+        double e = std::sqrt(dx2);
+        if (x.stop == PINV_STOP_PAPER) e /= std::pow(18.0, k) * I.alpha;
+        else e = x2 > 0 ? e / std::sqrt(x2) : INFINITY;
+        I.loops_run = k + 1;
+        if (k < PINV_HISTORY) { I.history[k] = e; I.precision[k] = (signed char)prec_k; }
+        if (G.stabilise) ++I.stabilized_loops;
+        const int maxit = x.max_iter ? x.max_iter : 100;
+        int stop = 0;   // 1: keep X_k (buffer cur); 2: keep X_{k+1} (buffer cur^1)
+        if (!std::isfinite(e)) { I.status = PINV_ERR_NONFINITE; stop = 1; }
+        else if (e < x.tol) { I.status = PINV_OK; I.stop_reason = 0; I.iters = k + 1; I.rel_step = e; stop = 2; }
+        else {
+            const double pv = G.prev[b];
+            const bool stalled = G.stabilise ? (e >= pv) : (pv < 1e-3 && e >= pv * pv);
+            const double rel = x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY;
+            if (stalled && final_class) { I.status = PINV_OK; I.stop_reason = 1; I.iters = k; I.rel_step = pv; stop = 1; }
+            else if (rel > 1e3 && k > 0) { I.status = PINV_ERR_DIVERGED; I.iters = k; stop = 1; }
+            else if (k + 1 >= maxit) { I.status = PINV_ERR_MAXITER; I.stop_reason = 2; I.iters = k + 1; stop = 2; }
+        }
+        if (stop) {
+            G.done[b] = 1;
+            mask[stop == 1 ? b : G.batch + b] = 1;
+            any_copy = true;
+        } else {
+            G.prev2[b] = G.prev[b];
+            G.prev[b] = e;
+            I.rel_step = e;
+            I.iters = k + 1;
+            if (!(e < (x.switch_tol > 0 ? x.switch_tol : 1e-3))) all_below_switch = false;
+        }
+    }
+    if (G.d[0].variant == PINV_VARIANT_STABILIZED && prec_k == G.fp64_class && all_below_switch) G.stabilise = true;
+    G.prev_prec = prec_k;
+    if (any_copy) {
+        std::memcpy(G.pinned, mask.data(), sizeof(int) * 2 * G.batch);   // norms already consumed
+        CK(cudaMemcpyAsync(G.dmask, G.pinned, sizeof(int) * 2 * G.batch, cudaMemcpyHostToDevice, G.st));
+        scatter_out(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[G.cur], G.M, c.stride, G.st);
+        scatter_out(G.tabX, G.dmask + G.batch, G.batch, G.N, G.M, c.X[G.cur ^ 1], G.M, c.stride, G.st);
+        CK(cudaStreamSynchronize(G.st));   // the masks live in pinned memory reused next loop
+    }
+    G.cur ^= 1;
+    G.k = k + 1;
+    return PINV_OK;
+}
+
+// The finish step for every instance that ended with PINV_OK: restore its kept
+// iterate, project, run one more loop, copy out.
+int group_finish(Group& G) {
+    if (!G.finish || G.err) return G.err;
+    Ctx& c = G.c;
+    std::vector<int> mask(G.batch, 0);
+    bool any = false;
+    for (int b = 0; b < G.batch; ++b)
+        if (G.info[b].status == PINV_OK) { mask[b] = 1; any = true; }
+    if (!any) return PINV_OK;
+    std::memcpy(G.pinned, mask.data(), sizeof(int) * G.batch);
+    CK(cudaMemcpyAsync(G.dmask, G.pinned, sizeof(int) * G.batch, cudaMemcpyHostToDevice, G.st));
+    scatter_in(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[0], G.M, c.stride, G.st);
+    c.prec_k = G.fp64_class;
+    pinv_desc d0 = G.d[0];
+    cleanup_f64(c, &d0, c.X[0], c.X[1]);
+    if (pm_loop_f64(c, c.X[1], c.X[0]) < 0) return G.err = PINV_ERR_CUDA;
+    scatter_out(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[0], G.M, c.stride, G.st);
+    CK(cudaStreamSynchronize(G.st));
+    return PINV_OK;
+}
+
+int pad_to(int x, int g) { return ((x + g - 1) / g) * g; }
+
+// Run groups concurrently (one stream each): issue loop k of every active
+// group, then complete them in order.
+int run_groups(std::vector<std::unique_ptr<Group>>& groups) {
+    int rc = PINV_OK;
+    for (auto& g : groups) {
+        int r = group_begin(*g);
+        if (r) { g->err = r; rc = r; }
+    }
+    for (;;) {
+        bool any = false;
+        for (auto& g : groups)
+            if (g->active() && g->k < g->max_iter) { if (group_issue(*g)) rc = g->err; any = true; }
+        if (!any) break;
+        for (auto& g : groups)
+            if (!g->err && g->active() && g->k < g->max_iter) { if (group_complete(*g)) rc = g->err; }
+    }
+    for (auto& g : groups) {
+        if (group_finish(*g)) rc = g->err;
+        for (auto& I : g->info) if (g->err && I.status == PINV_OK) I.status = g->err;
+        g->release();
+    }
+    return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -666,12 +962,52 @@ int pinv_solve(pinv_handle* h, const pinv_desc* desc, void* stream, pinv_info* i
 int pinv_solve_batched(pinv_handle* h, int count, const pinv_desc* descs, void* stream,
                        pinv_info* infos) {
     if (!h || count < 0 || (count && !descs)) return PINV_ERR_ARG;
-    int worst = PINV_OK;
+    if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
     for (int i = 0; i < count; ++i) {
-        pinv_info local;
-        int rc = pinv_solve(h, &descs[i], stream, infos ? &infos[i] : &local);
-        if (rc != PINV_OK && worst == PINV_OK) worst = rc;
+        int rc = validate(&descs[i]);
+        if (rc) return rc;
+        if (descs[i].kind == PINV_DRAZIN || descs[i].host_buffers || descs[i].check) return PINV_ERR_ARG;
     }
+    // the caller's stream is ordered before the groups' streams
+    cudaEvent_t ready;
+    CK(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    CK(cudaEventRecord(ready, (cudaStream_t)stream));
+    CK(cudaEventSynchronize(ready));
+    cudaEventDestroy(ready);
+    // buckets: same settings and side, m and n padded to multiples of 64
+    std::map<std::vector<long long>, std::vector<int>> buckets;
+    for (int i = 0; i < count; ++i) {
+        const pinv_desc& d = descs[i];
+        const int Mp = pad_to(d.m, 64), Np = pad_to(d.n, 64);
+        std::vector<long long> key = {Mp, Np, d.kind, d.prec, d.variant, d.finish, d.stop};
+        buckets[key].push_back(i);
+    }
+    std::vector<std::unique_ptr<Group>> groups;
+    std::vector<std::vector<int>> members;
+    const int max_batch = 1024;
+    for (auto& kv : buckets) {
+        for (size_t o = 0; o < kv.second.size(); o += max_batch) {
+            auto g = std::make_unique<Group>();
+            g->h = h;
+            g->M = (int)kv.first[0];
+            g->N = (int)kv.first[1];
+            std::vector<int> idx;
+            for (size_t j = o; j < std::min(kv.second.size(), o + max_batch); ++j) {
+                idx.push_back(kv.second[j]);
+                g->d.push_back(descs[kv.second[j]]);
+            }
+            groups.push_back(std::move(g));
+            members.push_back(idx);
+        }
+    }
+    int rc = run_groups(groups);
+    int worst = rc;
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+        for (size_t j = 0; j < members[gi].size(); ++j) {
+            const pinv_info& I = groups[gi]->info[j];
+            if (infos) infos[members[gi][j]] = I;
+            if (I.status != PINV_OK && worst == PINV_OK) worst = I.status;
+        }
     return worst;
 }
 

@@ -62,6 +62,9 @@ struct TcParams {
     int pair_s[64], pair_t[64];
     int chunk;            // K elements per exact accumulation
     int exact;            // 1: slices on power-of-two grids (integer-valued products)
+    int S;                // slices per operand (tensor-map slice index = instance * S + s)
+    int batch;            // instances; instance b uses every FP64 matrix at +b*stride
+    long long stride;
     int tiles_m, tiles_n;
     Epilogue epi;
     int* err;             // device error word (0 = ok)
@@ -203,7 +206,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ntiles = P.tiles_m * P.tiles_n;
+    const int tiles_per = P.tiles_m * P.tiles_n;
+    const int ntiles = tiles_per * P.batch;
     const int kchunks = (P.K + P.chunk - 1) / P.chunk;
     const int units = P.npairs * kchunks;
 
@@ -230,7 +234,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             int stage = 0;
             uint32_t phase = 0;
             for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
-                const int m0 = (tile % P.tiles_m) * BM, n0 = (tile / P.tiles_m) * BN;
+                const int b = tile / tiles_per, tt = tile % tiles_per;
+                const int m0 = (tt % P.tiles_m) * BM, n0 = (tt / P.tiles_m) * BN;
                 for (int u = 0; u < units && !*abort_flag; ++u) {
                     const int pr = u / kchunks, ch = u % kchunks;
                     const int k_begin = ch * P.chunk;
@@ -241,8 +246,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                         }
                         uint8_t* sa = smem + stage * STAGE_BYTES;
                         mbar_expect_tx(&full[stage], STAGE_BYTES);
-                        tma_load_3d(sa, &mapA, &full[stage], k, m0, P.pair_s[pr]);
-                        tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, P.pair_t[pr]);
+                        tma_load_3d(sa, &mapA, &full[stage], k, m0, b * P.S + P.pair_s[pr]);
+                        tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, b * P.S + P.pair_t[pr]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                 }
@@ -303,9 +308,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         const uint32_t acc64 = lane_base + 2 * BN + 2 * half * EPI_COLS;
         int buf = 0;
         uint32_t accphase[2] = {0, 0};
-        const Epilogue& E = P.epi;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int m0 = (tile % P.tiles_m) * BM, n0 = (tile / P.tiles_m) * BN;
+            const int b = tile / tiles_per, tt = tile % tiles_per;
+            const int m0 = (tt % P.tiles_m) * BM, n0 = (tt / P.tiles_m) * BN;
+            Epilogue E = P.epi;   // instance b's matrices
+            const long long off = (long long)b * P.stride;
+            if (E.s1) E.s1 += off;
+            if (E.s2) E.s2 += off;
+            for (int o = 0; o < 3; ++o)
+                if (E.o[o].out) E.o[o].out += off;
+            const unsigned long long* rmax = P.rmax ? P.rmax + (size_t)b * P.M : nullptr;
+            const unsigned long long* cmax = P.cmax ? P.cmax + (size_t)b * P.N : nullptr;
             int iacc[EPI_COLS];
             int dcur = -1;
             bool have64 = false;
@@ -363,7 +376,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             if (!ok) break;
             // fused FP64 epilogue for this row of the tile, 16 columns at a time
             const int row = m0 + row_in_tile;
-            const int ei = (P.rmax && row < P.M) ? grid_exponent(P.rmax, row) : 0;
+            const int ei = (rmax && row < P.M) ? grid_exponent(rmax, row) : 0;
             double sd = 0.0, sx = 0.0;
             const double* s1 = (E.s1 && row < P.M) ? E.s1 + (size_t)row * E.ld1 : nullptr;
             const double* s2 = (E.s2 && row < P.M) ? E.s2 + (size_t)row * E.ld2 : nullptr;
@@ -377,7 +390,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     const int col = n0 + half * EPI_COLS + c + j;
                     if (col < P.N) {
                         double a = __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]);
-                        if (P.rmax) a = ldexp(a, ei + grid_exponent(P.cmax, col));
+                        if (rmax) a = ldexp(a, ei + grid_exponent(cmax, col));
                         const double v1 = s1 ? s1[col] : 0.0;
                         const double v2 = s2 ? s2[col] : 0.0;
                         const double id = (row == col) ? 1.0 : 0.0;
@@ -420,7 +433,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 // Rows of op(X) (op(X)[i][k] = trans ? X[k][i] : X[i][k]): mx[i] receives the
 // bit pattern of max_k |op(X)[i][k]| (non-negative doubles order like their
 // bits, so integer max is the floating max).  mx must be zeroed first.
-__global__ void row_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx) {
+__global__ void row_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx,
+                                  long long stride) {
+    X += (long long)blockIdx.y * stride;
+    mx += (size_t)blockIdx.y * rows;
     const int warps = blockDim.x >> 5;
     const int i = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
@@ -432,8 +448,11 @@ __global__ void row_absmax_kernel(int rows, int K, const double* X, int ld, unsi
 }
 // Transposed view: X is K x rows; a (32 columns) x (256 rows of X) patch per
 // block, coalesced along the columns, combined with atomicMax.
-__global__ void col_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx) {
+__global__ void col_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx,
+                                  long long stride) {
     __shared__ double sh[8][33];
+    X += (long long)blockIdx.z * stride;
+    mx += (size_t)blockIdx.z * rows;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     const int i = blockIdx.x * 32 + tx;
     const int k0 = blockIdx.y * 256;
@@ -453,8 +472,12 @@ __global__ void col_absmax_kernel(int rows, int K, const double* X, int ld, unsi
 // exact = 1: slices on the per-row grid 2^(e_i - 6(s+1)); exact = 0: one
 // round-to-nearest slice.
 __global__ void slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans,
-                             const unsigned long long* mx, int S, int exact, __nv_bfloat16* out) {
+                             const unsigned long long* mx, int S, int exact, __nv_bfloat16* out,
+                             long long stride) {
     __shared__ double t[32][33];
+    X += (long long)blockIdx.z * stride;                  // instance blockIdx.z
+    out += (size_t)blockIdx.z * S * rows * Kp;
+    if (mx) mx += (size_t)blockIdx.z * rows;
     const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     for (int r = ty; r < 32; r += 8) {
@@ -573,48 +596,52 @@ int tc_pairs(const TcMode& m) {
     return n;
 }
 
-size_t tc_workspace_bytes(int M, int N, int K, const TcMode& m) {
+size_t tc_workspace_bytes(int M, int N, int K, const TcMode& m, int batch) {
     const size_t Kp = (size_t)((K + 7) / 8) * 8;
     auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
-    return al((size_t)m.S * M * Kp * 2) + al((size_t)m.S * N * Kp * 2) + al(8 * (size_t)(M + N)) + 1024;
+    return al((size_t)batch * m.S * M * Kp * 2) + al((size_t)batch * m.S * N * Kp * 2) +
+           al(8 * (size_t)batch * (M + N)) + 1024;
 }
 
 size_t tc_smem_bytes() { return STAGES * STAGE_BYTES + 1024 + 256; }
 
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb, bool transB,
             const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err, cudaStream_t st,
-            int* kernels, cudaEvent_t ev_begin, cudaEvent_t ev_end) {
+            int* kernels, cudaEvent_t ev_begin, cudaEvent_t ev_end, int batch, long long stride) {
     const int Kp = ((K + 7) / 8) * 8;
-    if (tc_workspace_bytes(M, N, K, mode) > ws_bytes) return -1;
+    if (batch < 1 || tc_workspace_bytes(M, N, K, mode, batch) > ws_bytes) return -1;
     auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
     char* p = static_cast<char*>(ws);
     __nv_bfloat16* sa = reinterpret_cast<__nv_bfloat16*>(p);
-    p += al((size_t)mode.S * M * Kp * 2);
+    p += al((size_t)batch * mode.S * M * Kp * 2);
     __nv_bfloat16* sb = reinterpret_cast<__nv_bfloat16*>(p);
-    p += al((size_t)mode.S * N * Kp * 2);
+    p += al((size_t)batch * mode.S * N * Kp * 2);
     unsigned long long* ea = reinterpret_cast<unsigned long long*>(p);
-    unsigned long long* eb = ea + M;
+    unsigned long long* eb = ea + (size_t)batch * M;
 
     // slices of op(A) (rows i, length K) and of op(B)^T (rows j, length K)
     if (mode.exact) {
         // per-row maxima of op(A) and of op(B)^T (= columns of op(B))
-        if (cudaMemsetAsync(ea, 0, 8 * (size_t)(M + N), st) != cudaSuccess) return -1;
+        if (cudaMemsetAsync(ea, 0, 8 * (size_t)batch * (M + N), st) != cudaSuccess) return -1;
         dim3 blk(32, 8);
-        if (!transA) row_absmax_kernel<<<(M + 7) / 8, 256, 0, st>>>(M, K, A, lda, ea);
-        else col_absmax_kernel<<<dim3((M + 31) / 32, (K + 255) / 256), blk, 0, st>>>(M, K, A, lda, ea);
-        if (transB) row_absmax_kernel<<<(N + 7) / 8, 256, 0, st>>>(N, K, B, ldb, eb);
-        else col_absmax_kernel<<<dim3((N + 31) / 32, (K + 255) / 256), blk, 0, st>>>(N, K, B, ldb, eb);
+        if (!transA) row_absmax_kernel<<<dim3((M + 7) / 8, batch), 256, 0, st>>>(M, K, A, lda, ea, stride);
+        else col_absmax_kernel<<<dim3((M + 31) / 32, (K + 255) / 256, batch), blk, 0, st>>>(M, K, A, lda, ea, stride);
+        if (transB) row_absmax_kernel<<<dim3((N + 7) / 8, batch), 256, 0, st>>>(N, K, B, ldb, eb, stride);
+        else col_absmax_kernel<<<dim3((N + 31) / 32, (K + 255) / 256, batch), blk, 0, st>>>(N, K, B, ldb, eb, stride);
         *kernels += 2;
     }
     {
         dim3 blk(32, 8);
-        dim3 ga((Kp + 31) / 32, (M + 31) / 32), gb((Kp + 31) / 32, (N + 31) / 32);
-        slice_kernel<<<ga, blk, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, ea, mode.S, mode.exact, sa);
-        slice_kernel<<<gb, blk, 0, st>>>(N, K, Kp, B, ldb, transB ? 0 : 1, eb, mode.S, mode.exact, sb);
+        dim3 ga((Kp + 31) / 32, (M + 31) / 32, batch), gb((Kp + 31) / 32, (N + 31) / 32, batch);
+        slice_kernel<<<ga, blk, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, mode.exact ? ea : nullptr,
+                                         mode.S, mode.exact, sa, stride);
+        slice_kernel<<<gb, blk, 0, st>>>(N, K, Kp, B, ldb, transB ? 0 : 1, mode.exact ? eb : nullptr,
+                                         mode.S, mode.exact, sb, stride);
         *kernels += 2;
     }
     CUtensorMap ma, mb;
-    if (!make_map(&ma, sa, mode.S, M, Kp, BM) || !make_map(&mb, sb, mode.S, N, Kp, BN)) return -1;
+    if (!make_map(&ma, sa, batch * mode.S, M, Kp, BM) || !make_map(&mb, sb, batch * mode.S, N, Kp, BN))
+        return -1;
 
     TcParams P;
     P.M = M; P.N = N; P.K = K;
@@ -625,6 +652,9 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
             if (t >= 0 && t < mode.S) { P.pair_s[P.npairs] = s; P.pair_t[P.npairs] = t; ++P.npairs; }
         }
     P.exact = mode.exact;
+    P.S = mode.S;
+    P.batch = batch;
+    P.stride = stride;
     P.chunk = mode.exact ? 2048 : ((K + BK - 1) / BK) * BK;
     P.tiles_m = (M + BM - 1) / BM;
     P.tiles_n = (N + BN - 1) / BN;
@@ -632,8 +662,9 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.err = err;
     P.rmax = mode.exact ? ea : nullptr;
     P.cmax = mode.exact ? eb : nullptr;
-    const int tiles = P.tiles_m * P.tiles_n;
-    const int grid = tiles < num_sms() ? tiles : num_sms();
+    const int tiles = P.tiles_m * P.tiles_n;   // per instance
+    const int all_tiles = tiles * batch;
+    const int grid = all_tiles < num_sms() ? all_tiles : num_sms();
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
@@ -644,7 +675,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
-    return EPI_WARPS * tiles;   // pair partials: one per (tile, epilogue warp)
+    return EPI_WARPS * tiles;   // pair partials per instance: one per (tile, epilogue warp)
 }
 
 }  // namespace pinv

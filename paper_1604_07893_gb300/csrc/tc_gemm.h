@@ -18,16 +18,19 @@ struct TcMode {
 
 TcMode tc_mode(int prec);
 int tc_pairs(const TcMode& m);
-size_t tc_workspace_bytes(int M, int N, int K, const TcMode& m);
+size_t tc_workspace_bytes(int M, int N, int K, const TcMode& m, int batch = 1);
 size_t tc_smem_bytes();
 
 // C = op(A) op(B) with the fused FP64 epilogue `epi`.  `ws` holds the slices.
 // ev_begin/ev_end (optional) are recorded around the tensor-core kernel alone.
 // `err` is a device int that records a timed-out wait (0 = ok).  Adds the
-// number of kernels launched to *kernels.  Returns the count of pair partials
-// written when epi.partials is set (8 per 128 x 128 output tile) or -1.
+// number of kernels launched to *kernels.  batch > 1: instance b uses every
+// FP64 matrix (operands, side inputs, outputs) at +b*stride elements.  Returns
+// the count of pair partials per instance (8 per 128 x 128 output tile, the
+// instances one after another) or -1.
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb,
             bool transB, const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err,
-            cudaStream_t st, int* kernels, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+            cudaStream_t st, int* kernels, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr,
+            int batch = 1, long long stride = 0);
 
 }  // namespace pinv

@@ -203,7 +203,8 @@ def test_batched_equals_single(handle):
     Xs, infos = handle.solve_batched(As, alpha=0.0, tol=1e-12)
     for A, X, info in zip(As, Xs, infos):
         X1, _ = handle.solve(A, alpha=0.0, tol=1e-12)
-        assert torch.equal(X, X1)
+        # the batch pads each problem to a multiple of 64: same iterate, other rounding
+        assert rel(host(X), host(X1)) <= 1e-11
 
 
 def test_submit_poll_equals_solve(handle):
