@@ -174,19 +174,33 @@ void pinv_destroy(pinv_handle *h);
  * one handle. */
 int  pinv_solve(pinv_handle *h, const pinv_desc *desc, void *stream, pinv_info *info);
 
-/* Solve `count` independent problems (same kind/prec/variant/stop fields are
- * read per descriptor).  info may be NULL or an array of `count`. */
+/* Solve `count` independent Moore-Penrose or general-G problems (device
+ * buffers).  Problems are grouped by shape padded to multiples of 64 and by
+ * settings; each group runs the loop chain for all its problems in lockstep
+ * (one launch per product for the whole group) on its own stream, groups
+ * concurrently; each problem keeps its own alpha, stop rule and result.
+ * Zero padding leaves every problem's iterate exact.  Blocks until done.
+ * infos may be NULL or an array of `count`.  Returns PINV_OK or the first
+ * non-OK problem status. */
 int  pinv_solve_batched(pinv_handle *h, int count, const pinv_desc *descs, void *stream,
                         pinv_info *infos);
 
 /* Non-blocking: queue a problem for the handle's serving loop and return its
  * id.  The descriptor is copied; A, G and X must stay valid until pinv_poll
- * reports a final status.  PINV_ERR_BUDGET if the problem's workspace alone
- * exceeds the budget. */
+ * reports a final status.  Moore-Penrose and general-G problems with device
+ * buffers (PINV_ERR_ARG otherwise); PINV_ERR_BUDGET if the problem's device
+ * memory alone exceeds the handle's HBM budget.  Thread-safe with pinv_poll. */
 int  pinv_submit(pinv_handle *h, const pinv_desc *desc, uint64_t *request_id);
 
-/* Drive the serving loop one round and report request `id`: PINV_PENDING, or
- * the final status with *info filled (the request is then forgotten). */
+/* Drive the serving loop one round and report request `id`.  A round admits
+ * queued requests, oldest first, into groups of equal padded shape while their
+ * memory fits under the HBM budget next to the groups already running; runs
+ * one loop of every running group, each on its own stream, so requests that
+ * arrived in different rounds compute at the same time; and retires groups
+ * whose requests have all stopped.  Returns PINV_PENDING, or the request's
+ * final status with *info filled (info->ms = submit-to-completion latency);
+ * the request is then forgotten.  Results equal a lone pinv_solve of the same
+ * request up to the rounding of the padded shape. */
 int  pinv_poll(pinv_handle *h, uint64_t request_id, pinv_info *info);
 
 /* Section 4's scaling for rectangular A: *alpha = 1/(||A||_1 ||A||_inf),

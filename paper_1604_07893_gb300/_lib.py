@@ -206,6 +206,8 @@ class Handle:
         return Xs, [i.to_dict() for i in infos]
 
     def submit(self, A, X, **kw) -> int:
+        """pinv_submit: queue a problem; A, X (and G) must stay alive until poll
+        returns its final status."""
         d = self.make_desc(A, X, **kw)
         rid = C.c_uint64()
         rc = self._lib.pinv_submit(self._h, C.byref(d), C.byref(rid))

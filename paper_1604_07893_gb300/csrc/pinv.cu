@@ -77,16 +77,20 @@ struct pinv_handle {
     double* dsmall = nullptr;  // device: reduction outputs
     int* derr = nullptr;       // device error word of the tensor-core kernels
     std::vector<cudaEvent_t> events;  // profiling pool (pairs), created on demand
-    // serving
+    // serving (pinv_submit / pinv_poll)
     std::mutex mu;
     uint64_t next_id = 1;
     struct Request {
         pinv_desc desc;
         int status = PINV_PENDING;
         pinv_info info{};
+        std::chrono::steady_clock::time_point t_submit;
     };
-    std::deque<uint64_t> queue;
+    std::deque<uint64_t> queue;                 // submitted, not yet admitted
     std::map<uint64_t, Request> requests;
+    struct Running;                             // a group of admitted requests on the device
+    std::vector<std::unique_ptr<Running>> running;
+    size_t serving_bytes = 0;                   // device memory held by running groups
 };
 
 namespace {
@@ -914,6 +918,104 @@ int run_groups(std::vector<std::unique_ptr<Group>>& groups) {
     return rc;
 }
 
+
+// ------------------------------------------------------------------ serving
+// Continuous batching at loop granularity: every pinv_poll runs one round.
+//  1. admission: pending requests, oldest first, are bucketed by padded shape
+//     and settings; each bucket becomes a new group if its memory fits under
+//     the handle's HBM budget together with the groups already running
+//     (otherwise admission stops: first come, first served);
+//  2. every running group issues its next loop on its own stream, so groups
+//     admitted in different rounds run on the device at the same time;
+//  3. every group completes its loop (per-request stop rule); groups whose
+//     requests have all stopped apply the finish step, report, free memory.
+}  // namespace
+
+struct pinv_handle::Running {
+    std::unique_ptr<Group> g;
+    std::vector<uint64_t> ids;
+    size_t bytes = 0;
+};
+
+namespace {
+
+int serve_round(pinv_handle* h) {
+    using clock = std::chrono::steady_clock;
+    // 1. admission
+    std::map<std::vector<long long>, std::vector<uint64_t>> buckets;
+    std::vector<std::vector<long long>> order;
+    while (!h->queue.empty()) {
+        const uint64_t id = h->queue.front();
+        const pinv_desc& d = h->requests[id].desc;
+        std::vector<long long> key = {pad_to(d.m, 64), pad_to(d.n, 64), d.kind, d.prec, d.variant, d.finish,
+                                      d.stop};
+        if (!buckets.count(key)) order.push_back(key);
+        buckets[key].push_back(id);
+        h->queue.pop_front();
+    }
+    std::deque<uint64_t> deferred;
+    bool full = false;
+    for (auto& key : order) {
+        auto& ids = buckets[key];
+        size_t o = 0;
+        while (o < ids.size()) {
+            const size_t n = std::min<size_t>(ids.size() - o, 256);
+            const size_t bytes = group_bytes((int)n, (int)key[0], (int)key[1], (int)key[3],
+                                             key[5] == PINV_FINISH_CLEAN, key[2] == PINV_OUTER_G);
+            if (full || (h->budget && h->serving_bytes + bytes > h->budget)) {
+                full = true;
+                for (size_t j = o; j < ids.size(); ++j) deferred.push_back(ids[j]);
+                break;
+            }
+            auto r = std::make_unique<pinv_handle::Running>();
+            r->g = std::make_unique<Group>();
+            r->g->h = h;
+            r->g->M = (int)key[0];
+            r->g->N = (int)key[1];
+            for (size_t j = o; j < o + n; ++j) {
+                r->ids.push_back(ids[j]);
+                r->g->d.push_back(h->requests[ids[j]].desc);
+            }
+            r->bytes = bytes;
+            const int rc = group_begin(*r->g);
+            if (rc) {
+                for (uint64_t id : r->ids) { h->requests[id].status = rc; h->requests[id].info.status = rc; }
+                r->g->release();
+            } else {
+                h->serving_bytes += bytes;
+                h->running.push_back(std::move(r));
+            }
+            o += n;
+        }
+    }
+    for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) h->queue.push_front(*it);
+    // 2. issue one loop of every running group, 3. complete them
+    for (auto& r : h->running)
+        if (r->g->active() && r->g->k < r->g->max_iter) group_issue(*r->g);
+    for (auto& r : h->running)
+        if (!r->g->err && r->g->active() && r->g->k < r->g->max_iter) group_complete(*r->g);
+    // retire finished groups
+    for (size_t i = 0; i < h->running.size();) {
+        auto& r = h->running[i];
+        Group& G = *r->g;
+        if (G.active() && G.k < G.max_iter && !G.err) { ++i; continue; }
+        group_finish(G);
+        const auto now = clock::now();
+        for (size_t j = 0; j < r->ids.size(); ++j) {
+            auto& q = h->requests[r->ids[j]];
+            q.info = G.info[j];
+            if (G.err && q.info.status == PINV_OK) q.info.status = G.err;
+            if (!G.done[j] && q.info.status == PINV_OK) q.info.status = PINV_ERR_MAXITER;
+            q.info.ms = std::chrono::duration<float, std::milli>(now - q.t_submit).count();
+            q.status = q.info.status;
+        }
+        G.release();
+        h->serving_bytes -= r->bytes;
+        h->running.erase(h->running.begin() + i);
+    }
+    return PINV_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -943,6 +1045,7 @@ void pinv_destroy(pinv_handle* h) {
     if (!h) return;
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
+    h->running.clear();
     if (h->derr) cudaFree(h->derr);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     if (h->ws) cudaFree(h->ws);
@@ -1015,14 +1118,15 @@ int pinv_submit(pinv_handle* h, const pinv_desc* desc, uint64_t* id) {
     if (!h || !desc || !id) return PINV_ERR_ARG;
     int rc = validate(desc);
     if (rc) return rc;
-    const size_t need = workspace_bytes(desc->m, desc->n, desc->kind == PINV_DRAZIN,
-                                        desc->host_buffers != 0,
-                                        desc->check != 0 || desc->finish == PINV_FINISH_CLEAN, desc->prec);
+    if (desc->kind == PINV_DRAZIN || desc->host_buffers || desc->check) return PINV_ERR_ARG;
+    const size_t need = group_bytes(1, pad_to(desc->m, 64), pad_to(desc->n, 64), desc->prec,
+                                    desc->finish == PINV_FINISH_CLEAN, desc->kind == PINV_OUTER_G);
     if (h->budget && need > h->budget) return PINV_ERR_BUDGET;
     std::lock_guard<std::mutex> lk(h->mu);
     *id = h->next_id++;
     pinv_handle::Request r;
     r.desc = *desc;
+    r.t_submit = std::chrono::steady_clock::now();
     h->requests[*id] = r;
     h->queue.push_back(*id);
     return PINV_OK;
@@ -1033,16 +1137,12 @@ int pinv_poll(pinv_handle* h, uint64_t id, pinv_info* info) {
     std::lock_guard<std::mutex> lk(h->mu);
     auto it = h->requests.find(id);
     if (it == h->requests.end()) return PINV_ERR_UNKNOWN_ID;
-    // drive one request per poll (FIFO)
-    if (!h->queue.empty()) {
-        uint64_t next = h->queue.front();
-        h->queue.pop_front();
-        auto& r = h->requests[next];
-        cudaSetDevice(h->device);
-        r.status = solve_one(h, &r.desc, nullptr, &r.info);
+    if (it->second.status == PINV_PENDING && (!h->queue.empty() || !h->running.empty())) {
+        if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
+        serve_round(h);
     }
     if (it->second.status == PINV_PENDING) return PINV_PENDING;
-    int st = it->second.status;
+    const int st = it->second.status;
     if (info) *info = it->second.info;
     h->requests.erase(it);
     return st;
