@@ -340,6 +340,253 @@ def run_ours(args):
     return 0
 
 
+
+
+# ---------------------------------------------------------------------------
+# further workloads (each prints its own JSON line; not the default run)
+# ---------------------------------------------------------------------------
+
+def _events(stream):
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def _pct(xs, q):
+    xs = sorted(xs)
+    return xs[min(len(xs) - 1, max(0, int(math.ceil(q * len(xs))) - 1))]
+
+
+def _emit(line):
+    print(json.dumps(line), flush=True)
+
+
+def run_mp64(args):
+    """64 x 48 Moore-Penrose, s log-spaced in [1e-2, 1], alpha = 2/(s1^2 + sr^2):
+    per-solve latency (the problem is launch-bound)."""
+    import torch
+    from oracle import hyperpower as H
+    from paper_1604_07893_gb300 import Handle, workloads as W
+    w = W.rectangular(64, 48, None, 1.0, 1e-2, seed=0)
+    alpha = 2.0 / (w.s[0] ** 2 + w.s[-1] ** 2)
+    A = torch.from_numpy(w.A).cuda()
+    X = torch.empty(48, 64, dtype=torch.float64, device="cuda")
+    h = Handle(0)
+    st = torch.cuda.current_stream()
+    out = {}
+    for prec in ("fp64_tc", "fp64"):
+        for _ in range(args.warmup):
+            h.solve(A, X, alpha=alpha, tol=1e-12, prec=prec)
+        lat = []
+        for _ in range(max(args.steps, 50)):
+            e0, e1 = _events(st)
+            e0.record(st)
+            _, info = h.solve(A, X, alpha=alpha, tol=1e-12, prec=prec)
+            e1.record(st)
+            torch.cuda.synchronize()
+            lat.append(e0.elapsed_time(e1))
+        err = float(np.linalg.norm(X.cpu().numpy() - (w.V / w.s) @ w.U.T) / np.linalg.norm((w.V / w.s) @ w.U.T))
+        out[prec] = {"value": 1e3 / statistics.mean(lat), "p50_ms": statistics.median(lat),
+                     "p99_ms": _pct(lat, 0.99), "rel_err_vs_closed_form": err, "loops": info["iters"],
+                     "kernels_per_solve": info["kernels"]}
+    t0 = time.perf_counter()
+    ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+    t_cpu = time.perf_counter() - t0
+    _emit({"metric": "pseudoinverses/s (64x48, latency-bound)", "value": out["fp64_tc"]["value"],
+           "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "config": {"workload": "moore_penrose_64x48", "alpha": alpha, "tol": 1e-12},
+           "fp64_tc": out["fp64_tc"], "fp64_gpu": out["fp64"],
+           "cpu_baseline": {"value": 1.0 / t_cpu, "unit": "solves/s", "kind": "oracle", "sample": "full solve",
+                            "cores": len(os.sched_getaffinity(0))}})
+    h.close()
+
+
+def run_drazin(args):
+    """Drazin inverse of a 2048 x 2048 index-2 matrix (C 1536 x 1536, 256 2x2
+    Jordan blocks), X0 = A^2 / Tr(A^3), FP64-class products on the tensor cores,
+    finish A^2 X^5 A^2 + one loop; native FP64 beside it."""
+    import torch
+    from oracle import hyperpower as H
+    from paper_1604_07893_gb300 import Handle, workloads as W
+    d = W.drazin_index2(2048, 512, seed=2)
+    B = np.zeros((2048, 2048))
+    B[:1536, :1536] = np.linalg.inv(d.C)
+    Pinv = np.linalg.inv(d.P)
+    rows = np.random.default_rng(0).choice(2048, 32, replace=False)
+    ref_rows = d.P[rows] @ B @ Pinv
+    A = torch.from_numpy(d.A).cuda()
+    X = torch.empty_like(A)
+    h = Handle(0)
+    st = torch.cuda.current_stream()
+    res = {}
+    for prec in ("fp64_tc", "fp64"):
+        kw = dict(kind="drazin", drazin_index=2, alpha=0.0, tol=1e-12, prec=prec, finish="clean")
+        for _ in range(args.warmup if prec == "fp64_tc" else 1):
+            h.solve(A, X, **kw)
+        times = []
+        for _ in range(args.steps if prec == "fp64_tc" else 1):
+            e0, e1 = _events(st)
+            e0.record(st)
+            _, info = h.solve(A, X, **kw)
+            e1.record(st)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        _, cinfo = h.solve(A, X, check=True, **kw)
+        err = float(np.linalg.norm(X.cpu().numpy()[rows] - ref_rows) / np.linalg.norm(ref_rows))
+        res[prec] = {"value": 1e3 / statistics.mean(times), "ms_per_solve": statistics.mean(times),
+                     "loops": info["iters"], "drazin_residuals": cinfo["drazin"], "sampled_rows_rel_err": err}
+    t0 = time.perf_counter()
+    H.hyperpower_step(d.A, H.x0_drazin(d.A, 2), side="right")
+    t_loop = time.perf_counter() - t0
+    loops = res["fp64_tc"]["loops"] + 2
+    _emit({"metric": "Drazin inverses/s at 1e-9 (2048x2048, index 2)", "value": res["fp64_tc"]["value"],
+           "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "dtype": "bf16 slices (fp64-class)",
+           "config": {"workload": "drazin_2048_index2", "n_nilpotent": 512, "spectrum": "sector |arg| <= pi/8",
+                      "steps": args.steps, "warmup": args.warmup},
+           "fp64_tc": res["fp64_tc"], "fp64_gpu": res["fp64"],
+           "cpu_baseline": {"value": 1.0 / (t_loop * loops), "unit": "solves/s", "kind": "oracle",
+                            "cores": len(os.sched_getaffinity(0)),
+                            "sample": f"one naive loop ({t_loop:.2f} s) x {loops} loops"}})
+    h.close()
+
+
+def run_batched(args):
+    """4096 independent problems, m ~ U{32..512}, n ~ U{16..m}, rank n,
+    singular values log-uniform in [1e-3, 1] (Householder-product factors),
+    alpha = 1/s_1^2: one pinv_solve_batched call (BF16 bulk loops, FP32-class,
+    FP64-class last loop) against the FP64 batched path and a sample of
+    per-matrix FP64 solves."""
+    import ctypes as C
+    import torch
+    from oracle import hyperpower as H
+    from paper_1604_07893_gb300 import Handle, workloads as W
+    from paper_1604_07893_gb300._lib import Desc, Info
+    count = args.count
+    ws = W.uneven_batch_fast(count, seed=3)
+    As = [torch.from_numpy(w.A).cuda() for w in ws]
+    Xs = [torch.empty(w.A.shape[1], w.A.shape[0], dtype=torch.float64, device="cuda") for w in ws]
+    h = Handle(0)
+    st = torch.cuda.current_stream()
+
+    def run(prec, tol):
+        descs = (Desc * count)(*[h.make_desc(A, X, alpha=1.0 / w.s[0] ** 2, tol=tol, prec=prec, finish="clean")
+                                 for A, X, w in zip(As, Xs, ws)])
+        infos = (Info * count)()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rc = h._lib.pinv_solve_batched(h._h, count, descs, C.c_void_p(st.cuda_stream), infos)
+        torch.cuda.synchronize()
+        return rc, time.perf_counter() - t0, infos
+
+    run("mixed_bf16", 1e-6)     # warm-up (allocations, tensor maps)
+    times = []
+    for _ in range(args.steps):
+        rc, t, infos = run("mixed_bf16", 1e-6)
+        times.append(t)
+    sample = np.random.default_rng(0).choice(count, 64, replace=False)
+    errs = [float(np.linalg.norm(Xs[i].cpu().numpy() - (ws[i].V / ws[i].s) @ ws[i].U.T) /
+                  np.linalg.norm((ws[i].V / ws[i].s) @ ws[i].U.T)) for i in sample]
+    loops = [infos[i].iters for i in range(count)]
+    rc64, t64, _ = run("fp64", 1e-12)
+    # per-matrix FP64 solves on a sample, extrapolated
+    t0 = time.perf_counter()
+    for i in sample[:32]:
+        h.solve(As[i], Xs[i], alpha=1.0 / ws[i].s[0] ** 2, tol=1e-12, prec="fp64")
+    torch.cuda.synchronize()
+    per_matrix = (time.perf_counter() - t0) / 32
+    t0 = time.perf_counter()
+    for i in sample[:8]:
+        w = ws[i]
+        H.solve(w.A, H.x0_moore_penrose(w.A, 1.0 / w.s[0] ** 2), tol=1e-12, alpha=1.0 / w.s[0] ** 2)
+    t_cpu = (time.perf_counter() - t0) / 8
+    t = statistics.median(times)
+    _emit({"metric": "pseudoinverses/s, 4096 uneven problems", "value": count / t, "unit": "solves/s",
+           "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "bf16 + bf16 slices",
+           "config": {"workload": f"uneven_batch_{count}", "m": [32, 512], "n": [16, "m"],
+                      "prec": "mixed_bf16 (BF16 growth loops, FP32-class, FP64-class last loop)", "tol": 1e-6,
+                      "finish": "clean",
+                      "steps": args.steps},
+           "ms_per_batch": t * 1e3, "status_ok": sum(1 for i in range(count) if infos[i].status == 0),
+           "loops": {"min": min(loops), "max": max(loops)},
+           "accuracy": {"sampled": 64, "max_rel_err_vs_closed_form": max(errs), "meets_1e-4": max(errs) <= 1e-4},
+           "fp64_gpu_batched": {"value": count / t64, "s_per_batch": t64, "status": rc64},
+           "fp64_gpu_per_matrix_loop": {"value": 1.0 / per_matrix, "sample": "32 single solves"},
+           "cpu_baseline": {"value": 1.0 / t_cpu, "unit": "solves/s", "kind": "oracle",
+                            "cores": len(os.sched_getaffinity(0)), "sample": "8 sampled problems, full solves"}})
+    h.close()
+
+
+def run_serving(args):
+    """Poisson stream (2000 requests/s) of preconditioner requests for SPD
+    A = Q diag(lambda) Q^T, lambda log-spaced in [1e-3, 1], n in {256 ... 8192}
+    (weights 40/25/15/10/7/3 %), G = I, alpha = 1/lambda_max, BF16 bulk loops,
+    under a 120 GB HBM budget; a bounded sample of the stream."""
+    import torch
+    from paper_1604_07893_gb300 import Handle, workloads as W
+    nreq = args.count
+    sizes = W.serving_sizes(nreq, seed=5)
+    arrivals = W.poisson_arrivals(2000.0, nreq, seed=5)
+    h = Handle(0, hbm_budget_bytes=120 << 30)
+    reqs = []
+    for i, n in enumerate(sizes):
+        Q, lam = W.spd_fast(int(n), seed=100 + i)
+        Qd = torch.from_numpy(Q).cuda()
+        QL = Qd * torch.from_numpy(lam).cuda()
+        A = h.gemm(QL, Qd, trans_b=True, prec="fp64_tc")
+        A = 0.5 * (A + A.T)
+        reqs.append((int(n), A.contiguous(), torch.eye(int(n), dtype=torch.float64, device="cuda"),
+                     torch.empty(int(n), int(n), dtype=torch.float64, device="cuda"), Q, lam))
+    torch.cuda.synchronize()
+    kw = dict(kind="outer_g", alpha=1.0, tol=1e-6, prec="mixed_bf16")
+    # warm-up: one request of each size alone
+    for n in sorted(set(int(x) for x in sizes)):
+        r = next(q for q in reqs if q[0] == n)
+        h.solve(r[1], r[3], G=r[2], **kw)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ids, submitted, done = {}, 0, {}
+    while len(done) < nreq:
+        now = time.perf_counter() - t0
+        while submitted < nreq and arrivals[submitted] <= now:   # requests arrive on their own clock
+            n, A, G, X, _, _ = reqs[submitted]
+            ids[submitted] = h.submit(A, X, G=G, **kw)
+            submitted += 1
+        pending = [i for i in ids if i not in done]
+        if not pending:
+            time.sleep(0.0002)
+            continue
+        for i in pending:                  # each poll of a pending request drives one round
+            r = h.poll(ids[i])
+            if r is not None:
+                done[i] = r
+    makespan = time.perf_counter() - t0
+    lat = [done[i][1]["ms"] for i in done]
+    by_size = {}
+    for i in done:
+        by_size.setdefault(int(sizes[i]), []).append(done[i][1]["ms"])
+    lat_by_size = {str(n): {"count": len(v), "p50_ms": statistics.median(v), "p99_ms": _pct(v, 0.99)}
+                   for n, v in sorted(by_size.items())}
+    errs = []
+    for i in range(min(nreq, 6)):
+        n, A, G, X, Q, lam = reqs[i]
+        inv = (Q / lam) @ Q.T
+        errs.append(float(np.linalg.norm(X.cpu().numpy() - inv) / np.linalg.norm(inv)))
+    flops = sum(14.0 * int(n) ** 3 * done[i][1]["iters"] for i, n in enumerate(sizes))
+    _emit({"metric": "preconditioner solves/s under continuous batching, p50/p99 latency",
+           "value": nreq / makespan, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
+           "data": "synthetic", "dtype": "bf16 + bf16 slices",
+           "config": {"workload": "serving_spd_poisson2000", "requests": nreq, "sizes": [256, 512, 1024, 2048, 4096, 8192],
+                      "weights": [0.40, 0.25, 0.15, 0.10, 0.07, 0.03], "hbm_budget_gb": 120, "tol": 1e-6,
+                      "prec": "mixed_bf16"},
+           "latency_ms": {"p50": statistics.median(lat), "p99": _pct(lat, 0.99), "max": max(lat),
+                          "by_size": lat_by_size},
+           "status_ok": sum(1 for i in done if done[i][0] == 0),
+           "makespan_s": makespan, "offered_rate": 2000.0,
+           "fp64_equivalent_tflops": flops / makespan / 1e12,
+           "accuracy": {"sampled": len(errs), "max_rel_err_vs_inverse": max(errs), "meets_1e-4": max(errs) <= 1e-4}})
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -349,9 +596,22 @@ def main():
     ap.add_argument("--prec", default="fp64_tc", choices=["fp64_tc", "fp64", "fp32", "mixed_bf16"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--workload", default="mp4096x3072",
+                    choices=["mp4096x3072", "mp64x48", "drazin2048", "batched4096", "serving"])
+    ap.add_argument("--count", type=int, default=None, help="instances (batched) or requests (serving)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "mp64x48":
+        return run_mp64(args)
+    if args.workload == "drazin2048":
+        return run_drazin(args)
+    if args.workload == "batched4096":
+        args.count = args.count or 4096
+        return run_batched(args)
+    if args.workload == "serving":
+        args.count = args.count or 64
+        return run_serving(args)
     return run_ours(args)
 
 

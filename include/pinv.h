@@ -119,7 +119,9 @@ typedef struct {
     pinv_prec    prec;
     pinv_variant variant;
     double       switch_tol; /* stabilised switch threshold; 0 = 1e-3                */
-    pinv_finish  finish;
+    pinv_finish  finish;     /* required (PINV_FINISH_CLEAN) for MIXED_BF16 / FP32
+                                schedules when m != n: the block the iteration does
+                                not contract keeps their rounding (PINV_ERR_ARG)   */
     int          host_buffers; /* 1: A, G and X are HOST pointers; the call copies
                                   A (and G) in and X out on `stream` and returns
                                   after the copy back has completed                  */

@@ -126,6 +126,7 @@ struct Ctx {
     int prec_k = 0;         // product precision of the GEMMs being issued (0 = DMMA FP64)
     int batch = 1;          // instances processed together (all buffers at +b*stride)
     long long stride = 0;
+    bool yield_sms = false; // tensor-core launches release SMs after every tile
     void* tcws = nullptr;   // slice workspace of the tensor-core engine
     size_t tcws_bytes = 0;
     int gemms = 0;
@@ -234,7 +235,7 @@ int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const d
         c.tensor_flops += 2.0 * M * N * K * tc_pairs(tc_mode(c.prec_k)) * c.batch;
         r = tc_gemm(M, N, K, A, lda, tA, B, ldb, tB, e, tc_mode(c.prec_k), c.tcws, c.tcws_bytes,
                     c.h->derr, c.st, &c.kernels, prof_ev(c, slot, 0), prof_ev(c, slot, 1), c.batch,
-                    c.stride);
+                    c.stride, c.yield_sms);
     }
     return r;
 }
@@ -424,6 +425,12 @@ int validate(const pinv_desc* d) {
         return PINV_ERR_ARG;
     if (d->variant != PINV_VARIANT_PLAIN && d->variant != PINV_VARIANT_STABILIZED) return PINV_ERR_ARG;
     if (d->finish != PINV_FINISH_NONE && d->finish != PINV_FINISH_CLEAN) return PINV_ERR_ARG;
+    // BF16/FP32-class loops leave rounding in the block the iteration does not
+    // contract when m != n (Theorem 6.2: E12 or E21 persists); only the finish
+    // step removes it, so low-precision schedules on rectangular problems need it
+    if ((d->prec == PINV_PREC_MIXED_BF16 || d->prec == PINV_PREC_FP32) && d->m != d->n &&
+        d->finish != PINV_FINISH_CLEAN)
+        return PINV_ERR_ARG;
     return PINV_OK;
 }
 
@@ -657,6 +664,8 @@ struct Group {
     std::vector<char> done;
     int parts = 0;
     int err = PINV_OK;
+    bool in_flight = false;        // a loop has been issued and not completed
+    bool serving = false;          // priority stream by size, SMs released per tile
 
     ~Group() { release(); }
     void release() {
@@ -712,7 +721,18 @@ int group_begin(Group& G) {
     G.prev.assign(G.batch, INFINITY);
     G.prev2.assign(G.batch, INFINITY);
     G.done.assign(G.batch, 0);
-    CK(cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking));
+    if (G.serving) {
+        // smaller problems on higher-priority streams: their CTAs are scheduled
+        // first whenever an SM frees up
+        int least = 0, greatest = 0;
+        cudaDeviceGetStreamPriorityRange(&least, &greatest);
+        const int big = std::max(G.M, G.N);
+        const int span = least - greatest;   // greatest is the numerically smallest
+        int prio = big <= 512 ? greatest : (big <= 2048 ? greatest + span / 2 : least);
+        CK(cudaStreamCreateWithPriority(&G.st, cudaStreamNonBlocking, prio));
+    } else {
+        CK(cudaStreamCreateWithFlags(&G.st, cudaStreamNonBlocking));
+    }
     CK(cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming));
     const size_t bytes = group_bytes(G.batch, G.M, G.N, G.prec, G.finish, gk);
     CK(cudaMalloc(&G.mem, bytes));
@@ -726,6 +746,7 @@ int group_begin(Group& G) {
     c.h = h; c.st = G.st; c.m = G.M; c.n = G.N; c.left = G.left; c.s = G.left ? G.N : G.M;
     c.c = pm_coefficients();
     c.batch = G.batch; c.stride = slab;
+    c.yield_sms = G.serving;
     {
         auto al = [](size_t x) { return (x + 31) & ~size_t(31); };
         const size_t s2 = (size_t)c.s * c.s, big = std::max(G.M, G.N);
@@ -806,12 +827,14 @@ int group_issue(Group& G) {
     CK(cudaMemcpyAsync(G.pinned, G.dnorms, sizeof(double) * 2 * G.batch, cudaMemcpyDeviceToHost, G.st));
     CK(cudaMemcpyAsync(G.pinned + 2 * G.batch, G.h->derr, sizeof(int), cudaMemcpyDeviceToHost, G.st));
     CK(cudaEventRecord(G.ev, G.st));
+    G.in_flight = true;
     return PINV_OK;
 }
 
 // Wait for loop k, apply the stop rule per instance, copy out stopped instances.
 int group_complete(Group& G) {
     CK(cudaEventSynchronize(G.ev));
+    G.in_flight = false;
     int derr;
     std::memcpy(&derr, G.pinned + 2 * G.batch, sizeof(int));
     if (derr) return G.err = PINV_ERR_TIMEOUT;
@@ -970,6 +993,7 @@ int serve_round(pinv_handle* h) {
             auto r = std::make_unique<pinv_handle::Running>();
             r->g = std::make_unique<Group>();
             r->g->h = h;
+            r->g->serving = true;
             r->g->M = (int)key[0];
             r->g->N = (int)key[1];
             for (size_t j = o; j < o + n; ++j) {
@@ -989,16 +1013,24 @@ int serve_round(pinv_handle* h) {
         }
     }
     for (auto it = deferred.rbegin(); it != deferred.rend(); ++it) h->queue.push_front(*it);
-    // 2. issue one loop of every running group, 3. complete them
-    for (auto& r : h->running)
-        if (r->g->active() && r->g->k < r->g->max_iter) group_issue(*r->g);
-    for (auto& r : h->running)
-        if (!r->g->err && r->g->active() && r->g->k < r->g->max_iter) group_complete(*r->g);
+    // 2./3. every group advances on its own: a group whose loop has finished on
+    // the device is completed and immediately issued its next loop; a group
+    // still computing is left alone, so small problems are not held back by
+    // large ones in other groups
+    for (auto& r : h->running) {
+        Group& G = *r->g;
+        if (G.err) continue;
+        if (G.in_flight) {
+            if (cudaEventQuery(G.ev) != cudaSuccess) continue;
+            group_complete(G);
+        }
+        if (!G.err && G.active() && G.k < G.max_iter) group_issue(G);
+    }
     // retire finished groups
     for (size_t i = 0; i < h->running.size();) {
         auto& r = h->running[i];
         Group& G = *r->g;
-        if (G.active() && G.k < G.max_iter && !G.err) { ++i; continue; }
+        if (G.in_flight || (G.active() && G.k < G.max_iter && !G.err)) { ++i; continue; }
         group_finish(G);
         const auto now = clock::now();
         for (size_t j = 0; j < r->ids.size(); ++j) {

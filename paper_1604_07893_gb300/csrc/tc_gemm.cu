@@ -591,7 +591,8 @@ size_t tc_smem_bytes() { return STAGES * STAGE_BYTES + 1024 + 256; }
 
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb, bool transB,
             const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err, cudaStream_t st,
-            int* kernels, cudaEvent_t ev_begin, cudaEvent_t ev_end, int batch, long long stride) {
+            int* kernels, cudaEvent_t ev_begin, cudaEvent_t ev_end, int batch, long long stride,
+            bool one_tile_per_cta) {
     const int Kp = ((K + 7) / 8) * 8;
     if (batch < 1 || tc_workspace_bytes(M, N, K, mode, batch) > ws_bytes) return -1;
     auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
@@ -648,7 +649,9 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.cmax = mode.exact ? eb : nullptr;
     const int tiles = P.tiles_m * P.tiles_n;   // per instance
     const int all_tiles = tiles * batch;
-    const int grid = all_tiles < num_sms() ? all_tiles : num_sms();
+    // persistent (one CTA per SM walking the tiles) unless the caller wants the
+    // SMs released after every tile (so higher-priority streams get in)
+    const int grid = (one_tile_per_cta || all_tiles < num_sms()) ? all_tiles : num_sms();
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());

@@ -31,6 +31,6 @@ size_t tc_smem_bytes();
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb,
             bool transB, const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err,
             cudaStream_t st, int* kernels, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr,
-            int batch = 1, long long stride = 0);
+            int batch = 1, long long stride = 0, bool one_tile_per_cta = false);
 
 }  // namespace pinv

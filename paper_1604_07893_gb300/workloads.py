@@ -186,3 +186,42 @@ def hilbert(m: int, n: int) -> np.ndarray:
     j = np.arange(1, n + 1)[None, :]
     return 1.0 / (i + j - 1.0)
 
+
+
+def householder_orthogonal(rng: np.random.Generator, n: int, k: int | None = None,
+                           reflectors: int = 3) -> np.ndarray:
+    """First k columns of H_1 H_2 ... H_r, H_i = I - 2 v_i v_i^T / (v_i^T v_i) with
+    Gaussian v_i: a dense seeded orthogonal matrix formed in O(r n^2) (used where
+    a workload needs many or very large orthogonal factors and does not ask for
+    Haar ones)."""
+    k = n if k is None else k
+    Q = np.eye(n)[:, :k].copy()
+    for _ in range(reflectors):
+        v = rng.standard_normal(n)
+        v /= np.linalg.norm(v)
+        Q -= 2.0 * np.outer(v, v @ Q)
+    return Q
+
+
+def uneven_batch_fast(count: int, seed: int = 3, s_min: float = 1e-3, m_lo: int = 32,
+                      m_hi: int = 512, n_lo: int = 16) -> list[Rectangular]:
+    """The uneven batch family with Householder-product factors: A = U diag(s) V^T,
+    m ~ U{m_lo..m_hi}, n ~ U{n_lo..m}, rank n, s log-uniform in [s_min, 1]."""
+    shapes = uneven_shapes(count, seed, m_lo, m_hi, n_lo)
+    out = []
+    for i, (m, n) in enumerate(shapes):
+        rng = np.random.default_rng(seed * 1_000_003 + i)
+        U = householder_orthogonal(rng, m, n)
+        V = householder_orthogonal(rng, n, n)
+        s = np.sort(10.0 ** rng.uniform(math.log10(s_min), 0.0, n))[::-1].copy()
+        out.append(Rectangular(A=np.ascontiguousarray((U * s) @ V.T), U=U, s=s, V=V))
+    return out
+
+
+def spd_fast(n: int, lam_min: float = 1e-3, lam_max: float = 1.0, seed: int = 5):
+    """Factors of the SPD family with a Householder-product Q (A itself is formed
+    by the caller, e.g. on the device): returns (Q, lambda)."""
+    rng = np.random.default_rng(seed)
+    Q = householder_orthogonal(rng, n)
+    lam = np.logspace(math.log10(lam_max), math.log10(lam_min), n)
+    return Q, lam

@@ -30,16 +30,17 @@ def make_request(n, seed, lam_min=1e-3):
     return s, A, G, X
 
 
-def drain(h, ids, rounds=2000):
+def drain(h, ids, limit_s=120.0):
+    """Poll until every request is final (polls return at once; the groups
+    advance on the device between them)."""
     done = {}
-    for _ in range(rounds):
+    t0 = time.time()
+    while len(done) < len(ids) and time.time() - t0 < limit_s:
         for i in ids:
             if i not in done:
                 r = h.poll(i)
                 if r is not None:
                     done[i] = r
-        if len(done) == len(ids):
-            break
     return done
 
 
@@ -74,17 +75,16 @@ def test_late_arrivals_overlap_with_running_requests(cuda):
     h = Handle(0)
     slow = make_request(256, seed=1, lam_min=1e-4)
     sid = h.submit(slow[1], slow[3], G=slow[2], kind="outer_g", alpha=1.0, tol=1e-12, prec="fp64_tc")
-    assert h.poll(sid) is None                 # admitted, first loop done
+    assert h.poll(sid) is None                 # admitted, first loop issued
     fast = [make_request(64, seed=10 + i, lam_min=0.1) for i in range(3)]
     fids = [h.submit(f[1], f[3], G=f[2], kind="outer_g", alpha=1.0, tol=1e-12, prec="fp64_tc")
             for f in fast]
     order = []
-    for _ in range(500):
+    t0 = time.time()
+    while len(order) < 4 and time.time() - t0 < 120:
         for i in [sid] + fids:
             if i not in order and h.poll(i) is not None:
                 order.append(i)
-        if len(order) == 4:
-            break
     assert order[-1] == sid                     # the fast ones overtook it
     assert rel(slow[3].cpu().numpy(), spd_inverse(slow[0])) <= 1e-9
     h.close()

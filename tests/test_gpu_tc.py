@@ -138,3 +138,14 @@ def test_gemm_fp64_tc_wide_dynamic_range(handle):
     A = rng.standard_normal((96, 200)) * 10.0 ** rng.uniform(-30, 30, (96, 1))
     B = rng.standard_normal((200, 80)) * 10.0 ** rng.uniform(-30, 30, (1, 80))
     assert check_gemm(handle, A, B, False, False, "fp64_tc") <= BOUND["fp64_tc"]
+
+
+def test_low_precision_on_rectangular_requires_the_finish(handle):
+    """Theorem 6.2: on m != n the block the loop does not contract keeps the
+    BF16/FP32 rounding; the library refuses such a schedule without the finish."""
+    from paper_1604_07893_gb300 import PinvError
+    w = W.rectangular(100, 60, None, 1.0, 1e-2, seed=2)
+    for prec in ("mixed_bf16", "fp32"):
+        with pytest.raises(PinvError) as e:
+            handle.solve(dev(w.A), alpha=1.0, tol=1e-12, prec=prec)
+        assert e.value.code == -1
