@@ -77,6 +77,10 @@ struct pinv_handle {
     double* dsmall = nullptr;  // device: reduction outputs
     int* derr = nullptr;       // device error word of the tensor-core kernels
     std::vector<cudaEvent_t> events;  // profiling pool (pairs), created on demand
+    // pinned readback blocks for groups, reused (pinned allocation can
+    // synchronise the device, so it happens only when the pool is empty)
+    std::vector<void*> pinned_blocks;
+    bool pool_ready = false;
     // serving (pinv_submit / pinv_poll)
     std::mutex mu;
     uint64_t next_id = 1;
@@ -668,12 +672,14 @@ struct Group {
     bool serving = false;          // priority stream by size, SMs released per tile
 
     ~Group() { release(); }
+    // Stream-ordered release: no device-wide synchronisation, so retiring a
+    // group never waits for other groups' kernels.
     void release() {
         if (st) cudaStreamSynchronize(st);
-        if (mem) cudaFree(mem);
-        if (pinned) cudaFreeHost(pinned);
+        if (mem) cudaFreeAsync(mem, st);
+        if (pinned) h->pinned_blocks.push_back(pinned);
         if (ev) cudaEventDestroy(ev);
-        if (st) cudaStreamDestroy(st);
+        if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
         mem = nullptr; pinned = nullptr; ev = nullptr; st = nullptr;
     }
     bool active() const {
@@ -683,6 +689,8 @@ struct Group {
         return false;
     }
 };
+
+constexpr size_t kPinnedBlock = 64 * 1024;   // readback block of a group (batch <= 1024)
 
 size_t slab_doubles(int M, int N, bool big2, bool g) {
     auto al = [](size_t x) { return (x + 31) & ~size_t(31); };   // 256-byte multiples
@@ -735,8 +743,22 @@ int group_begin(Group& G) {
     }
     CK(cudaEventCreateWithFlags(&G.ev, cudaEventDisableTiming));
     const size_t bytes = group_bytes(G.batch, G.M, G.N, G.prec, G.finish, gk);
-    CK(cudaMalloc(&G.mem, bytes));
-    CK(cudaMallocHost(&G.pinned, sizeof(double) * 2 * G.batch + sizeof(int) * 2 * G.batch + 64));
+    if (!h->pool_ready) {   // keep freed group memory in the stream-ordered pool
+        cudaMemPool_t pool;
+        if (cudaDeviceGetDefaultMemPool(&pool, h->device) == cudaSuccess) {
+            uint64_t keep = ~0ull;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+        }
+        h->pool_ready = true;
+    }
+    CK(cudaMallocAsync((void**)&G.mem, bytes, G.st));
+    const size_t pin_bytes = sizeof(double) * 2 * G.batch + sizeof(int) * 2 * G.batch + 64;
+    if (pin_bytes <= kPinnedBlock && !h->pinned_blocks.empty()) {
+        G.pinned = (double*)h->pinned_blocks.back();
+        h->pinned_blocks.pop_back();
+    } else {
+        CK(cudaMallocHost(&G.pinned, std::max(pin_bytes, kPinnedBlock)));
+    }
     // carve
     char* p = G.mem;
     auto take = [&](size_t n) { char* q = p; p += align_up(n); return q; };
@@ -1078,6 +1100,8 @@ void pinv_destroy(pinv_handle* h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     h->running.clear();
+    for (void* p : h->pinned_blocks) cudaFreeHost(p);
+    h->pinned_blocks.clear();
     if (h->derr) cudaFree(h->derr);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     if (h->ws) cudaFree(h->ws);
