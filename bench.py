@@ -478,10 +478,10 @@ def run_batched(args):
         torch.cuda.synchronize()
         return rc, time.perf_counter() - t0, infos
 
-    run("mixed_bf16", 1e-6)     # warm-up (allocations, tensor maps)
+    run("bf16_fp32", 1e-6)     # warm-up (allocations, tensor maps)
     times = []
     for _ in range(args.steps):
-        rc, t, infos = run("mixed_bf16", 1e-6)
+        rc, t, infos = run("bf16_fp32", 1e-6)
         times.append(t)
     sample = np.random.default_rng(0).choice(count, 64, replace=False)
     errs = [float(np.linalg.norm(Xs[i].cpu().numpy() - (ws[i].V / ws[i].s) @ ws[i].U.T) /
@@ -503,7 +503,8 @@ def run_batched(args):
     _emit({"metric": "pseudoinverses/s, 4096 uneven problems", "value": count / t, "unit": "solves/s",
            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "bf16 + bf16 slices",
            "config": {"workload": f"uneven_batch_{count}", "m": [32, 512], "n": [16, "m"],
-                      "prec": "mixed_bf16 (BF16 growth loops, FP32-class, FP64-class last loop)", "tol": 1e-6,
+                      "prec": "bf16_fp32 (BF16 growth loops, FP32-class finish, FP64-class projection + loop)",
+                      "tol": 1e-6,
                       "finish": "clean",
                       "steps": args.steps},
            "ms_per_batch": t * 1e3, "status_ok": sum(1 for i in range(count) if infos[i].status == 0),
@@ -537,7 +538,7 @@ def run_serving(args):
         reqs.append((int(n), A.contiguous(), torch.eye(int(n), dtype=torch.float64, device="cuda"),
                      torch.empty(int(n), int(n), dtype=torch.float64, device="cuda"), Q, lam))
     torch.cuda.synchronize()
-    kw = dict(kind="outer_g", alpha=1.0, tol=1e-6, prec="mixed_bf16")
+    kw = dict(kind="outer_g", alpha=1.0, tol=1e-6, prec="bf16_fp32", symmetric=True)
     # warm-up: one request of each size alone
     for n in sorted(set(int(x) for x in sizes)):
         r = next(q for q in reqs if q[0] == n)
@@ -574,10 +575,10 @@ def run_serving(args):
     flops = sum(14.0 * int(n) ** 3 * done[i][1]["iters"] for i, n in enumerate(sizes))
     _emit({"metric": "preconditioner solves/s under continuous batching, p50/p99 latency",
            "value": nreq / makespan, "unit": "solves/s", "n_gpus": 1, "higher_is_better": True,
-           "data": "synthetic", "dtype": "bf16 + bf16 slices",
+           "data": "synthetic", "dtype": "bf16 + bf16 slices (fp32-class)",
            "config": {"workload": "serving_spd_poisson2000", "requests": nreq, "sizes": [256, 512, 1024, 2048, 4096, 8192],
                       "weights": [0.40, 0.25, 0.15, 0.10, 0.07, 0.03], "hbm_budget_gb": 120, "tol": 1e-6,
-                      "prec": "mixed_bf16"},
+                      "prec": "bf16_fp32 (BF16 growth loops, FP32-class to the end)", "symmetric": True},
            "latency_ms": {"p50": statistics.median(lat), "p99": _pct(lat, 0.99), "max": max(lat),
                           "by_size": lat_by_size},
            "status_ok": sum(1 for i in done if done[i][0] == 0),

@@ -75,11 +75,16 @@ typedef enum {
                                  null block (full column rank, nonsingular); needs
                                  alpha <= 1/sigma_max^2 (e.g. the alpha = 0 recipe) */
     PINV_PREC_MIXED_FP8  = 2, /* reserved: FP8 early loops (returns PINV_ERR_ARG)  */
-    PINV_PREC_FP32       = 3, /* FP32-class loops (4 exact BF16 slices, 10 slice
-                                 products) until the step is < 1e-4 or stops falling,
-                                 then FP64-class                                   */
-    PINV_PREC_FP64_TC    = 4  /* every product FP64-accurate on the BF16 tensor
+    PINV_PREC_FP32       = 3, /* FP32-class loops (5 exact BF16 slices, 15 slice
+                                 products, ~30 bits) until the step is < 1e-4 or
+                                 stops falling, then FP64-class                    */
+    PINV_PREC_FP64_TC    = 4, /* every product FP64-accurate on the BF16 tensor
                                  cores: 9 exact slices per operand, 45 products    */
+    PINV_PREC_BF16_FP32  = 5  /* FP32-finished: BF16 while the step is > 0.5, then
+                                 FP32-class to the end (the stop rule ends at the
+                                 FP32 noise floor); the finish, if asked, in
+                                 FP64-class products.  Accuracy ~ u_fp32 * kappa;
+                                 problems without a null block                   */
 } pinv_prec;
 
 typedef enum {
@@ -128,7 +133,14 @@ typedef struct {
     int          check;      /* 1: fill info->penrose / info->drazin (extra GEMMs)   */
     int          profile;    /* 1: time every GEMM with CUDA events on `stream`
                                 (info->gemm_ms / gemm_flops)                         */
-    int          reserved[3];
+    int          symmetric;  /* PINV_OUTER_G only: 1 asserts A is symmetric and G
+                                commutes with it (e.g. G = I, the preconditioner
+                                family), so the exact R is symmetric: the four
+                                products of its even polynomial (R2, R4, M, TS)
+                                compute half their tiles and mirror them.  R and
+                                R Z stay full (their antisymmetric part corrects
+                                the iterate).  Nonsingular A only.                 */
+    int          reserved[2];
 } pinv_desc;
 
 #define PINV_HISTORY 128

@@ -19,7 +19,7 @@ ERRORS = {-1: "PINV_ERR_ARG", -2: "PINV_ERR_BUDGET", -3: "PINV_ERR_NONFINITE", -
           -5: "PINV_ERR_MAXITER", -6: "PINV_ERR_TIMEOUT", -7: "PINV_ERR_CUDA", -8: "PINV_ERR_UNKNOWN_ID"}
 KIND = {"moore_penrose": 0, "drazin": 1, "outer_g": 2}
 STOP = {"rel_fro": 0, "paper": 1}
-PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3, "fp64_tc": 4}
+PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3, "fp64_tc": 4, "bf16_fp32": 5}
 VARIANT = {"plain": 0, "stabilized": 1}
 FINISH = {None: 0, "none": 0, "clean": 1}
 HISTORY = 128
@@ -42,7 +42,8 @@ class Desc(C.Structure):
                 ("alpha", C.c_double), ("tol", C.c_double), ("stop", C.c_int),
                 ("max_iter", C.c_int), ("prec", C.c_int), ("variant", C.c_int),
                 ("switch_tol", C.c_double), ("finish", C.c_int), ("host_buffers", C.c_int),
-                ("check", C.c_int), ("profile", C.c_int), ("reserved", C.c_int * 3)]
+                ("check", C.c_int), ("profile", C.c_int), ("symmetric", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 
 class Info(C.Structure):
@@ -149,7 +150,7 @@ class Handle:
     @staticmethod
     def make_desc(A, X, *, kind="moore_penrose", G=None, drazin_index=0, alpha=0.0, tol=1e-12,
                   stop="rel_fro", max_iter=0, prec="fp64", variant="plain", switch_tol=0.0,
-                  finish=None, check=False, host=False, profile=False) -> Desc:
+                  finish=None, check=False, host=False, profile=False, symmetric=False) -> Desc:
         if host:
             import numpy as np
             for M in (A, X) + ((G,) if G is not None else ()):
@@ -170,7 +171,8 @@ class Handle:
                     kind=KIND[kind], drazin_index=drazin_index, alpha=alpha, tol=tol,
                     stop=STOP[stop], max_iter=max_iter, prec=PREC[prec], variant=VARIANT[variant],
                     switch_tol=switch_tol, finish=FINISH[finish], host_buffers=1 if host else 0,
-                    check=1 if check else 0, profile=1 if profile else 0)
+                    check=1 if check else 0, profile=1 if profile else 0,
+                    symmetric=1 if symmetric else 0)
 
     # ------------------------------------------------------------ entry points
     def solve(self, A, X=None, *, stream=None, raise_on_error=True, **kw):

@@ -39,10 +39,13 @@ inline Epilogue epi_none() {
 // transA: A is stored K x M (element (i,k) at A[k*lda + i]); likewise transB.
 // batch > 1: instance b uses every matrix (operands, side inputs, outputs) at
 // +b*stride elements and writes its pair partials after those of instance b-1.
+// sym_out (M == N, no partials): the product is known to be symmetric; only
+// tiles on or above the diagonal are computed, off-diagonal ones also written
+// transposed.
 // Returns the pair partials per instance (the CTA count) or -1 on a launch error.
 int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
              const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st,
-             int batch = 1, long long stride = 0);
+             int batch = 1, long long stride = 0, bool sym_out = false);
 int gemm_f64_ctas(int M, int N);
 
 // Deterministic sum of `count` (pair) partials into out[0..1] (device); with

@@ -33,6 +33,7 @@ struct GemmArgs {
     const double* A; int lda; int transA;
     const double* B; int ldb; int transB;
     long long stride;   // batch: instance b reads/writes every matrix at +b*stride
+    int sym;            // symmetric output: only tiles with n-block >= m-block, mirrored
 };
 
 __device__ __forceinline__ double loadA(const GemmArgs& g, int i, int k) {
@@ -53,6 +54,8 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int wm = warp >> 1, wn = warp & 1;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+    if (g.sym && blockIdx.y > blockIdx.x) return;   // lower triangle: mirrored by its partner
+    const bool mirror = g.sym && blockIdx.y != blockIdx.x;
     if (blockIdx.z) {   // instance blockIdx.z of a batch: shift every matrix
         const long long off = (long long)blockIdx.z * g.stride;
         g.A += off; g.B += off;
@@ -141,7 +144,10 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
                         if (o < epi.nout) {
                             const EpiTerm& t = epi.o[o];
                             double v = t.a_acc * a + t.a_s1 * v1 + t.a_s2 * v2 + t.a_id * id;
-                            if (t.out) t.out[(size_t)row * t.ld + col] = v;
+                            if (t.out) {
+                                t.out[(size_t)row * t.ld + col] = v;
+                                if (mirror) t.out[(size_t)col * t.ld + row] = v;
+                            }
                             if (o == 0 && epi.partials) {
                                 const double d = v - v1;
                                 sd += d * d;
@@ -177,8 +183,9 @@ int gemm_f64_ctas(int M, int N) { return ((N + BN - 1) / BN) * ((M + BM - 1) / B
 
 int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
              const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st,
-             int batch, long long stride) {
-    GemmArgs g{M, N, K, A, lda, transA ? 1 : 0, B, ldb, transB ? 1 : 0, stride};
+             int batch, long long stride, bool sym_out) {
+    if (sym_out && (M != N || epi.partials)) return -1;
+    GemmArgs g{M, N, K, A, lda, transA ? 1 : 0, B, ldb, transB ? 1 : 0, stride, sym_out ? 1 : 0};
     dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
     gemm_f64_kernel<<<grid, THREADS, 0, st>>>(g, epi);
     if (cudaPeekAtLastError() != cudaSuccess) return -1;

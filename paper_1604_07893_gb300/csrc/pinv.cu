@@ -131,6 +131,7 @@ struct Ctx {
     int batch = 1;          // instances processed together (all buffers at +b*stride)
     long long stride = 0;
     bool yield_sms = false; // tensor-core launches release SMs after every tile
+    bool symmetric = false; // R and its polynomials are symmetric: half the tiles, mirrored
     void* tcws = nullptr;   // slice workspace of the tensor-core engine
     size_t tcws_bytes = 0;
     int gemms = 0;
@@ -224,22 +225,26 @@ void carve(Ctx& c, bool drazin, bool host, bool check, int prec) {
 }
 
 int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const double* B, int ldb,
-         bool tB, const Epilogue& e) {
+         bool tB, const Epilogue& e, bool sym = false) {
     ++c.gemms;
     ++c.kernels;
-    c.gemm_flops += 2.0 * M * N * K * c.batch;
+    c.gemm_flops += 2.0 * M * N * K * c.batch;   // algorithmic work of the full product
     const int slot = prof_slot(c);
     int r;
     if (c.prec_k == 0) {
         if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 0), c.st);
-        r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st, c.batch, c.stride);
+        r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st, c.batch, c.stride, sym);
         if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 1), c.st);
     } else {
         --c.kernels;  // tc_gemm counts its own launches (slicing + GEMM)
-        c.tensor_flops += 2.0 * M * N * K * tc_pairs(tc_mode(c.prec_k)) * c.batch;
+        {
+            const int tm = (M + 127) / 128;   // executed tiles: the upper triangle in symmetric mode
+            const double frac = sym ? (double)(tm * (tm + 1) / 2) / (double)(tm * tm) : 1.0;
+            c.tensor_flops += 2.0 * M * N * K * tc_pairs(tc_mode(c.prec_k)) * c.batch * frac;
+        }
         r = tc_gemm(M, N, K, A, lda, tA, B, ldb, tB, e, tc_mode(c.prec_k), c.tcws, c.tcws_bytes,
                     c.h->derr, c.st, &c.kernels, prof_ev(c, slot, 0), prof_ev(c, slot, 1), c.batch,
-                    c.stride, c.yield_sms);
+                    c.stride, c.yield_sms, sym);
     }
     return r;
 }
@@ -272,28 +277,35 @@ int pm_loop_f64(Ctx& c, const double* Xin, double* Xout) {
            *S = c.sq[6];
     double *Z = L1, *D = L2;  // L1/L2 are dead once M is formed
     const Coef& k = c.c;
+    // With a symmetric A and a commuting G the exact R is symmetric.  R itself
+    // and R Z are computed in full: their antisymmetric part is the first-order
+    // correction of the iterate's error (near convergence R = -E11 Sigma), and
+    // dropping it stops the self-correction (measured: 1e-6 errors after the
+    // finish).  Products 2-5 only build the even polynomial of R, where
+    // symmetrising drops second-order terms: they compute half their tiles.
+    const bool y = c.symmetric;
     // 1: R = I - X A  |  I - A X
     if (c.left) gemm(c, s, s, m, Xin, m, false, c.A, c.lda, false, epi1(term(R, s, -1, 0, 0, 1)));
     else        gemm(c, s, s, n, c.A, c.lda, false, Xin, m, false, epi1(term(R, s, -1, 0, 0, 1)));
     // 2: R2
-    gemm(c, s, s, s, R, s, false, R, s, false, epi1(term(R2, s, 1)));
+    gemm(c, s, s, s, R, s, false, R, s, false, epi1(term(R2, s, 1)), y);
     // 3: R4, L1, L2
     {
         Epilogue e = epi1(term(R4, s, 1), R2, s);
         e.o[1] = term(L1, s, 1, k.c1, 0, 1);
         e.o[2] = term(L2, s, 1, k.c2, 0, 1);
         e.nout = 3;
-        gemm(c, s, s, s, R2, s, false, R2, s, false, e);
+        gemm(c, s, s, s, R2, s, false, R2, s, false, e, y);
     }
     // 4: M = L1 L2 -> T, S
     {
         Epilogue e = epi1(term(T, s, 1, k.c3), R2, s, R4, s);
         e.o[1] = term(S, s, 1, k.d1, k.d2);
         e.nout = 2;
-        gemm(c, s, s, s, L1, s, false, L2, s, false, e);
+        gemm(c, s, s, s, L1, s, false, L2, s, false, e, y);
     }
     // 5: Z = T S + mu R2 + psi R4
-    gemm(c, s, s, s, T, s, false, S, s, false, epi1(term(Z, s, 1, k.mu, k.psi), R2, s, R4, s));
+    gemm(c, s, s, s, T, s, false, S, s, false, epi1(term(Z, s, 1, k.mu, k.psi), R2, s, R4, s), y);
     // 6: D = R Z + Z - I
     gemm(c, s, s, s, R, s, false, Z, s, false, epi1(term(D, s, 1, 1, 0, -1), Z, s));
     // 7: X' = X + D X | X + X D, with stop partials
@@ -412,6 +424,14 @@ int residual_checks(Ctx& c, const pinv_desc* d, const double* X, pinv_info* info
     return PINV_OK;
 }
 
+// The caller's hint: a symmetric A with a G that commutes with it (e.g. G = I),
+// so the exact iterates are polynomials in A and R is symmetric.  Not used for
+// Moore-Penrose: on rank-deficient problems even the symmetrised even
+// polynomial loses accuracy (6e-9 instead of 2e-12 on 512 x 384 rank 288).
+bool iterates_symmetric(const pinv_desc* d) {
+    return d->kind == PINV_OUTER_G && d->symmetric;
+}
+
 int validate(const pinv_desc* d) {
     if (!d) return PINV_ERR_ARG;
     if (d->m < 1 || d->n < 1) return PINV_ERR_ARG;
@@ -425,14 +445,15 @@ int validate(const pinv_desc* d) {
     if (d->stop != PINV_STOP_REL_FRO && d->stop != PINV_STOP_PAPER) return PINV_ERR_ARG;
     if (d->max_iter < 0 || d->max_iter > PINV_HISTORY) return PINV_ERR_ARG;
     if (d->prec != PINV_PREC_FP64 && d->prec != PINV_PREC_MIXED_BF16 && d->prec != PINV_PREC_FP32 &&
-        d->prec != PINV_PREC_FP64_TC)
+        d->prec != PINV_PREC_FP64_TC && d->prec != PINV_PREC_BF16_FP32)
         return PINV_ERR_ARG;
     if (d->variant != PINV_VARIANT_PLAIN && d->variant != PINV_VARIANT_STABILIZED) return PINV_ERR_ARG;
     if (d->finish != PINV_FINISH_NONE && d->finish != PINV_FINISH_CLEAN) return PINV_ERR_ARG;
     // BF16/FP32-class loops leave rounding in the block the iteration does not
     // contract when m != n (Theorem 6.2: E12 or E21 persists); only the finish
     // step removes it, so low-precision schedules on rectangular problems need it
-    if ((d->prec == PINV_PREC_MIXED_BF16 || d->prec == PINV_PREC_FP32) && d->m != d->n &&
+    if ((d->prec == PINV_PREC_MIXED_BF16 || d->prec == PINV_PREC_FP32 || d->prec == PINV_PREC_BF16_FP32) &&
+        d->m != d->n &&
         d->finish != PINV_FINISH_CLEAN)
         return PINV_ERR_ARG;
     return PINV_OK;
@@ -454,6 +475,7 @@ int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
     if (rc) return rc;
     carve(c, drazin, host, check, d->prec);
     c.prec_k = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;
+    c.symmetric = iterates_symmetric(d);
     if (host) {
         CK(cudaMemcpy2DAsync(c.Ad, sizeof(double) * d->n, d->A, sizeof(double) * d->lda,
                              sizeof(double) * d->n, d->m, cudaMemcpyHostToDevice, st));
@@ -548,14 +570,17 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
     bool stabilise = false;
     int status = PINV_ERR_MAXITER, reason = 2;
     // precision of the final (FP64-class) products: native FP64 or the tensor-core engine
-    const int fp64_class = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;
+    // the precision of the last loops (and of the stop rule): native FP64, the
+    // FP64-class slice engine, or FP32-class for the FP32-finished schedule
+    const int fp64_class = d->prec == PINV_PREC_FP64 ? 0 : (d->prec == PINV_PREC_BF16_FP32 ? TC_FP32 : TC_FP64);
     // Precision schedule: the level only rises.  BF16 serves the growth phase
     // (step > 0.5: the iterate is still being scaled up and any error is
     // corrected later -- for problems without a null block); FP32-class
     // products then run until the step falls below 1e-4 or stops falling
     // (their noise floor); every later loop, the stop rule and the switch to
     // the stabilised loop use FP64-class products.
-    int level = d->prec == PINV_PREC_MIXED_BF16 ? TC_BF16 : (d->prec == PINV_PREC_FP32 ? TC_FP32 : fp64_class);
+    int level = (d->prec == PINV_PREC_MIXED_BF16 || d->prec == PINV_PREC_BF16_FP32)
+                    ? TC_BF16 : (d->prec == PINV_PREC_FP32 ? TC_FP32 : fp64_class);
     int prev_prec = -1;
     double prev2 = INFINITY;
     for (int k = 0; k < max_iter; ++k) {
@@ -605,7 +630,7 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         info->iters = k + 1;
     }
     info->stop_reason = reason;
-    c.prec_k = fp64_class;
+    c.prec_k = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;   // the finish is FP64-class
     if (status == PINV_OK && d->finish == PINV_FINISH_CLEAN) {
         // projection, then one FP64 loop (Theorems 6.2 / 7.1: the blocks the
         // loop does not contract are removed, the range block is re-contracted)
@@ -718,8 +743,9 @@ int group_begin(Group& G) {
     const pinv_desc& d0 = G.d[0];
     G.batch = (int)G.d.size();
     G.prec = d0.prec;
-    G.fp64_class = d0.prec == PINV_PREC_FP64 ? 0 : TC_FP64;
-    G.level = d0.prec == PINV_PREC_MIXED_BF16 ? TC_BF16 : (d0.prec == PINV_PREC_FP32 ? TC_FP32 : G.fp64_class);
+    G.fp64_class = d0.prec == PINV_PREC_FP64 ? 0 : (d0.prec == PINV_PREC_BF16_FP32 ? TC_FP32 : TC_FP64);
+    G.level = (d0.prec == PINV_PREC_MIXED_BF16 || d0.prec == PINV_PREC_BF16_FP32)
+                  ? TC_BF16 : (d0.prec == PINV_PREC_FP32 ? TC_FP32 : G.fp64_class);
     G.left = G.M > G.N;
     G.finish = d0.finish == PINV_FINISH_CLEAN;
     G.max_iter = 0;
@@ -769,6 +795,7 @@ int group_begin(Group& G) {
     c.c = pm_coefficients();
     c.batch = G.batch; c.stride = slab;
     c.yield_sms = G.serving;
+    c.symmetric = iterates_symmetric(&d0);
     {
         auto al = [](size_t x) { return (x + 31) & ~size_t(31); };
         const size_t s2 = (size_t)c.s * c.s, big = std::max(G.M, G.N);
@@ -928,7 +955,7 @@ int group_finish(Group& G) {
     std::memcpy(G.pinned, mask.data(), sizeof(int) * G.batch);
     CK(cudaMemcpyAsync(G.dmask, G.pinned, sizeof(int) * G.batch, cudaMemcpyHostToDevice, G.st));
     scatter_in(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[0], G.M, c.stride, G.st);
-    c.prec_k = G.fp64_class;
+    c.prec_k = G.prec == PINV_PREC_FP64 ? 0 : TC_FP64;   // the finish is FP64-class
     pinv_desc d0 = G.d[0];
     cleanup_f64(c, &d0, c.X[0], c.X[1]);
     if (pm_loop_f64(c, c.X[1], c.X[0]) < 0) return G.err = PINV_ERR_CUDA;
@@ -1226,7 +1253,7 @@ int pinv_step(pinv_handle* h, int m, int n, const double* A, int lda, const doub
     if (!h || m < 1 || n < 1 || !A || !X_in || !X_out || lda < n || ldx != m || X_in == X_out)
         return PINV_ERR_ARG;
     if (prec != PINV_PREC_FP64 && prec != PINV_PREC_MIXED_BF16 && prec != PINV_PREC_FP32 &&
-        prec != PINV_PREC_FP64_TC)
+        prec != PINV_PREC_FP64_TC && prec != PINV_PREC_BF16_FP32)
         return PINV_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
     pinv_desc d{};
@@ -1236,7 +1263,8 @@ int pinv_step(pinv_handle* h, int m, int n, const double* A, int lda, const doub
     cudaStream_t st = (cudaStream_t)stream;
     int rc = setup_context(h, &d, st, c);
     if (rc) return rc;
-    c.prec_k = prec == PINV_PREC_FP64 ? 0 : (prec == PINV_PREC_MIXED_BF16 ? TC_BF16 : (prec == PINV_PREC_FP32 ? TC_FP32 : TC_FP64));
+    c.prec_k = prec == PINV_PREC_FP64 ? 0 : (prec == PINV_PREC_MIXED_BF16 ? TC_BF16 :
+               ((prec == PINV_PREC_FP32 || prec == PINV_PREC_BF16_FP32) ? TC_FP32 : TC_FP64));
     int parts = pm_loop_f64(c, X_in, stabilized ? c.X[2] : X_out);
     if (stabilized) parts = stabilise_f64(c, c.X[2], X_in, X_out);
     if (parts < 0) return PINV_ERR_CUDA;
@@ -1254,11 +1282,12 @@ int pinv_gemm(pinv_handle* h, int M, int N, int K, const double* A, int lda, int
     if (!h || M < 1 || N < 1 || K < 1 || !A || !B || !C || ldc < N) return PINV_ERR_ARG;
     if (lda < (trans_a ? M : K) || ldb < (trans_b ? K : N)) return PINV_ERR_ARG;
     if (prec != PINV_PREC_FP64 && prec != PINV_PREC_MIXED_BF16 && prec != PINV_PREC_FP32 &&
-        prec != PINV_PREC_FP64_TC)
+        prec != PINV_PREC_FP64_TC && prec != PINV_PREC_BF16_FP32)
         return PINV_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
     cudaStream_t st = (cudaStream_t)stream;
-    const int pk = prec == PINV_PREC_FP64 ? 0 : (prec == PINV_PREC_MIXED_BF16 ? TC_BF16 : (prec == PINV_PREC_FP32 ? TC_FP32 : TC_FP64));
+    const int pk = prec == PINV_PREC_FP64 ? 0 : (prec == PINV_PREC_MIXED_BF16 ? TC_BF16 :
+                   ((prec == PINV_PREC_FP32 || prec == PINV_PREC_BF16_FP32) ? TC_FP32 : TC_FP64));
     Epilogue e = epi1(term(C, ldc, 1));
     if (pk == 0) {
         if (gemm_f64(M, N, K, A, lda, trans_a != 0, B, ldb, trans_b != 0, e, st) < 0) return PINV_ERR_CUDA;

@@ -13,7 +13,7 @@
 // only rounding is the FP64 sum of the slice products and the truncation of
 // slices beyond s + t > L.
 //   FP64-class: 9 slices per operand, s + t <= 8 (45 products)
-//   FP32-class: 4 slices, s + t <= 3 (10 products)
+//   FP32-class: 5 slices, s + t <= 4 (15 products, about 30 bits)
 //   BF16:       1 slice rounded to nearest (no grid), one product
 //
 // Kernel layout (one persistent CTA per SM, 6 warps):
@@ -65,6 +65,7 @@ struct TcParams {
     int S;                // slices per operand (tensor-map slice index = instance * S + s)
     int batch;            // instances; instance b uses every FP64 matrix at +b*stride
     long long stride;
+    int sym;              // output symmetric (M == N): only tiles with nb >= mb, mirrored
     int tiles_m, tiles_n;
     Epilogue epi;
     int* err;             // device error word (0 = ok)
@@ -73,6 +74,15 @@ struct TcParams {
     const unsigned long long* rmax;
     const unsigned long long* cmax;
 };
+
+// Tile t of one instance -> (mb, nb).  Symmetric mode enumerates the upper
+// triangle row by row: row mb holds tiles nb = mb .. tm-1.
+__device__ __forceinline__ void tile_coords(int t, int tm, int sym, int& mb, int& nb) {
+    if (!sym) { mb = t % tm; nb = t / tm; return; }
+    mb = 0;
+    while (t >= tm - mb) { t -= tm - mb; ++mb; }
+    nb = mb + t;
+}
 
 __device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i) {
     int e = 0;
@@ -190,7 +200,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_per = P.tiles_m * P.tiles_n;
+    const int tiles_per = P.sym ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;
     const int ntiles = tiles_per * P.batch;
     const int kchunks = (P.K + P.chunk - 1) / P.chunk;
     const int units = P.npairs * kchunks;
@@ -219,7 +229,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             uint32_t phase = 0;
             for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
                 const int b = tile / tiles_per, tt = tile % tiles_per;
-                const int m0 = (tt % P.tiles_m) * BM, n0 = (tt / P.tiles_m) * BN;
+                int mb, nb;
+                tile_coords(tt, P.tiles_m, P.sym, mb, nb);
+                const int m0 = mb * BM, n0 = nb * BN;
                 for (int u = 0; u < units && !*abort_flag; ++u) {
                     const int pr = u / kchunks, ch = u % kchunks;
                     const int k_begin = ch * P.chunk;
@@ -294,7 +306,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         uint32_t accphase[2] = {0, 0};
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const int b = tile / tiles_per, tt = tile % tiles_per;
-            const int m0 = (tt % P.tiles_m) * BM, n0 = (tt / P.tiles_m) * BN;
+            int mb, nb;
+            tile_coords(tt, P.tiles_m, P.sym, mb, nb);
+            const int m0 = mb * BM, n0 = nb * BN;
+            const bool mirror = P.sym && mb != nb;   // also write the transposed tile
             Epilogue E = P.epi;   // instance b's matrices
             const long long off = (long long)b * P.stride;
             if (E.s1) E.s1 += off;
@@ -383,7 +398,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                             if (o < E.nout) {
                                 const EpiTerm& t = E.o[o];
                                 const double v = t.a_acc * a + t.a_s1 * v1 + t.a_s2 * v2 + t.a_id * id;
-                                if (t.out) t.out[(size_t)row * t.ld + col] = v;
+                                if (t.out) {
+                                    t.out[(size_t)row * t.ld + col] = v;
+                                    if (mirror) t.out[(size_t)col * t.ld + row] = v;   // warp-coalesced
+                                }
                                 if (o == 0) { const double dd = v - v1; sd += dd * dd; sx += v1 * v1; }
                             }
                         }
@@ -567,7 +585,7 @@ int num_sms() {
 TcMode tc_mode(int prec) {
     TcMode m;
     if (prec == TC_BF16) { m.S = 1; m.L = 0; m.exact = 0; }
-    else if (prec == TC_FP32) { m.S = 4; m.L = 3; m.exact = 1; }
+    else if (prec == TC_FP32) { m.S = 5; m.L = 4; m.exact = 1; }   // ~30 bits: FP32-class or better
     else { m.S = 9; m.L = 8; m.exact = 1; }
     return m;
 }
@@ -592,7 +610,8 @@ size_t tc_smem_bytes() { return STAGES * STAGE_BYTES + 1024 + 256; }
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb, bool transB,
             const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err, cudaStream_t st,
             int* kernels, cudaEvent_t ev_begin, cudaEvent_t ev_end, int batch, long long stride,
-            bool one_tile_per_cta) {
+            bool one_tile_per_cta, bool sym_out) {
+    if (sym_out && (M != N || epi.partials)) return -1;
     const int Kp = ((K + 7) / 8) * 8;
     if (batch < 1 || tc_workspace_bytes(M, N, K, mode, batch) > ws_bytes) return -1;
     auto al = [](size_t x) { return (x + 1023) & ~size_t(1023); };
@@ -637,6 +656,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
             if (t >= 0 && t < mode.S) { P.pair_s[P.npairs] = s; P.pair_t[P.npairs] = t; ++P.npairs; }
         }
     P.exact = mode.exact;
+    P.sym = sym_out ? 1 : 0;
     P.S = mode.S;
     P.batch = batch;
     P.stride = stride;
@@ -647,7 +667,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.err = err;
     P.rmax = mode.exact ? ea : nullptr;
     P.cmax = mode.exact ? eb : nullptr;
-    const int tiles = P.tiles_m * P.tiles_n;   // per instance
+    const int tiles = sym_out ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;   // per instance
     const int all_tiles = tiles * batch;
     // persistent (one CTA per SM walking the tiles) unless the caller wants the
     // SMs released after every tile (so higher-priority streams get in)

@@ -27,10 +27,13 @@ size_t tc_smem_bytes();
 // number of kernels launched to *kernels.  batch > 1: instance b uses every
 // FP64 matrix (operands, side inputs, outputs) at +b*stride elements.  Returns
 // the count of pair partials per instance (8 per 128 x 128 output tile, the
-// instances one after another) or -1.
+// instances one after another) or -1.  sym_out (M == N, no partials): the
+// caller guarantees op(A) op(B) is symmetric; only the upper-triangle tiles are
+// computed and each off-diagonal tile is also written transposed.
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb,
             bool transB, const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err,
             cudaStream_t st, int* kernels, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr,
-            int batch = 1, long long stride = 0, bool one_tile_per_cta = false);
+            int batch = 1, long long stride = 0, bool one_tile_per_cta = false,
+            bool sym_out = false);
 
 }  // namespace pinv

@@ -50,7 +50,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix(cuda, prec):
     h = Handle(0)
     sizes = [64, 256, 128, 64, 300, 128, 64]
     reqs = [make_request(n, seed=i) for i, n in enumerate(sizes)]
-    kw = dict(kind="outer_g", tol=1e-12, prec=prec)
+    kw = dict(kind="outer_g", tol=1e-12, prec=prec, symmetric=True)
     ids = []
     for j, (s, A, G, X) in enumerate(reqs):
         ids.append(h.submit(A, X, G=G, alpha=1.0 / s.lam.max(), **kw))

@@ -4,8 +4,9 @@ pinv_solve) against extended-precision references and the oracle.
 Error bounds, per element, relative to (|op(A)| |op(B)|)_ij:
 * FP64-class (9 exact slices, 45 products): 4e-16 (native FP64 rounding is
   about K u / sqrt(K) ~ 1e-16 here; the dropped slice products are 2^-60);
-* FP32-class (4 slices, 10 products): 5e-7 (the five dropped products with
-  s + t = 4 are each up to 2^-30 of the row/column maxima);
+* FP32-class (5 slices, 15 products): 5e-9 (the dropped products with
+  s + t = 5 are each up to 2^-36 of the row/column maxima; the slices hold
+  30 bits);
 * BF16 (one round-to-nearest slice, FP32 accumulation): 2^-7.
 """
 
@@ -19,7 +20,7 @@ from tests.helpers import pinv_closed_form, rel
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
-BOUND = {"fp64_tc": 4e-16, "fp32": 5e-7, "mixed_bf16": 2.0 ** -7}
+BOUND = {"fp64_tc": 4e-16, "fp32": 5e-9, "mixed_bf16": 2.0 ** -7}
 
 
 @pytest.fixture(scope="module")
@@ -149,3 +150,29 @@ def test_low_precision_on_rectangular_requires_the_finish(handle):
         with pytest.raises(PinvError) as e:
             handle.solve(dev(w.A), alpha=1.0, tol=1e-12, prec=prec)
         assert e.value.code == -1
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_tc"])
+def test_symmetric_hint_matches_full_products(handle, prec):
+    """A symmetric A with G = I: the symmetric-output products (upper tiles,
+    mirrored) give the same inverse as the full products."""
+    s = W.spd(300, 1e-3, 1.0, seed=9)
+    G = dev(np.eye(300))
+    alpha = 1.0 / s.lam.max()
+    Xf, i1 = handle.solve(dev(s.A), kind="outer_g", G=G, alpha=alpha, tol=1e-12, prec=prec)
+    Xs, i2 = handle.solve(dev(s.A), kind="outer_g", G=G, alpha=alpha, tol=1e-12, prec=prec, symmetric=True)
+    assert i1["status"] == 0 and i2["status"] == 0
+    assert rel(Xs.cpu().numpy(), Xf.cpu().numpy()) <= 1e-11
+    assert rel(Xs.cpu().numpy(), (s.Q / s.lam) @ s.Q.T) <= 1e-9
+
+
+def test_fp32_finished_schedule(handle):
+    """PINV_PREC_BF16_FP32: BF16 growth loops then FP32-class to the end; the
+    result carries FP32-class accuracy (u_fp32 kappa) on a nonsingular problem."""
+    s = W.spd(400, 1e-3, 1.0, seed=12)
+    X, info = handle.solve(dev(s.A), kind="outer_g", G=dev(np.eye(400)), alpha=1.0, tol=1e-12,
+                           prec="bf16_fp32", symmetric=True)
+    assert info["status"] == 0
+    assert set(info["precision"]) <= {1, 3} and info["precision"][-1] == 3
+    err = rel(X.cpu().numpy(), (s.Q / s.lam) @ s.Q.T)
+    assert err <= 1e-4
