@@ -131,6 +131,23 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The slowest rank's value (the timed region ends when every replica has
+    finished).  dist: torch.distributed or None for a single process."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_throughput(world: int, steps: int, max_ms: float) -> float:
+    """Whole-job throughput of independent replicas: every rank solves `steps`
+    problems, all of them in the max-over-ranks time."""
+    return world * steps / (max_ms * 1e-3)
+
+
 def workload():
     from paper_1604_07893_gb300 import workloads as W
     w = W.rectangular(M, N, RANK, 1.0, S_MIN, seed=SEED)
@@ -233,12 +250,8 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    total_ms = t_all0.elapsed_time(t_all1)
+    total_ms = max_over_ranks(t_all0.elapsed_time(t_all1), dist, dev)
     per_step = [a.elapsed_time(b) for a, b in ev]
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     clocks = clk.summary()
 
     # accuracy of the last timed result (untimed)
@@ -297,7 +310,7 @@ def run_ours(args):
     traffic = TRAFFIC_BYTES.get(args.prec)
     if traffic is not None and gemm_launches:
         traffic = traffic * (gemm_flops / gemm_launches) / TRAFFIC_REF_FLOPS   # per mean launch
-    value = world * args.steps / (total_ms * 1e-3)
+    value = replica_throughput(world, args.steps, total_ms)
     sorted_ms = sorted(per_step)
     p50 = statistics.median(per_step)
     p99 = sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(0.99 * len(sorted_ms))) - 1)]
