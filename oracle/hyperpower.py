@@ -233,11 +233,12 @@ def cleanup_drazin(A: np.ndarray, X: np.ndarray, l: int) -> np.ndarray:
 
 STOP_REL_FRO = 0   # ||X_{k+1} - X_k||_F / ||X_k||_F < tol
 STOP_PAPER = 1     # ||X_{k+1} - X_k||_F / (18^k alpha) < tol   (Eq. stopreliable)
+STOP_ORDER18 = 2   # relative step < tol (tol = delta, e.g. 1e-2): keep X_{k+1}, no further loop
 
 
 def stop_measure(Xn: np.ndarray, X: np.ndarray, k: int, alpha: float, mode: int) -> float:
     d = float(fro(Xn - X))
-    if mode == STOP_REL_FRO:
+    if mode in (STOP_REL_FRO, STOP_ORDER18):
         nx = float(fro(X))
         return d / nx if nx > 0 else math.inf
     if mode == STOP_PAPER:
@@ -263,7 +264,11 @@ def solve(A: np.ndarray, X0: np.ndarray, tol: float = 1e-12, stop: int = STOP_RE
 
     Loop k computes X_{k+1} from X_k with the naive order-p step (plus X A X
     once the stabilised variant is switched on) and the stop measure e_k.
-    * e_k < tol: keep X_{k+1}, status 'converged'.
+    * e_k < tol: keep X_{k+1}, status 'converged'.  With STOP_ORDER18, tol is a
+      threshold delta with delta^18 below the FP64 unit roundoff: by Theorem
+      3.1 (F_{k+1} = F_k^18) the loop that produced a step below delta has
+      already brought the error to the rounding floor, so no loop is spent
+      observing the floor (reading of the order-18 contraction).
     * Plain loops, reading of the first remark closing Section 6: once the
       previous step e_{k-1} was below ``floor_guard`` (the converged regime,
       where order 18 makes e_k of order e_{k-1}^18), a step with

@@ -18,7 +18,7 @@ PINV_OK, PINV_PENDING = 0, 1
 ERRORS = {-1: "PINV_ERR_ARG", -2: "PINV_ERR_BUDGET", -3: "PINV_ERR_NONFINITE", -4: "PINV_ERR_DIVERGED",
           -5: "PINV_ERR_MAXITER", -6: "PINV_ERR_TIMEOUT", -7: "PINV_ERR_CUDA", -8: "PINV_ERR_UNKNOWN_ID"}
 KIND = {"moore_penrose": 0, "drazin": 1, "outer_g": 2}
-STOP = {"rel_fro": 0, "paper": 1}
+STOP = {"rel_fro": 0, "paper": 1, "order18": 2}
 PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3, "fp64_tc": 4, "bf16_fp32": 5}
 VARIANT = {"plain": 0, "stabilized": 1}
 FINISH = {None: 0, "none": 0, "clean": 1}

@@ -442,7 +442,8 @@ int validate(const pinv_desc* d) {
     if (d->kind < PINV_MOORE_PENROSE || d->kind > PINV_OUTER_G) return PINV_ERR_ARG;
     if (!(d->alpha >= 0.0) || !std::isfinite(d->alpha)) return PINV_ERR_ARG;
     if (!(d->tol >= 0.0)) return PINV_ERR_ARG;
-    if (d->stop != PINV_STOP_REL_FRO && d->stop != PINV_STOP_PAPER) return PINV_ERR_ARG;
+    if (d->stop != PINV_STOP_REL_FRO && d->stop != PINV_STOP_PAPER && d->stop != PINV_STOP_ORDER18)
+        return PINV_ERR_ARG;
     if (d->max_iter < 0 || d->max_iter > PINV_HISTORY) return PINV_ERR_ARG;
     if (d->prec != PINV_PREC_FP64 && d->prec != PINV_PREC_MIXED_BF16 && d->prec != PINV_PREC_FP32 &&
         d->prec != PINV_PREC_FP64_TC && d->prec != PINV_PREC_BF16_FP32)
@@ -611,7 +612,9 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
             info->precision[k] = (signed char)(prec_k == 0 ? 0 : prec_k);
         }
         if (!std::isfinite(e)) { status = PINV_ERR_NONFINITE; info->iters = k; break; }
-        if (e < d->tol) { status = PINV_OK; reason = 0; cur ^= 1; info->iters = k + 1; info->rel_step = e; break; }
+        // ORDER18: the threshold is trusted in final-precision loops only
+        const bool tol_ok = d->stop != PINV_STOP_ORDER18 || prec_k == fp64_class;
+        if (e < d->tol && tol_ok) { status = PINV_OK; reason = 0; cur ^= 1; info->iters = k + 1; info->rel_step = e; break; }
         // the stop rule compares two consecutive FP64-class loops only: the first
         // FP64-class step after lower-precision loops removes their noise
         const bool final_class = prec_k == fp64_class && prev_prec == fp64_class;
@@ -907,7 +910,9 @@ int group_complete(Group& G) {
         const int maxit = x.max_iter ? x.max_iter : 100;
         int stop = 0;   // 1: keep X_k (buffer cur); 2: keep X_{k+1} (buffer cur^1)
         if (!std::isfinite(e)) { I.status = PINV_ERR_NONFINITE; stop = 1; }
-        else if (e < x.tol) { I.status = PINV_OK; I.stop_reason = 0; I.iters = k + 1; I.rel_step = e; stop = 2; }
+        else if (e < x.tol && (x.stop != PINV_STOP_ORDER18 || prec_k == G.fp64_class)) {
+            I.status = PINV_OK; I.stop_reason = 0; I.iters = k + 1; I.rel_step = e; stop = 2;
+        }
         else {
             const double pv = G.prev[b];
             const bool stalled = G.stabilise ? (e >= pv) : (pv < 1e-3 && e >= pv * pv);

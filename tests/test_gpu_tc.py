@@ -176,3 +176,16 @@ def test_fp32_finished_schedule(handle):
     assert set(info["precision"]) <= {1, 3} and info["precision"][-1] == 3
     err = rel(X.cpu().numpy(), (s.Q / s.lam) @ s.Q.T)
     assert err <= 1e-4
+
+
+def test_order18_stop_parity(handle):
+    w = W.rectangular(512, 384, 288, 1.0, 1e-4, seed=1)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    kw = dict(tol=1e-2, alpha=alpha, variant="stabilised", switch_tol=0.5, finish="moore_penrose")
+    ref, oinfo = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), stop=H.STOP_ORDER18, **kw)
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", variant="stabilized",
+                           switch_tol=0.5, finish="clean", prec="fp64_tc", check=True)
+    assert info["iters"] == oinfo.iters and info["stabilized_loops"] == oinfo.stabilised_loops
+    assert rel(X.cpu().numpy(), ref) <= 1e-9
+    assert rel(X.cpu().numpy(), pinv_closed_form(w)) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9

@@ -381,3 +381,18 @@ def test_nonfinite_input_stops():
     A[0, 0] = np.nan
     X, info = H.solve(A, H.x0_moore_penrose(A, 0.1), alpha=0.1)
     assert info.status == "nonfinite"
+
+
+def test_order18_stop_reaches_the_same_accuracy_in_fewer_loops():
+    """Theorem 3.1 (F_{k+1} = F_k^18): after a loop whose step is below 1e-2 the
+    iterate is at the rounding floor, so stopping there loses nothing."""
+    w = W.rectangular(256, 192, 144, 1.0, 1e-4, seed=12)
+    ref = pinv_closed_form(w)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    Xa, ia = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha,
+                     variant="stabilised", finish="moore_penrose")
+    Xb, ib = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-2, stop=H.STOP_ORDER18, alpha=alpha,
+                     variant="stabilised", switch_tol=0.5, finish="moore_penrose")
+    assert ib.loops_run < ia.loops_run and ib.stabilised_loops >= 1
+    assert rel(Xb, ref) < 3e-12 and rel(Xa, ref) < 3e-12
+    assert H.penrose_residuals(w.A, Xb).max() < 3e-10
