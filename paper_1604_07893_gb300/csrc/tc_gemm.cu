@@ -150,6 +150,31 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
 }
+// Multicast variant: the tile lands at the same shared-memory offset in every
+// CTA of `mask` and completes bytes on the barrier at the same offset in each.
+__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                               int c1, int c2, uint16_t mask) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
+        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+            smem_u32(bar)),
+        "h"(mask)
+        : "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
                      smem_u32(bar))
@@ -187,6 +212,12 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 }
 
 // ------------------------------------------------------------------ the kernel
+// MC = false: one CTA per tile.  MC = true: clusters of two CTAs on vertically
+// adjacent tiles (m-blocks 2i, 2i+1, same n-block): each CTA loads its own A
+// tile and half of the shared B tile, multicast to both, so every CTA reads 24
+// instead of 32 KiB from L2 per stage; a stage is released only when both CTAs'
+// MMAs are done with it (the commit is multicast to both empty barriers).
+template <bool MC>
 __global__ void __launch_bounds__(THREADS, 1)
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                const __grid_constant__ TcParams P) {
@@ -200,13 +231,26 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int tiles_per = P.sym ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;
+    // Work items: tiles (MC = false) or vertical tile pairs (MC = true, one per cluster).
+    const int tiles_m2 = (P.tiles_m + 1) / 2;
+    const int tiles_per = MC ? tiles_m2 * P.tiles_n
+                             : (P.sym ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n);
     const int ntiles = tiles_per * P.batch;
+    const uint32_t crank = MC ? cluster_rank() : 0;
+    const int work0 = MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
+    const int wstep = MC ? (int)(gridDim.x >> 1) : (int)gridDim.x;
+    // tile of work item w for this CTA: instance b, blocks (mb, nb)
+    auto locate = [&](int w, int& b, int& mb, int& nb) {
+        b = w / tiles_per;
+        const int tt = w % tiles_per;
+        if (MC) { mb = 2 * (tt % tiles_m2) + (int)crank; nb = tt / tiles_m2; }
+        else tile_coords(tt, P.tiles_m, P.sym, mb, nb);
+    };
     const int kchunks = (P.K + P.chunk - 1) / P.chunk;
     const int units = P.npairs * kchunks;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], MC ? 2 : 1); }
         for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 32 * EPI_WARPS); }
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -219,6 +263,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     }
     tc_fence_before();
     __syncthreads();
+    if (MC) cluster_sync();   // the peer's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
@@ -227,10 +272,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
-                const int b = tile / tiles_per, tt = tile % tiles_per;
-                int mb, nb;
-                tile_coords(tt, P.tiles_m, P.sym, mb, nb);
+            for (int tile = work0; tile < ntiles && !*abort_flag; tile += wstep) {
+                int b, mb, nb;
+                locate(tile, b, mb, nb);
                 const int m0 = mb * BM, n0 = nb * BN;
                 for (int u = 0; u < units && !*abort_flag; ++u) {
                     const int pr = u / kchunks, ch = u % kchunks;
@@ -243,7 +287,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                         uint8_t* sa = smem + stage * STAGE_BYTES;
                         mbar_expect_tx(&full[stage], STAGE_BYTES);
                         tma_load_3d(sa, &mapA, &full[stage], k, m0, b * P.S + P.pair_s[pr]);
-                        tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, b * P.S + P.pair_t[pr]);
+                        if (MC)   // my half of the B tile, to both CTAs (8 KiB = 64 rows)
+                            tma_load_3d_mc(sa + A_TILE_BYTES + crank * (B_TILE_BYTES / 2), &mapB, &full[stage], k,
+                                           n0 + (int)crank * (BN / 2), b * P.S + P.pair_t[pr], (uint16_t)3);
+                        else
+                            tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, b * P.S + P.pair_t[pr]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                 }
@@ -257,7 +305,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             uint32_t phase = 0;
             int buf = 0;
             uint32_t accphase[2] = {0, 0};
-            for (int tile = blockIdx.x; tile < ntiles && !*abort_flag; tile += gridDim.x) {
+            for (int tile = work0; tile < ntiles && !*abort_flag; tile += wstep) {
                 for (int u = 0; u < units && !*abort_flag; ++u) {
                     const int ch = u % kchunks;
                     const int k_begin = ch * P.chunk;
@@ -280,7 +328,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                             mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc, acc);
                             acc = 1;
                         }
-                        mma_commit(&empty[stage]);
+                        if (MC) mma_commit_mc(&empty[stage], (uint16_t)3);   // release in both CTAs
+                        else mma_commit(&empty[stage]);
                         if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                     mma_commit(&accf[buf]);
@@ -304,11 +353,14 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         const uint32_t acc64 = lane_base + 2 * BN + 2 * half * EPI_COLS;
         int buf = 0;
         uint32_t accphase[2] = {0, 0};
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-            const int b = tile / tiles_per, tt = tile % tiles_per;
-            int mb, nb;
-            tile_coords(tt, P.tiles_m, P.sym, mb, nb);
+        for (int tile = work0; tile < ntiles; tile += wstep) {
+            int b, mb, nb;
+            locate(tile, b, mb, nb);
             const int m0 = mb * BM, n0 = nb * BN;
+            // slot of the tile's partials (instance-major, nb-major then mb); an
+            // MC partner past the last m-block computes zeros and writes none
+            const int slot = b * P.tiles_m * P.tiles_n + nb * P.tiles_m + mb;
+            const bool real_tile = mb < P.tiles_m;
             const bool mirror = P.sym && mb != nb;   // also write the transposed tile
             Epilogue E = P.epi;   // instance b's matrices
             const long long off = (long long)b * P.stride;
@@ -414,9 +466,9 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     sd += __shfl_xor_sync(0xffffffffu, sd, off);
                     sx += __shfl_xor_sync(0xffffffffu, sx, off);
                 }
-                if (lane == 0) {
-                    E.partials[2 * (EPI_WARPS * tile + ew)] = sd;
-                    E.partials[2 * (EPI_WARPS * tile + ew) + 1] = sx;
+                if (lane == 0 && real_tile) {
+                    E.partials[2 * (EPI_WARPS * slot + ew)] = sd;
+                    E.partials[2 * (EPI_WARPS * slot + ew) + 1] = sx;
                 }
             }
         }
@@ -425,6 +477,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     __syncwarp();
     tc_fence_before();
     __syncthreads();
+    if (MC) cluster_sync();   // no CTA leaves while its peer may still write into it
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
@@ -643,8 +696,12 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
                                          mode.S, mode.exact, sb, stride);
         *kernels += 2;
     }
+    // clusters of two when there are at least two m-blocks to pair (not in symmetric mode)
+    const int tiles_m_ = (M + BM - 1) / BM;
+    const bool mc = !sym_out && tiles_m_ >= 2;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, sa, batch * mode.S, M, Kp, BM) || !make_map(&mb, sb, batch * mode.S, N, Kp, BN))
+    if (!make_map(&ma, sa, batch * mode.S, M, Kp, BM) ||
+        !make_map(&mb, sb, batch * mode.S, N, Kp, mc ? BN / 2 : BN))
         return -1;
 
     TcParams P;
@@ -668,17 +725,37 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.rmax = mode.exact ? ea : nullptr;
     P.cmax = mode.exact ? eb : nullptr;
     const int tiles = sym_out ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;   // per instance
-    const int all_tiles = tiles * batch;
-    // persistent (one CTA per SM walking the tiles) unless the caller wants the
-    // SMs released after every tile (so higher-priority streams get in)
-    const int grid = (one_tile_per_cta || all_tiles < num_sms()) ? all_tiles : num_sms();
     static bool attr = false;
     if (!attr) {
-        cudaFuncSetAttribute(tc_gemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+        cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+        cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
         attr = true;
     }
     if (ev_begin) cudaEventRecord(ev_begin, st);
-    tc_gemm_kernel<<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+    if (mc) {
+        // one work item per cluster: a vertical pair of tiles
+        const int items = ((P.tiles_m + 1) / 2) * P.tiles_n * batch;
+        const int clusters = (one_tile_per_cta || items < num_sms() / 2) ? items : num_sms() / 2;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(2 * clusters);
+        cfg.blockDim = dim3(THREADS);
+        cfg.dynamicSmemBytes = tc_smem_bytes();
+        cfg.stream = st;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = 2;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        if (cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true>, ma, mb, P) != cudaSuccess) return -1;
+    } else {
+        const int all_tiles = tiles * batch;
+        // persistent (one CTA per SM walking the tiles) unless the caller wants
+        // the SMs released after every tile (so higher-priority streams get in)
+        const int grid = (one_tile_per_cta || all_tiles < num_sms()) ? all_tiles : num_sms();
+        tc_gemm_kernel<false><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+    }
     if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
