@@ -59,7 +59,12 @@ extern "C" {
 typedef enum {
     PINV_MOORE_PENROSE = 0,  /* G = A^T (Section 4; Theorem 6.2)                  */
     PINV_DRAZIN        = 1,  /* G = A^l, l = drazin_index >= ind(A) (Section 4)   */
-    PINV_OUTER_G       = 2   /* caller's G (n x m): A^(2)_{R(G),N(G)} (Thm 3.1)   */
+    PINV_OUTER_G       = 2,  /* caller's G (n x m): A^(2)_{R(G),N(G)} (Thm 3.1)   */
+    PINV_DRAZIN_NORMAL = 3   /* Drazin inverse from G = A^l (A^{2l+1})^T A^l: same
+                                range and null space as A^D, GA has a real
+                                nonnegative spectrum, so it converges whatever the
+                                eigenvalues of A; alpha = 0 gives
+                                1/sqrt(||GA||_1 ||GA||_inf)                          */
 } pinv_kind;
 
 typedef enum {

@@ -194,6 +194,21 @@ def x0_drazin(A: np.ndarray, l: int, alpha=None) -> np.ndarray:
     return alpha * Al
 
 
+def x0_drazin_normal(A: np.ndarray, l: int, alpha=None) -> np.ndarray:
+    """X0 = alpha G with G = A^l (A^{2l+1})^T A^l.  R(G) = R(A^l) and N(G) = N(A^l),
+    the range and null space of the Drazin inverse (Section 1.1 names A^D as the
+    outer inverse with those subspaces; Theorem 3.1 takes any such G), and GA
+    has a real nonnegative spectrum, so the iteration converges whatever the
+    eigenvalues of A (X0 = A^l / Tr(A^{l+1}) needs them in a sector).  alpha
+    defaults to 1 / sqrt(||GA||_1 ||GA||_inf) <= 1 / ||GA||_2."""
+    Al = matpow(A, l)
+    G = Al @ matpow(A, 2 * l + 1).T @ Al
+    if alpha is None:
+        GA = G @ A
+        alpha = 1.0 / math.sqrt(float(np.abs(GA).sum(axis=0).max()) * float(np.abs(GA).sum(axis=1).max()))
+    return alpha * G
+
+
 def alpha_pan_schreiber(sigma_1: float, sigma_r: float) -> float:
     """alpha = 2 / (sigma_1^2 + sigma_r^2) (Section 4), sigma_1 >= sigma_r > 0 the
     extreme nonzero singular values of A (reading of 'eigenvalues of GA' for

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(HERE, "libpinv.so")
 PINV_OK, PINV_PENDING = 0, 1
 ERRORS = {-1: "PINV_ERR_ARG", -2: "PINV_ERR_BUDGET", -3: "PINV_ERR_NONFINITE", -4: "PINV_ERR_DIVERGED",
           -5: "PINV_ERR_MAXITER", -6: "PINV_ERR_TIMEOUT", -7: "PINV_ERR_CUDA", -8: "PINV_ERR_UNKNOWN_ID"}
-KIND = {"moore_penrose": 0, "drazin": 1, "outer_g": 2}
+KIND = {"moore_penrose": 0, "drazin": 1, "outer_g": 2, "drazin_normal": 3}
 STOP = {"rel_fro": 0, "paper": 1, "order18": 2}
 PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3, "fp64_tc": 4, "bf16_fp32": 5}
 VARIANT = {"plain": 0, "stabilized": 1}

@@ -336,7 +336,7 @@ int stabilise_f64(Ctx& c, const double* Xh, const double* Xprev, double* Xout) {
 // A^l X^{2l+1} A^l (Drazin).  Xin -> Xout.
 void cleanup_f64(Ctx& c, const pinv_desc* d, const double* X, double* Xout) {
     const int s = c.s, m = c.m, n = c.n;
-    if (d->kind == PINV_DRAZIN) {
+    if (d->kind == PINV_DRAZIN || d->kind == PINV_DRAZIN_NORMAL) {
         const int l = d->drazin_index;
         double* V[2] = {c.sq[0], c.sq[1]};
         scale_copy(n, n, X, m, 1.0, V[0], n, c.st);
@@ -375,7 +375,7 @@ int residual_checks(Ctx& c, const pinv_desc* d, const double* X, pinv_info* info
     };
     gemm(c, m, m, n, c.A, c.lda, false, X, m, false, epi1(term(AX, m, 1)));
     gemm(c, n, n, m, X, m, false, c.A, c.lda, false, epi1(term(XA, n, 1)));
-    if (d->kind == PINV_DRAZIN) {
+    if (d->kind == PINV_DRAZIN || d->kind == PINV_DRAZIN_NORMAL) {
         const int l = d->drazin_index;
         // ||XAX - X|| / ||X||
         Epilogue e = epi1(term(nullptr, 0, 1), X, m);
@@ -437,9 +437,10 @@ int validate(const pinv_desc* d) {
     if (d->m < 1 || d->n < 1) return PINV_ERR_ARG;
     if (!d->A || !d->X) return PINV_ERR_ARG;
     if (d->lda < d->n || d->ldx < d->m) return PINV_ERR_ARG;
-    if (d->kind == PINV_DRAZIN && (d->m != d->n || d->drazin_index < 1)) return PINV_ERR_ARG;
+    if ((d->kind == PINV_DRAZIN || d->kind == PINV_DRAZIN_NORMAL) && (d->m != d->n || d->drazin_index < 1))
+        return PINV_ERR_ARG;
     if (d->kind == PINV_OUTER_G && (!d->G || d->ldg < d->m)) return PINV_ERR_ARG;
-    if (d->kind < PINV_MOORE_PENROSE || d->kind > PINV_OUTER_G) return PINV_ERR_ARG;
+    if (d->kind < PINV_MOORE_PENROSE || d->kind > PINV_DRAZIN_NORMAL) return PINV_ERR_ARG;
     if (!(d->alpha >= 0.0) || !std::isfinite(d->alpha)) return PINV_ERR_ARG;
     if (!(d->tol >= 0.0)) return PINV_ERR_ARG;
     if (d->stop != PINV_STOP_REL_FRO && d->stop != PINV_STOP_PAPER && d->stop != PINV_STOP_ORDER18)
@@ -468,7 +469,7 @@ int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
     c.left = d->m > d->n;  // residual on the smaller side; the paper's right form when m <= n
     c.s = c.left ? d->n : d->m;
     c.c = pm_coefficients();
-    const bool drazin = d->kind == PINV_DRAZIN;
+    const bool drazin = d->kind == PINV_DRAZIN || d->kind == PINV_DRAZIN_NORMAL;
     const bool host = d->host_buffers != 0;
     const bool check = d->check != 0 || d->finish == PINV_FINISH_CLEAN;
     size_t bytes = workspace_bytes(d->m, d->n, drazin, host, check, d->prec);
@@ -497,7 +498,7 @@ int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
 int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
     const int m = c.m, n = c.n;
     double a = d->alpha;
-    if (d->kind == PINV_DRAZIN) {
+    if (d->kind == PINV_DRAZIN || d->kind == PINV_DRAZIN_NORMAL) {
         const int l = d->drazin_index;
         // A^l by l - 1 products
         scale_copy(n, n, c.A, c.lda, 1.0, c.Al, n, c.st);
@@ -506,6 +507,29 @@ int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
             gemm(c, n, n, n, c.Al, n, false, c.A, c.lda, false, epi1(term(c.sq[0], n, 1)));
             scale_copy(n, n, c.sq[0], n, 1.0, c.Al, n, c.st);
             ++c.kernels;
+        }
+        if (d->kind == PINV_DRAZIN_NORMAL) {
+            // G = A^l (A^{2l+1})^T A^l: A^{l+1} = A^l A, A^{2l+1} = A^{l+1} A^l,
+            // W = (A^{2l+1})^T A^l, G = A^l W   (sq[0..2] as temporaries)
+            double *Al1 = c.sq[0], *A2 = c.sq[1], *Wm = c.sq[2];
+            gemm(c, n, n, n, c.Al, n, false, c.A, c.lda, false, epi1(term(Al1, n, 1)));
+            gemm(c, n, n, n, Al1, n, false, c.Al, n, false, epi1(term(A2, n, 1)));
+            gemm(c, n, n, n, A2, n, true, c.Al, n, false, epi1(term(Wm, n, 1)));
+            gemm(c, n, n, n, c.Al, n, false, Wm, n, false, epi1(term(c.X[1], m, 1)));   // G
+            if (a == 0.0) {   // 1 / sqrt(||GA||_1 ||GA||_inf) <= 1 / ||GA||_2
+                gemm(c, n, n, n, c.X[1], m, false, c.A, c.lda, false, epi1(term(A2, n, 1)));
+                norms_1_inf(n, n, A2, n, c.h->dsmall, c.red, c.st);
+                c.kernels += 4;
+                CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
+                CK(cudaStreamSynchronize(c.st));
+                const double pr = c.h->pinned[0] * c.h->pinned[1];
+                if (!(pr > 0.0) || !std::isfinite(pr)) return PINV_ERR_NONFINITE;
+                a = 1.0 / std::sqrt(pr);
+            }
+            scale_copy(n, n, c.X[1], m, a, c.X[0], m, c.st);
+            ++c.kernels;
+            *alpha = a;
+            return PINV_OK;
         }
         if (a == 0.0) {  // alpha = 1 / Tr(A^{l+1}) = 1 / sum_ij (A^l)_ij A_ji
             trace_of_product(n, c.Al, n, c.A, c.lda, c.h->dsmall, c.red, c.st);
@@ -1157,7 +1181,9 @@ int pinv_solve_batched(pinv_handle* h, int count, const pinv_desc* descs, void* 
     for (int i = 0; i < count; ++i) {
         int rc = validate(&descs[i]);
         if (rc) return rc;
-        if (descs[i].kind == PINV_DRAZIN || descs[i].host_buffers || descs[i].check) return PINV_ERR_ARG;
+        if (descs[i].kind == PINV_DRAZIN || descs[i].kind == PINV_DRAZIN_NORMAL || descs[i].host_buffers ||
+            descs[i].check)
+            return PINV_ERR_ARG;
     }
     // the caller's stream is ordered before the groups' streams
     cudaEvent_t ready;
@@ -1206,7 +1232,8 @@ int pinv_submit(pinv_handle* h, const pinv_desc* desc, uint64_t* id) {
     if (!h || !desc || !id) return PINV_ERR_ARG;
     int rc = validate(desc);
     if (rc) return rc;
-    if (desc->kind == PINV_DRAZIN || desc->host_buffers || desc->check) return PINV_ERR_ARG;
+    if (desc->kind == PINV_DRAZIN || desc->kind == PINV_DRAZIN_NORMAL || desc->host_buffers || desc->check)
+        return PINV_ERR_ARG;
     const size_t need = group_bytes(1, pad_to(desc->m, 64), pad_to(desc->n, 64), desc->prec,
                                     desc->finish == PINV_FINISH_CLEAN, desc->kind == PINV_OUTER_G);
     if (h->budget && need > h->budget) return PINV_ERR_BUDGET;

@@ -278,3 +278,18 @@ def test_full_size_rank_deficient_sampled_rows(handle):
     ref_rows = (w.V[rows] / w.s) @ w.U.T
     assert rel(Xh[rows], ref_rows) <= 1e-9
     assert max(info["penrose"]) <= 1e-9
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_tc"])
+def test_drazin_normal_on_the_full_annulus(handle, prec):
+    """Eigenvalues all around the annulus (where X0 = A^2/Tr(A^3) cannot
+    converge): G = A^l (A^{2l+1})^T A^l reaches the closed-form A^D."""
+    d = W.drazin_index2(256, 64, seed=2, sector=np.pi)
+    ref, oinfo = H.solve(d.A, H.x0_drazin_normal(d.A, 2), tol=1e-2, stop=H.STOP_ORDER18, alpha=1.0,
+                         finish="drazin", drazin_index=2)
+    X, info = handle.solve(dev(d.A), kind="drazin_normal", drazin_index=2, alpha=0.0, tol=1e-2,
+                           stop="order18", finish="clean", prec=prec, check=True)
+    assert info["status"] == 0
+    assert rel(host(X), drazin_closed_form(d)) < 1e-9
+    assert rel(host(X), ref) < 1e-9
+    assert max(info["drazin"]) < 1e-9

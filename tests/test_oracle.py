@@ -396,3 +396,14 @@ def test_order18_stop_reaches_the_same_accuracy_in_fewer_loops():
     assert ib.loops_run < ia.loops_run and ib.stabilised_loops >= 1
     assert rel(Xb, ref) < 3e-12 and rel(Xa, ref) < 3e-12
     assert H.penrose_residuals(w.A, Xb).max() < 3e-10
+
+
+def test_drazin_normal_initial_value_for_any_spectrum():
+    """Eigenvalues all around the annulus 0.5 <= |z| <= 2: Tr(A^3) is not a
+    usable scaling for A^2, but G = A^l (A^{2l+1})^T A^l (same range and null
+    space as A^D) converges to the closed-form Drazin inverse."""
+    d = W.drazin_index2(96, 24, seed=2, sector=np.pi)
+    X, info = H.solve(d.A, H.x0_drazin_normal(d.A, 2), tol=1e-2, stop=H.STOP_ORDER18, alpha=1.0)
+    assert info.status == "converged"
+    assert rel(X, drazin_closed_form(d)) < 1e-10
+    assert H.drazin_residuals(d.A, X, 2).max() < 1e-10
