@@ -52,10 +52,10 @@ WORKLOAD = "moore_penrose_rank_deficient_4096x3072_r2304"
 # kernel from the committed ncu summary under profiles/ (None until captured
 # for the current kernel).
 TRAFFIC_BYTES = {"fp64": None, "fp32": None, "mixed_bf16": None,
-                 # profiles/tc_gemm_kernel_fp64class_3072x3072x4096.md: 5.449 GB read + 75.8 MB
-                 # written for a 3072x3072x4096 launch; scaled to this workload's mean launch
-                 # by the FP64-equivalent flops it processes (see TRAFFIC_SCALE below)
-                 "fp64_tc": 5.449e9 + 75.8e6}
+                 # profiles/tc_gemm_kernel_fp64class_3072x3072x4096.md: 5.512 GB read + 82.7 MB
+                 # written for a 3072x3072x4096 launch of the current kernel; scaled to this
+                 # workload's mean launch by the FP64-equivalent flops it processes
+                 "fp64_tc": 5.512e9 + 82.7e6}
 TRAFFIC_REF_FLOPS = 2.0 * 3072 * 3072 * 4096   # the captured launch's 2MNK
 
 
