@@ -395,7 +395,10 @@ def run_mp64(args):
     h = Handle(0)
     st = torch.cuda.current_stream()
     out = {}
-    for prec in ("fp64_tc", "fp64"):
+    for key in ("fp64_tc", "autotuned"):
+        prec = "fp64_tc"
+        if key == "autotuned":   # the engine crossover, measured on this device, routes small products to DMMA
+            out["crossover"] = h.autotune()
         for _ in range(args.warmup):
             h.solve(A, X, alpha=alpha, tol=1e-12, prec=prec)
         lat = []
@@ -407,16 +410,16 @@ def run_mp64(args):
             torch.cuda.synchronize()
             lat.append(e0.elapsed_time(e1))
         err = float(np.linalg.norm(X.cpu().numpy() - (w.V / w.s) @ w.U.T) / np.linalg.norm((w.V / w.s) @ w.U.T))
-        out[prec] = {"value": 1e3 / statistics.mean(lat), "p50_ms": statistics.median(lat),
+        out[key] = {"value": 1e3 / statistics.mean(lat), "p50_ms": statistics.median(lat),
                      "p99_ms": _pct(lat, 0.99), "rel_err_vs_closed_form": err, "loops": info["iters"],
                      "kernels_per_solve": info["kernels"]}
     t0 = time.perf_counter()
     ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
     t_cpu = time.perf_counter() - t0
-    _emit({"metric": "pseudoinverses/s (64x48, latency-bound)", "value": out["fp64_tc"]["value"],
+    _emit({"metric": "pseudoinverses/s (64x48, latency-bound)", "value": out["autotuned"]["value"],
            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
            "config": {"workload": "moore_penrose_64x48", "alpha": alpha, "tol": 1e-12},
-           "fp64_tc": out["fp64_tc"], "fp64_gpu": out["fp64"],
+           "fp64_tc": out["fp64_tc"], "autotuned": out["autotuned"], "crossover": out["crossover"],
            "cpu_baseline": {"value": 1.0 / t_cpu, "unit": "solves/s", "kind": "oracle", "sample": "full solve",
                             "cores": len(os.sched_getaffinity(0))}})
     h.close()

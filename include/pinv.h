@@ -250,6 +250,15 @@ int  pinv_gemm(pinv_handle *h, int M, int N, int K, const double *A, int lda, in
                const double *B, int ldb, int trans_b, double *C, int ldc, pinv_prec prec,
                void *stream);
 
+/* Autotune the product engine for FP64-class products on this device: time one
+ * n x n x n product with the native FP64 (DMMA) kernel and with the tensor-core
+ * slice engine for n = 64 ... 1024, and route FP64-class products whose largest
+ * dimension is below the measured crossover to DMMA from then on (the tensor-
+ * core engine's fixed costs -- slicing launches, 128 x 128 tiles -- dominate
+ * small products).  *crossover (may be NULL) receives the size; 0 means the
+ * tensor-core engine won everywhere.  The choice belongs to the handle. */
+int  pinv_autotune(pinv_handle *h, void *stream, int *crossover);
+
 /* For callers that cannot allocate device memory (a plugin whose host
  * framework owns the allocator, code under a pool that forbids cudaMalloc,
  * code that must not trigger the implicit synchronisation of cudaMalloc or

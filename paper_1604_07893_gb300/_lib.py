@@ -25,7 +25,8 @@ FINISH = {None: 0, "none": 0, "clean": 1}
 HISTORY = 128
 
 EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_batched", "pinv_submit",
-           "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_step_noalloc")
+           "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_autotune",
+           "pinv_step_noalloc")
 NOALLOC_MAX_DIM = 128
 
 
@@ -92,6 +93,7 @@ def load() -> C.CDLL:
                               C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
     lib.pinv_gemm.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
                               C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+    lib.pinv_autotune.argtypes = [C.c_void_p, C.c_void_p, P(C.c_int)]
     lib.pinv_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
     for name in EXPORTS:
@@ -252,6 +254,16 @@ class Handle:
         if rc != PINV_OK:
             raise PinvError(rc, "pinv_gemm")
         return C
+
+    def autotune(self, stream=None) -> int:
+        """pinv_autotune: measure the DMMA / tensor-core crossover for FP64-class
+        products on this device; returns the crossover size (0 = tensor cores
+        everywhere)."""
+        out = C.c_int()
+        rc = self._lib.pinv_autotune(self._h, C.c_void_p(_stream_ptr(stream)), C.byref(out))
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_autotune")
+        return out.value
 
     def step(self, A, X_in, X_out=None, *, prec="fp64", stabilized=False, stream=None):
         """pinv_step: one loop of Eq. PM (or PM-modified).  Returns (X_out, rel_step)."""

@@ -199,7 +199,20 @@ __global__ void scale_copy_batched_kernel(int rows, int cols, const double* X0, 
         Y[(size_t)i * ldy + j] = a * X[(size_t)i * ldx + j];
 }
 
+__global__ void fill_pattern_kernel(int rows, int cols, double* X, int ld, unsigned seed) {
+    const size_t total = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        unsigned h = (unsigned)e * 2654435761u ^ seed * 40503u;
+        h ^= h >> 13; h *= 0x5bd1e995u; h ^= h >> 15;
+        X[(e / cols) * ld + e % cols] = ((double)h / 4294967296.0) * 2.0 - 1.0;
+    }
+}
+
 }  // namespace
+
+void fill_pattern(int rows, int cols, double* X, int ld, unsigned seed, cudaStream_t st) {
+    fill_pattern_kernel<<<152 * 4, 256, 0, st>>>(rows, cols, X, ld, seed);
+}
 
 void gather_pad(const InstanceRef* table, int batch, int rows_pad, int cols_pad, double* slab0,
                 long long stride, cudaStream_t st) {

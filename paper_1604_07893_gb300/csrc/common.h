@@ -69,6 +69,9 @@ void diff_norms(int rows, int cols, const double* P, int ldp, const double* Q, i
                 bool transQ, double* out, double* scratch, cudaStream_t st);
 int diff_norms_scratch_pairs();
 
+// X[i][j] = a deterministic pseudo-random value in (-1, 1) from (i, j, seed).
+void fill_pattern(int rows, int cols, double* X, int ld, unsigned seed, cudaStream_t st);
+
 // One instance of a batch: a caller matrix (rows x cols, leading dimension ld).
 struct InstanceRef {
     const double* src;

@@ -76,6 +76,7 @@ struct pinv_handle {
     double* pinned = nullptr;  // host pinned readback block
     double* dsmall = nullptr;  // device: reduction outputs
     int* derr = nullptr;       // device error word of the tensor-core kernels
+    int tc_crossover = 0;      // pinv_autotune: FP64-class products below this size use DMMA
     std::vector<cudaEvent_t> events;  // profiling pool (pairs), created on demand
     // pinned readback blocks for groups, reused (pinned allocation can
     // synchronise the device, so it happens only when the pool is empty)
@@ -231,7 +232,9 @@ int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const d
     c.gemm_flops += 2.0 * M * N * K * c.batch;   // algorithmic work of the full product
     const int slot = prof_slot(c);
     int r;
-    if (c.prec_k == 0) {
+    // autotuned engine choice: small FP64-class products run on the DMMA kernel
+    const bool small = c.prec_k == TC_FP64 && std::max(M, std::max(N, K)) < c.h->tc_crossover;
+    if (c.prec_k == 0 || small) {
         if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 0), c.st);
         r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st, c.batch, c.stride, sym);
         if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 1), c.st);
@@ -1356,6 +1359,57 @@ int pinv_step(pinv_handle* h, int m, int n, const double* A, int lda, const doub
     if (rc) return rc;
     if (rel_step) *rel_step = x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY;
     CK(cudaGetLastError());
+    return PINV_OK;
+}
+
+int pinv_autotune(pinv_handle* h, void* stream, int* crossover) {
+    if (!h) return PINV_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int sizes[] = {64, 128, 192, 256, 384, 512, 768, 1024};
+    const int nmax = 1024;
+    const TcMode mode = tc_mode(TC_FP64);
+    const size_t mat = align_up(sizeof(double) * nmax * nmax);
+    const size_t need = 3 * mat + align_up(tc_workspace_bytes(nmax, nmax, nmax, mode));
+    int rc = ensure_workspace(h, std::max(need, h->ws_bytes));
+    if (rc) return rc;
+    double* A = (double*)h->ws;
+    double* B = (double*)((char*)h->ws + mat);
+    double* C = (double*)((char*)h->ws + 2 * mat);
+    void* tcws = (char*)h->ws + 3 * mat;
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    int cross = 0;
+    bool tc_won_all_above = true;
+    for (int i = (int)(sizeof(sizes) / sizeof(sizes[0])) - 1; i >= 0; --i) {
+        const int n = sizes[i];
+        fill_pattern(n, n, A, n, 1u, st);
+        fill_pattern(n, n, B, n, 2u, st);
+        Epilogue e = epi1(term(C, n, 1));
+        float ms[2] = {0, 0};
+        for (int eng = 0; eng < 2; ++eng) {
+            for (int rep = 0; rep < 4; ++rep) {   // first call warms up
+                int kernels = 0;
+                if (rep == 1) CK(cudaEventRecord(e0, st));
+                if (eng == 0) gemm_f64(n, n, n, A, n, false, B, n, false, e, st);
+                else tc_gemm(n, n, n, A, n, false, B, n, false, e, mode, tcws, h->ws_bytes - 3 * mat, h->derr, st,
+                             &kernels);
+            }
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            CK(cudaEventElapsedTime(&ms[eng], e0, e1));
+        }
+        if (tc_won_all_above && ms[1] <= ms[0]) continue;   // tensor cores still faster here
+        tc_won_all_above = false;
+        cross = sizes[i] + 1;                                  // DMMA at this size and below
+        break;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    CK(cudaGetLastError());
+    h->tc_crossover = cross;
+    if (crossover) *crossover = cross;
     return PINV_OK;
 }
 

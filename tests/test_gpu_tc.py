@@ -189,3 +189,28 @@ def test_order18_stop_parity(handle):
     assert rel(X.cpu().numpy(), ref) <= 1e-9
     assert rel(X.cpu().numpy(), pinv_closed_form(w)) <= 1e-9
     assert max(info["penrose"]) <= 1e-9
+
+
+def test_autotune_routes_small_products_and_keeps_parity():
+    """pinv_autotune measures the DMMA / tensor-core crossover on this device;
+    after it a small FP64-class solve (DMMA side of the crossover) and a larger
+    one (tensor-core side) both still match the oracle."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_07893_gb300 import Handle
+    h = Handle(0)
+    try:
+        cross = h.autotune()
+        assert cross == 0 or 65 <= cross <= 1025
+        for (m, n, r) in [(64, 48, 40), (512, 384, 288)]:
+            w = W.rectangular(m, n, r, 1.0, 1e-3, seed=5)
+            alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+            ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha,
+                             variant="stabilised", finish="moore_penrose")
+            X, info = h.solve(dev(w.A), alpha=alpha, tol=1e-12, variant="stabilized", finish="clean",
+                              prec="fp64_tc", check=True)
+            assert info["status"] == 0
+            assert rel(X.cpu().numpy(), ref) <= 1e-9
+            assert max(info["penrose"]) <= 1e-9
+    finally:
+        h.close()
