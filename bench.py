@@ -19,7 +19,7 @@ V diag(1/s) U^T).
   python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64_tc|fp64|fp32|mixed_bf16]
 
 The default path computes every product FP64-accurately on the BF16 tensor
-cores (9 exact BF16 slices per operand, 45 slice products per FP64 product);
+cores (7 exact BF16 slices per operand, 28 slice products per FP64 product);
 the plain FP64 iteration (native FP64 DMMA products) is timed beside it.
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
@@ -52,10 +52,10 @@ WORKLOAD = "moore_penrose_rank_deficient_4096x3072_r2304"
 # kernel from the committed ncu summary under profiles/ (None until captured
 # for the current kernel).
 TRAFFIC_BYTES = {"fp64": None, "fp32": None, "mixed_bf16": None,
-                 # profiles/tc_gemm_kernel_fp64class_3072x3072x4096.md: 5.512 GB read + 82.7 MB
-                 # written for a 3072x3072x4096 launch of the current kernel; scaled to this
-                 # workload's mean launch by the FP64-equivalent flops it processes
-                 "fp64_tc": 5.512e9 + 82.7e6}
+                 # profiles/tc_gemm_kernel_fp64class_3072x3072x4096.md gives the bytes of
+                 # a 3072x3072x4096 launch, scaled to this workload's mean launch by the
+                 # FP64-equivalent flops it processes
+                 "fp64_tc": None}
 TRAFFIC_REF_FLOPS = 2.0 * 3072 * 3072 * 4096   # the captured launch's 2MNK
 
 
@@ -310,7 +310,7 @@ def run_ours(args):
     gemm_flops = sum(i["gemm_flops"] for i in infos)
     gemm_launches = sum(i["gemms"] for i in infos)
     # the dominant kernel's algorithmic work: FP64 products for the DMMA path;
-    # for the tensor-core path the BF16 slice products it executes (45 per FP64
+    # for the tensor-core path the BF16 slice products it executes (28 per FP64
     # product at FP64 class), reported beside the FP64-equivalent rate
     work = gemm_flops if args.prec == "fp64" else sum(i["tensor_flops"] for i in infos)
     achieved = work / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None

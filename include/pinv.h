@@ -85,11 +85,11 @@ typedef enum {
                                  null block (full column rank, nonsingular); needs
                                  alpha <= 1/sigma_max^2 (e.g. the alpha = 0 recipe) */
     PINV_PREC_MIXED_FP8  = 2, /* reserved: FP8 early loops (returns PINV_ERR_ARG)  */
-    PINV_PREC_FP32       = 3, /* FP32-class loops (5 exact BF16 slices, 15 slice
-                                 products, ~30 bits) until the step is < 1e-4 or
+    PINV_PREC_FP32       = 3, /* FP32-class loops (4 exact BF16 slices, 10 slice
+                                 products, 31 bits) until the step is < 1e-4 or
                                  stops falling, then FP64-class                    */
     PINV_PREC_FP64_TC    = 4, /* every product FP64-accurate on the BF16 tensor
-                                 cores: 9 exact slices per operand, 45 products    */
+                                 cores: 7 exact slices per operand, 28 products    */
     PINV_PREC_BF16_FP32  = 5  /* FP32-finished: BF16 while the step is > 0.5, then
                                  FP32-class to the end (the stop rule ends at the
                                  FP32 noise floor); the finish, if asked, in

@@ -1,10 +1,13 @@
 // FP64 GEMM with the fused epilogue used by every product of the iteration.
 //
 // tcgen05 has no FP64 kind, so FP64 products run on the FP64 tensor path
-// through mma.sync m8n8k4 (DMMA).  A 64x64 CTA tile, four warps of 32x32,
-// BK = 16; the next K-slab is fetched into registers while the current one is
-// multiplied from shared memory.  Ragged edges are zero-filled on load and
-// masked on store, so any M, N, K >= 1 works.
+// through mma.sync m8n8k4 (DMMA).  A CTA tile of 64x64, 32x32 or 16x16 with
+// four warps in a 2x2 arrangement, BK = 16; the next K-slab is fetched into
+// registers while the current one is multiplied from shared memory.  Ragged
+// edges are zero-filled on load and masked on store, so any M, N, K >= 1 works.
+// GB300's FP64 rate is about 2 FMA per clock per SM, so even a 16x16 tile is
+// bound by the FP64 pipe, not by memory: small products take the smallest tile
+// that still fills the GPU, which spreads them over the most SMs.
 //
 // The epilogue forms the linear combinations of Eq. PM directly from the
 // accumulator (identity subtraction for R = I - AX, the I + c R2 + R4 factors,
@@ -17,7 +20,7 @@
 namespace pinv {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16;
+constexpr int BK = 16;
 constexpr int APAD = 4;   // As row stride BK + APAD doubles: conflict-free fragment reads
 constexpr int BPAD = 4;   // Bs row stride BN + BPAD
 constexpr int THREADS = 128;
@@ -45,8 +48,13 @@ __device__ __forceinline__ double loadB(const GemmArgs& g, int k, int j) {
     return g.transB ? g.B[(size_t)j * g.ldb + k] : g.B[(size_t)k * g.ldb + j];
 }
 
+// BM x BN CTA tile (BM == BN); each of the four warps owns a (BM/2) x (BN/2)
+// quadrant of (BM/16) x (BN/16) 8x8 accumulators.
+template <int BM, int BN>
 __global__ void __launch_bounds__(THREADS)
 gemm_f64_kernel(GemmArgs g, Epilogue epi) {
+    constexpr int FM = BM / 16, FN = BN / 16;          // 8x8 fragments per warp
+    constexpr int NA = BM * BK / THREADS, NB = BK * BN / THREADS;   // slab elements per thread
     __shared__ double As[BM][BK + APAD];
     __shared__ double Bs[BK][BN + BPAD];
     __shared__ double red[2][THREADS / 32];
@@ -66,16 +74,20 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
         if (epi.partials) epi.partials += 2LL * blockIdx.z * gridDim.x * gridDim.y;
     }
 
-    // Register staging of one K-slab: 1024 A elements and 1024 B elements, 8 each.
-    double ra[8], rb[8];
+    // Register staging of one K-slab: BM*BK A elements and BK*BN B elements.
+    double ra[NA], rb[NB];
     auto fetch = [&](int k0) {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
+        for (int t = 0; t < NA; ++t) {
             int idx = tid + t * THREADS;
             int r, k;
             if (g.transA) { r = idx % BM; k = idx / BM; }   // consecutive threads: consecutive i
             else          { k = idx % BK; r = idx / BK; }   // consecutive threads: consecutive k
             ra[t] = loadA(g, m0 + r, k0 + k);
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            int idx = tid + t * THREADS;
             int kb, c;
             if (g.transB) { kb = idx % BK; c = idx / BK; }
             else          { c = idx % BN; kb = idx / BN; }
@@ -84,12 +96,16 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
     };
     auto stash = [&]() {
 #pragma unroll
-        for (int t = 0; t < 8; ++t) {
+        for (int t = 0; t < NA; ++t) {
             int idx = tid + t * THREADS;
             int r, k;
             if (g.transA) { r = idx % BM; k = idx / BM; }
             else          { k = idx % BK; r = idx / BK; }
             As[r][k] = ra[t];
+        }
+#pragma unroll
+        for (int t = 0; t < NB; ++t) {
+            int idx = tid + t * THREADS;
             int kb, c;
             if (g.transB) { kb = idx % BK; c = idx / BK; }
             else          { c = idx % BN; kb = idx / BN; }
@@ -97,11 +113,11 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
         }
     };
 
-    double acc[4][4][2];
+    double acc[FM][FN][2];
 #pragma unroll
-    for (int i = 0; i < 4; ++i)
+    for (int i = 0; i < FM; ++i)
 #pragma unroll
-        for (int j = 0; j < 4; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
+        for (int j = 0; j < FN; ++j) acc[i][j][0] = acc[i][j][1] = 0.0;
 
     const int ktiles = (g.K + BK - 1) / BK;
     fetch(0);
@@ -112,28 +128,28 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
         if (kt + 1 < ktiles) fetch((kt + 1) * BK);
 #pragma unroll
         for (int kk = 0; kk < BK; kk += 4) {
-            double af[4], bf[4];
+            double af[FM], bf[FN];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) af[i] = As[wm * 32 + i * 8 + (lane >> 2)][kk + (lane & 3)];
+            for (int i = 0; i < FM; ++i) af[i] = As[wm * (BM / 2) + i * 8 + (lane >> 2)][kk + (lane & 3)];
 #pragma unroll
-            for (int j = 0; j < 4; ++j) bf[j] = Bs[kk + (lane & 3)][wn * 32 + j * 8 + (lane >> 2)];
+            for (int j = 0; j < FN; ++j) bf[j] = Bs[kk + (lane & 3)][wn * (BN / 2) + j * 8 + (lane >> 2)];
 #pragma unroll
-            for (int i = 0; i < 4; ++i)
+            for (int i = 0; i < FM; ++i)
 #pragma unroll
-                for (int j = 0; j < 4; ++j) dmma(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
+                for (int j = 0; j < FN; ++j) dmma(acc[i][j][0], acc[i][j][1], af[i], bf[j]);
         }
     }
 
     // ---- fused epilogue
     double sd = 0.0, sx = 0.0;
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const int row = m0 + wm * 32 + i * 8 + (lane >> 2);
+    for (int i = 0; i < FM; ++i) {
+        const int row = m0 + wm * (BM / 2) + i * 8 + (lane >> 2);
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
+        for (int j = 0; j < FN; ++j) {
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const int col = n0 + wn * 32 + j * 8 + 2 * (lane & 3) + h;
+                const int col = n0 + wn * (BN / 2) + j * 8 + 2 * (lane & 3) + h;
                 if (row < g.M && col < g.N) {
                     const double a = acc[i][j][h];
                     const double v1 = epi.s1 ? epi.s1[(size_t)row * epi.ld1 + col] : 0.0;
@@ -179,15 +195,24 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
 
 }  // namespace
 
-int gemm_f64_ctas(int M, int N) { return ((N + BN - 1) / BN) * ((M + BM - 1) / BM); }
+int gemm_f64_ctas(int M, int N, int tile) { return ((N + tile - 1) / tile) * ((M + tile - 1) / tile); }
+
+int gemm_f64_pick_tile(int M, int N, int batch, int sms) {
+    for (int tile : {64, 32})
+        if ((long long)gemm_f64_ctas(M, N, tile) * batch >= sms) return tile;
+    return 16;
+}
 
 int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
              const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st,
-             int batch, long long stride, bool sym_out) {
+             int batch, long long stride, bool sym_out, int tile) {
     if (sym_out && (M != N || epi.partials)) return -1;
     GemmArgs g{M, N, K, A, lda, transA ? 1 : 0, B, ldb, transB ? 1 : 0, stride, sym_out ? 1 : 0};
-    dim3 grid((N + BN - 1) / BN, (M + BM - 1) / BM, batch);
-    gemm_f64_kernel<<<grid, THREADS, 0, st>>>(g, epi);
+    dim3 grid((N + tile - 1) / tile, (M + tile - 1) / tile, batch);
+    if (tile == 64) gemm_f64_kernel<64, 64><<<grid, THREADS, 0, st>>>(g, epi);
+    else if (tile == 32) gemm_f64_kernel<32, 32><<<grid, THREADS, 0, st>>>(g, epi);
+    else if (tile == 16) gemm_f64_kernel<16, 16><<<grid, THREADS, 0, st>>>(g, epi);
+    else return -1;
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return grid.x * grid.y;   // pair partials per instance
 }

@@ -77,6 +77,7 @@ struct pinv_handle {
     double* dsmall = nullptr;  // device: reduction outputs
     int* derr = nullptr;       // device error word of the tensor-core kernels
     int tc_crossover = 0;      // pinv_autotune: FP64-class products below this size use DMMA
+    int sms = 1;               // streaming multiprocessors of the device
     std::vector<cudaEvent_t> events;  // profiling pool (pairs), created on demand
     // pinned readback blocks for groups, reused (pinned allocation can
     // synchronise the device, so it happens only when the pool is empty)
@@ -186,8 +187,7 @@ size_t workspace_bytes(int m, int n, bool drazin, bool host, bool check, int pre
     if (drazin) b += align_up(sizeof(double) * n * (size_t)n);
     if (host) b += 2 * align_up(sizeof(double) * n * (size_t)m);
     if (check) b += 2 * align_up(sizeof(double) * big * big);
-    const size_t tiles = (size_t)((big + 63) / 64) * ((big + 63) / 64);
-    b += align_up(sizeof(double) * 2 * 8 * tiles);   // pair partials (8 per 128 x 128 tensor-core tile)
+    b += align_up(sizeof(double) * 2 * partial_pairs_bound(big, big));   // stop-norm pair partials
     b += align_up(sizeof(double) * 2 * 2 * 256);
     b += align_up(tc_bytes(m, n, prec));
     return b;
@@ -218,8 +218,7 @@ void carve(Ctx& c, bool drazin, bool host, bool check, int prec) {
     c.Gd = host ? take(sizeof(double) * c.n * (size_t)c.m) : nullptr;
     c.big[0] = check ? take(sizeof(double) * big * big) : nullptr;
     c.big[1] = check ? take(sizeof(double) * big * big) : nullptr;
-    const size_t tiles = (size_t)((big + 63) / 64) * ((big + 63) / 64);
-    c.partials = take(sizeof(double) * 2 * 8 * tiles);
+    c.partials = take(sizeof(double) * 2 * partial_pairs_bound(big, big));
     c.red = take(sizeof(double) * 2 * 2 * 256);
     c.tcws_bytes = tc_bytes(c.m, c.n, prec);
     c.tcws = c.tcws_bytes ? (void*)take(c.tcws_bytes) : nullptr;
@@ -236,7 +235,8 @@ int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const d
     const bool small = c.prec_k == TC_FP64 && std::max(M, std::max(N, K)) < c.h->tc_crossover;
     if (c.prec_k == 0 || small) {
         if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 0), c.st);
-        r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st, c.batch, c.stride, sym);
+        r = gemm_f64(M, N, K, A, lda, tA, B, ldb, tB, e, c.st, c.batch, c.stride, sym,
+                     gemm_f64_pick_tile(M, N, c.batch, c.h->sms));
         if (slot >= 0) cudaEventRecord(prof_ev(c, slot, 1), c.st);
     } else {
         --c.kernels;  // tc_gemm counts its own launches (slicing + GEMM)
@@ -764,9 +764,8 @@ size_t slab_doubles(int M, int N, bool big2, bool g) {
 
 size_t group_bytes(int batch, int M, int N, int prec, bool big2, bool g) {
     const size_t big = std::max(M, N);
-    const size_t tiles = ((big + 63) / 64) * ((big + 63) / 64);
     size_t b = sizeof(double) * slab_doubles(M, N, big2, g) * batch;
-    b += align_up(sizeof(double) * 2 * 8 * tiles * batch);            // partials
+    b += align_up(sizeof(double) * 2 * partial_pairs_bound(big, big) * batch);   // partials
     b += align_up(sizeof(double) * 2 * 2 * 256);                      // reduction scratch
     b += 3 * align_up(sizeof(InstanceRef) * batch) + align_up(sizeof(int) * 2 * batch) +
          2 * align_up(sizeof(double) * 2 * batch);
@@ -846,8 +845,7 @@ int group_begin(Group& G) {
         c.A = c.Ad; c.lda = G.N; c.Al = nullptr;
     }
     const size_t big = std::max(G.M, G.N);
-    const size_t tiles = ((big + 63) / 64) * ((big + 63) / 64);
-    c.partials = (double*)take(sizeof(double) * 2 * 8 * tiles * G.batch);
+    c.partials = (double*)take(sizeof(double) * 2 * partial_pairs_bound(big, big) * G.batch);
     c.red = (double*)take(sizeof(double) * 2 * 2 * 256);
     G.tabA = (InstanceRef*)take(sizeof(InstanceRef) * G.batch);
     G.tabX = (InstanceRef*)take(sizeof(InstanceRef) * G.batch);
@@ -1195,6 +1193,7 @@ int pinv_init(pinv_handle** out, const pinv_config* cfg) {
     if (e == cudaSuccess) e = cudaMalloc(&h->dsmall, 64 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->derr, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(h->derr, 0, sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device);
     if (e != cudaSuccess) {
         std::fprintf(stderr, "pinv_init: %s\n", cudaGetErrorString(e));
         if (h->pinned) cudaFreeHost(h->pinned);
@@ -1392,7 +1391,8 @@ int pinv_autotune(pinv_handle* h, void* stream, int* crossover) {
             for (int rep = 0; rep < 4; ++rep) {   // first call warms up
                 int kernels = 0;
                 if (rep == 1) CK(cudaEventRecord(e0, st));
-                if (eng == 0) gemm_f64(n, n, n, A, n, false, B, n, false, e, st);
+                if (eng == 0) gemm_f64(n, n, n, A, n, false, B, n, false, e, st, 1, 0, false,
+                                       gemm_f64_pick_tile(n, n, 1, h->sms));
                 else tc_gemm(n, n, n, A, n, false, B, n, false, e, mode, tcws, h->ws_bytes - 3 * mat, h->derr, st,
                              &kernels);
             }
@@ -1427,7 +1427,9 @@ int pinv_gemm(pinv_handle* h, int M, int N, int K, const double* A, int lda, int
                    ((prec == PINV_PREC_FP32 || prec == PINV_PREC_BF16_FP32) ? TC_FP32 : TC_FP64));
     Epilogue e = epi1(term(C, ldc, 1));
     if (pk == 0) {
-        if (gemm_f64(M, N, K, A, lda, trans_a != 0, B, ldb, trans_b != 0, e, st) < 0) return PINV_ERR_CUDA;
+        if (gemm_f64(M, N, K, A, lda, trans_a != 0, B, ldb, trans_b != 0, e, st, 1, 0, false,
+                     gemm_f64_pick_tile(M, N, 1, h->sms)) < 0)
+            return PINV_ERR_CUDA;
     } else {
         const size_t need = tc_workspace_bytes(M, N, K, tc_mode(pk));
         int rc = ensure_workspace(h, std::max(need, h->ws_bytes));

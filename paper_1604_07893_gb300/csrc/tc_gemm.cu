@@ -4,16 +4,18 @@
 //   op(A) = sum_s A_s,  op(B) = sum_t B_t,   C = sum_{s + t <= L} A_s B_t.
 // Slices are BF16 matrices.  In the exact modes (FP64-class, FP32-class) each
 // row of op(A) (column of op(B)) is scaled by its power of two 2^-e (so its
-// largest entry lies in [1/2, 1)) and cut on a grid with 6 bits per slice:
-// every slice entry is q * 2^-6(s+1) with |q| <= 64, bf16 holds it exactly,
-// every product q q' 2^(e+e') is exact, and a K-chunk of <= 2048 products sums
-// to an integer multiple of one power of two below 2^23 -- the FP32 tensor-core
-// accumulation is exact.  Each (pair, chunk) accumulator is drained from TMEM
-// and added in FP64 in the epilogue, which finally applies 2^(e_i + f_j); the
-// only rounding is the FP64 sum of the slice products and the truncation of
-// slices beyond s + t > L.
-//   FP64-class: 9 slices per operand, s + t <= 8 (45 products)
-//   FP32-class: 5 slices, s + t <= 4 (15 products, about 30 bits)
+// largest entry lies in [1/2, 1)), rounded to a T = 8S - 1 bit signed integer
+// F and cut into S balanced base-256 digits: slice s holds q_s 2^(8(S-1-s) - T)
+// with |q_s| <= 128, which bf16 (8 significant bits) holds exactly.  Every
+// product q q' is an integer below 2^14 in magnitude times the power of two of
+// its diagonal d = s + t, so a K-chunk of <= 512 products sums to an integer
+// multiple of that power below 2^23 -- the FP32 tensor-core accumulation is
+// exact.  Each (pair, chunk) accumulator is drained from TMEM and summed
+// exactly per diagonal in the epilogue, which adds each diagonal once in FP64
+// and finally applies 2^(e_i + f_j); the only rounding is the FP64 sum of the
+// diagonals, the rounding of F and the truncation of pairs with s + t > L.
+//   FP64-class: 7 slices per operand (55 bits), s + t <= 6 (28 products)
+//   FP32-class: 4 slices (31 bits), s + t <= 3 (10 products)
 //   BF16:       1 slice rounded to nearest (no grid), one product
 //
 // Kernel layout (one persistent CTA per SM, 6 warps):
@@ -32,6 +34,8 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
+#include <cmath>
 #include <cstdio>
 #include <mutex>
 
@@ -61,6 +65,8 @@ struct TcParams {
     int npairs;
     int pair_s[64], pair_t[64];
     int chunk;            // K elements per exact accumulation
+    int dint;             // diagonals 0..dint are summed exactly in int64 (Horner), -1: none
+    int ubase;            // the tile sums in TMEM are in units of 2^-ubase (row-normalised)
     int exact;            // 1: slices on power-of-two grids (integer-valued products)
     int S;                // slices per operand (tensor-map slice index = instance * S + s)
     int batch;            // instances; instance b uses every FP64 matrix at +b*stride
@@ -84,11 +90,23 @@ __device__ __forceinline__ void tile_coords(int t, int tm, int sym, int& mb, int
     nb = mb + t;
 }
 
-__device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i) {
-    int e = 0;
-    const double v = __longlong_as_double((long long)mx[i]);
+// e with max = f 2^e, 1/2 <= f < 1 (0 for a zero maximum), by integer
+// arithmetic on the bit pattern (GB300's FP64 pipe is narrow).
+__device__ __forceinline__ int exponent_of(unsigned long long bits) {
+    const int bexp = (int)((bits >> 52) & 0x7FF);
+    if (bexp) return bexp - 1022;
+    int e = 0;   // zero or subnormal
+    const double v = __longlong_as_double((long long)bits);
     if (v > 0.0) frexp(v, &e);
     return e;
+}
+__device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i) { return exponent_of(mx[i]); }
+
+// a * 2^e: one multiplication by a constructed power of two when 2^e is a
+// normal double (then it rounds exactly like ldexp), ldexp otherwise.
+__device__ __forceinline__ double scale_pow2(double a, int e) {
+    if (e >= -1022 && e <= 1023) return a * __longlong_as_double((long long)(e + 1023) << 52);
+    return ldexp(a, e);
 }
 
 // ------------------------------------------------------------------ PTX helpers
@@ -218,7 +236,7 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 // instead of 32 KiB from L2 per stage; a stage is released only when both CTAs'
 // MMAs are done with it (the commit is multicast to both empty barriers).
 template <bool MC>
-__global__ void __launch_bounds__(THREADS, 1)
+__global__ void __launch_bounds__(THREADS, 1)   // 10 warps: 3 share a sub-partition (16K registers): <= 168 each
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
@@ -341,10 +359,16 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     } else {
         // ---------------------------------------------------------- epilogue (warps 2..9)
         // Drained accumulators of one slice diagonal d = s + t share the unit
-        // 2^-6(d+2) (the slices are integer digits times powers of two), so in
-        // the exact modes they are summed exactly as int32 (at most 18 drains of
-        // |value| <= 2^23 units: < 2^28).  Each diagonal is then added once, in
-        // FP64, to the running sums kept in TMEM columns [2BN, 4BN).
+        // 2^-(14+8d) (the slices are integer digits times powers of two), so in
+        // the exact modes they are summed exactly as int32: each drain is below
+        // 2^23 units, and at most 255 drains are summed before the int32 sums
+        // are added to the running sums of the tile in TMEM columns [2BN, 4BN)
+        // (once per diagonal, or every 255 drains).  Diagonals 0..dint go into
+        // an exact int64 by Horner's rule (C <- 256 C + I_d on the integer
+        // pipe; the host picks dint so that |C| < 2^62); at the end of diagonal
+        // dint C becomes one FP64 value, and later (tiny) diagonals are added in
+        // FP64.  This keeps FP64 instructions -- about 2 per clock per SM on
+        // GB300 -- out of all but the last flushes.
         const int lg = warp & 3;                 // TMEM lane group of this warp
         const int half = (warp - 2) >> 2;        // which BN/2 columns of the tile
         const int ew = warp - 2;                 // epilogue warp index
@@ -371,23 +395,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             const unsigned long long* rmax = P.rmax ? P.rmax + (size_t)b * P.M : nullptr;
             const unsigned long long* cmax = P.cmax ? P.cmax + (size_t)b * P.N : nullptr;
             int iacc[EPI_COLS];
-            int dcur = -1;
+            int ndrain = 0;   // drains summed in iacc since its last flush
+            int hdiag = -1;   // diagonal of the last flush
             bool have64 = false;
             bool ok = true;
             for (int u = 0; u < units; ++u) {
                 const int pr = u / kchunks;
                 const int d = P.pair_s[pr] + P.pair_t[pr];
-                if (d != dcur) {
+                if (ndrain == 0) {
 #pragma unroll
                     for (int j = 0; j < EPI_COLS; ++j) iacc[j] = 0;
-                    dcur = d;
                 }
                 if (*abort_flag || !mbar_wait(&accf[buf], accphase[buf])) {
                     record_error(P.err, 4); *abort_flag = 1; ok = false; break;
                 }
                 tc_fence_after();
                 const uint32_t taddr = lane_base + buf * BN + half * EPI_COLS;
-                const float unit = P.exact ? ldexpf(1.0f, 6 * (d + 2)) : 1.0f;
+                const int uexp = 14 + 8 * d;   // slice products q q' 2^-(14+8d): accumulator / unit
+                const float unit = P.exact ? ldexpf(1.0f, uexp) : 1.0f;
 #pragma unroll
                 for (int c = 0; c < EPI_COLS; c += 32) {
                     uint32_t r[32];
@@ -404,24 +429,44 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 buf ^= 1;
                 const bool diag_done =
                     (u + 1 == units) || (P.pair_s[(u + 1) / kchunks] + P.pair_t[(u + 1) / kchunks] != d);
-                if (diag_done) {   // add this diagonal to the FP64 sums in TMEM
-                    const double sc = P.exact ? ldexp(1.0, -6 * (d + 2)) : 1.0;
+                if (diag_done || ++ndrain == 255) {   // add the int32 sums to the tile sums in TMEM
+                    ndrain = 0;
+                    const bool horner = P.exact && d <= P.dint;
+                    const bool shift = horner && have64 && d != hdiag;       // first flush of diagonal d > 0
+                    const bool to_fp64 = horner && diag_done && d == P.dint;  // C is complete: one FP64 value
+                    // FP64 flush of a diagonal past dint: I_d 2^-(14+8d) in units of 2^-ubase
+                    const double sc = scale_pow2(1.0, P.ubase - uexp);
 #pragma unroll
                     for (int c = 0; c < EPI_COLS; c += 16) {
                         uint32_t r[32];
                         if (have64) tmem_ld32_raw(acc64 + 2 * c, r);
 #pragma unroll
                         for (int j = 0; j < 16; ++j) {
-                            const double v = P.exact ? (double)iacc[c + j] * sc
-                                                     : (double)__int_as_float(iacc[c + j]);
-                            const double o = have64 ? __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]) : 0.0;
-                            const double nw = o + v;
-                            r[2 * j] = (uint32_t)__double2loint(nw);
-                            r[2 * j + 1] = (uint32_t)__double2hiint(nw);
+                            if (horner) {
+                                long long C = have64 ? (long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j])
+                                                     : 0LL;
+                                if (shift) C *= 256;
+                                C += iacc[c + j];
+                                if (to_fp64) {
+                                    const double v = (double)C;   // units 2^-(14+8 dint) = 2^-ubase
+                                    r[2 * j] = (uint32_t)__double2loint(v);
+                                    r[2 * j + 1] = (uint32_t)__double2hiint(v);
+                                } else {
+                                    r[2 * j] = (uint32_t)(unsigned long long)C;
+                                    r[2 * j + 1] = (uint32_t)((unsigned long long)C >> 32);
+                                }
+                            } else {
+                                const double o = have64 ? __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]) : 0.0;
+                                const double nw = P.exact ? fma((double)iacc[c + j], sc, o)
+                                                          : o + (double)__int_as_float(iacc[c + j]);
+                                r[2 * j] = (uint32_t)__double2loint(nw);
+                                r[2 * j + 1] = (uint32_t)__double2hiint(nw);
+                            }
                         }
                         tmem_st32_raw(acc64 + 2 * c, r);
                     }
                     have64 = true;
+                    hdiag = d;
                 }
             }
             if (!ok) break;
@@ -431,6 +476,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             double sd = 0.0, sx = 0.0;
             const double* s1 = (E.s1 && row < P.M) ? E.s1 + (size_t)row * E.ld1 : nullptr;
             const double* s2 = (E.s2 && row < P.M) ? E.s2 + (size_t)row * E.ld2 : nullptr;
+            // FP64 instructions are scarce: terms with a zero coefficient are
+            // skipped (warp-uniform branches), the identity is added on the
+            // diagonal only, the norms only when asked for
+            const bool norms = E.partials != nullptr;
 #pragma unroll 1
             for (int c = 0; c < EPI_COLS; c += 16) {
                 uint32_t r[32];
@@ -441,20 +490,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     const int col = n0 + half * EPI_COLS + c + j;
                     if (col < P.N) {
                         double a = __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]);
-                        if (rmax) a = ldexp(a, ei + grid_exponent(cmax, col));
+                        if (rmax) a = scale_pow2(a, ei + grid_exponent(cmax, col) - P.ubase);
                         const double v1 = s1 ? s1[col] : 0.0;
                         const double v2 = s2 ? s2[col] : 0.0;
-                        const double id = (row == col) ? 1.0 : 0.0;
 #pragma unroll
                         for (int o = 0; o < 3; ++o) {
                             if (o < E.nout) {
                                 const EpiTerm& t = E.o[o];
-                                const double v = t.a_acc * a + t.a_s1 * v1 + t.a_s2 * v2 + t.a_id * id;
+                                double v = t.a_acc * a;
+                                if (t.a_s1 != 0.0) v = fma(t.a_s1, v1, v);
+                                if (t.a_s2 != 0.0) v = fma(t.a_s2, v2, v);
+                                if (row == col) v += t.a_id;
                                 if (t.out) {
                                     t.out[(size_t)row * t.ld + col] = v;
                                     if (mirror) t.out[(size_t)col * t.ld + row] = v;   // warp-coalesced
                                 }
-                                if (o == 0) { const double dd = v - v1; sd += dd * dd; sx += v1 * v1; }
+                                if (o == 0 && norms) { const double dd = v - v1; sd = fma(dd, dd, sd); sx = fma(v1, v1, sx); }
                             }
                         }
                     }
@@ -487,7 +538,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 // ------------------------------------------------------------------ slicing
 // Rows of op(X) (op(X)[i][k] = trans ? X[k][i] : X[i][k]): mx[i] receives the
 // bit pattern of max_k |op(X)[i][k]| (non-negative doubles order like their
-// bits, so integer max is the floating max).  mx must be zeroed first.
+// bits, so integer max is the floating max, taken on the integer pipe; a NaN
+// or infinity wins and poisons the row).  mx must be zeroed first.
 __global__ void row_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx,
                                   long long stride) {
     X += (long long)blockIdx.y * stride;
@@ -496,36 +548,40 @@ __global__ void row_absmax_kernel(int rows, int K, const double* X, int ld, unsi
     const int i = blockIdx.x * warps + (threadIdx.x >> 5);
     const int lane = threadIdx.x & 31;
     if (i >= rows) return;
-    double m = 0.0;
-    for (int k = lane; k < K; k += 32) m = fmax(m, fabs(X[(size_t)i * ld + k]));
-    for (int off = 16; off; off >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if (lane == 0) mx[i] = (unsigned long long)__double_as_longlong(m);
+    const unsigned long long* Xb = reinterpret_cast<const unsigned long long*>(X);
+    constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+    unsigned long long m = 0;
+    for (int k = lane; k < K; k += 32) m = max(m, Xb[(size_t)i * ld + k] & ABS);
+    for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+    if (lane == 0) mx[i] = m;
 }
 // Transposed view: X is K x rows; a (32 columns) x (256 rows of X) patch per
 // block, coalesced along the columns, combined with atomicMax.
 __global__ void col_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx,
                                   long long stride) {
-    __shared__ double sh[8][33];
+    __shared__ unsigned long long sh[8][33];
     X += (long long)blockIdx.z * stride;
     mx += (size_t)blockIdx.z * rows;
+    const unsigned long long* Xb = reinterpret_cast<const unsigned long long*>(X);
+    constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
     const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
     const int i = blockIdx.x * 32 + tx;
     const int k0 = blockIdx.y * 256;
     const int k1 = min(K, k0 + 256);
-    double m = 0.0;
+    unsigned long long m = 0;
     if (i < rows)
-        for (int k = k0 + ty; k < k1; k += 8) m = fmax(m, fabs(X[(size_t)k * ld + i]));
+        for (int k = k0 + ty; k < k1; k += 8) m = max(m, Xb[(size_t)k * ld + i] & ABS);
     sh[ty][tx] = m;
     __syncthreads();
     if (ty == 0 && i < rows) {
-        for (int j = 1; j < 8; ++j) m = fmax(m, sh[j][tx]);
-        atomicMax(&mx[i], (unsigned long long)__double_as_longlong(m));
+        for (int j = 1; j < 8; ++j) m = max(m, sh[j][tx]);
+        atomicMax(&mx[i], m);
     }
 }
 
 // out[s][i][k] (bf16, row length Kp) for 32 x 32 tiles of op(X); zero beyond K.
-// exact = 1: slices on the per-row grid 2^(e_i - 6(s+1)); exact = 0: one
-// round-to-nearest slice.
+// exact = 1: base-256 digit slices of the row-normalised value (slice s holds
+// q_s 2^(8(S-1-s) - T), T = 8S - 1); exact = 0: one round-to-nearest slice.
 __global__ void slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans,
                              const unsigned long long* mx, int S, int exact, __nv_bfloat16* out,
                              long long stride) {
@@ -558,34 +614,39 @@ __global__ void slice_kernel(int rows, int K, int Kp, const double* X, int ld, i
             for (int s = 1; s < S; ++s) out[s * plane + (size_t)i * Kp + k] = __double2bfloat16(0.0);
             continue;
         }
-        int ei = 0;   // 2^ei > max |row i| (frexp: max = f 2^ei, 0.5 <= f < 1)
-        const double rmax = __longlong_as_double((long long)mx[i]);
-        if (rmax > 0.0) frexp(rmax, &ei);
+        // 2^ei > max |row i| (max = f 2^ei, 1/2 <= f < 1)
+        const int ei = exponent_of(mx[i]);
         // Integer digit extraction (GB300's FP64 pipe is narrow): x = m 2^E with
-        // a 53-bit integer m; F = round(x / 2^(ei - 6S)) is a signed fixed-point
-        // integer with |F| < 2^(6S); slice s is the balanced 6-bit digit
-        // q_s = round(F / 2^(6(S-1-s))) taken from the top, F -= q_s 2^(...).
+        // a 53-bit integer m; U = round(|x| / 2^(ei - T)) <= 2^T is a fixed-point
+        // integer; its bytes u_s (most significant first) become balanced
+        // digits from the least significant up (u_s + carry >= 128: digit
+        // u_s + carry - 256, carry 1); the top digit takes the last carry and
+        // stays <= 128 because U <= 2^T.  Then q_s = +-digit, |q_s| <= 128.
         const long long bits = __double_as_longlong(x);
         const int bexp = (int)((bits >> 52) & 0x7FF);
         if (bexp == 0x7FF) {   // NaN/Inf: poison every slice so the product reports it
             for (int s = 0; s < S; ++s) out[s * plane + (size_t)i * Kp + k] = __float2bfloat16_rn(NAN);
             continue;
         }
-        long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (bexp ? (1LL << 52) : 0LL);
+        const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (bexp ? (1LL << 52) : 0LL);
         const int E = (bexp ? bexp : 1) - 1075;             // x = mant * 2^E
-        const int shift = E - (ei - 6 * S);                 // F = mant * 2^shift
-        long long F;
-        if (shift >= 0) F = mant << shift;                  // < 2^(6S) <= 2^54 since |x| < 2^ei
-        else if (shift > -62) F = (mant + (1LL << (-shift - 1))) >> (-shift);
-        else F = 0;
-        if (bits < 0) F = -F;
-        for (int s = 0; s < S; ++s) {
-            const int w = 6 * (S - 1 - s);
-            const long long q = w ? ((F + (1LL << (w - 1))) >> w) : F;   // |q| <= 64
-            F -= q << w;
-            // row-normalised: the slice holds q 2^(-6(s+1)); 2^ei is applied in the
+        const int T = 8 * S - 1;
+        const int shift = E - (ei - T);                     // U = mant * 2^shift
+        unsigned long long U;
+        if (shift >= 0) U = (unsigned long long)mant << shift;   // <= 2^T <= 2^55 since |x| < 2^ei
+        else if (shift > -62) U = (unsigned long long)((mant + (1LL << (-shift - 1))) >> (-shift));
+        else U = 0;
+        const unsigned lo = (unsigned)U, hi = (unsigned)(U >> 32);
+        const int sgn = bits < 0 ? -1 : 1;
+        int carry = 0;
+        for (int s = S - 1; s >= 0; --s) {
+            const int b = S - 1 - s;                         // byte index from the bottom
+            int v = (int)(((b < 4 ? lo >> (8 * b) : hi >> (8 * (b - 4)))) & 0xFFu) + carry;
+            if (s > 0 && v >= 128) { v -= 256; carry = 1; } else carry = 0;
+            // row-normalised: the slice holds q 2^(w - T); 2^ei is applied in the
             // GEMM epilogue, so no product leaves the FP32 range whatever the row scale
-            const float piece = ldexpf((float)q, w - 6 * S);                  // exact: q has <= 7 bits
+            const float p2 = __int_as_float((127 + 8 * b - T) << 23);   // 2^(w - T), w = 8b
+            const float piece = (float)(sgn * v) * p2;       // exact: |q| <= 2^7
             out[s * plane + (size_t)i * Kp + k] = __float2bfloat16_rn(piece);
         }
     }
@@ -638,8 +699,8 @@ int num_sms() {
 TcMode tc_mode(int prec) {
     TcMode m;
     if (prec == TC_BF16) { m.S = 1; m.L = 0; m.exact = 0; }
-    else if (prec == TC_FP32) { m.S = 5; m.L = 4; m.exact = 1; }   // ~30 bits: FP32-class or better
-    else { m.S = 9; m.L = 8; m.exact = 1; }
+    else if (prec == TC_FP32) { m.S = 4; m.L = 3; m.exact = 1; }   // 31 bits: FP32-class or better
+    else { m.S = 7; m.L = 6; m.exact = 1; }                        // 55 bits: FP64-class
     return m;
 }
 
@@ -717,7 +778,13 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.S = mode.S;
     P.batch = batch;
     P.stride = stride;
-    P.chunk = mode.exact ? 2048 : ((K + BK - 1) / BK) * BK;
+    P.chunk = mode.exact ? 512 : ((K + BK - 1) / BK) * BK;   // 512 * 2^14 = 2^23
+    // Horner in int64 up to the last diagonal d with |C| <= 1.01 K 2^(14+8d) < 2^62
+    P.dint = -1;
+    if (mode.exact)
+        for (int d = 0; d <= mode.L; ++d)
+            if (1.01 * (double)K * std::ldexp(1.0, 14 + 8 * d) < std::ldexp(1.0, 62)) P.dint = d;
+    P.ubase = mode.exact ? 14 + 8 * std::max(P.dint, 0) : 0;
     P.tiles_m = (M + BM - 1) / BM;
     P.tiles_n = (N + BN - 1) / BN;
     P.epi = epi;
@@ -729,6 +796,12 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     if (!attr) {
         cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
         cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, tc_gemm_kernel<false>) == cudaSuccess && fa.maxThreadsPerBlock < THREADS) {
+            std::fprintf(stderr, "tc_gemm: kernel uses %d registers; at most %d threads per block fit\n",
+                         fa.numRegs, fa.maxThreadsPerBlock);
+            return -1;
+        }
         attr = true;
     }
     if (ev_begin) cudaEventRecord(ev_begin, st);
@@ -748,7 +821,10 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        if (cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true>, ma, mb, P) != cudaSuccess) return -1;
+        if (cudaError_t e = cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true>, ma, mb, P); e != cudaSuccess) {
+            std::fprintf(stderr, "tc_gemm: cluster launch failed: %s\n", cudaGetErrorString(e));
+            return -1;
+        }
     } else {
         const int all_tiles = tiles * batch;
         // persistent (one CTA per SM walking the tiles) unless the caller wants
@@ -758,7 +834,10 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     }
     if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;
-    if (cudaPeekAtLastError() != cudaSuccess) return -1;
+    if (cudaError_t e = cudaPeekAtLastError(); e != cudaSuccess) {
+        std::fprintf(stderr, "tc_gemm: launch failed: %s\n", cudaGetErrorString(e));
+        return -1;
+    }
     return EPI_WARPS * tiles;   // pair partials per instance: one per (tile, epilogue warp)
 }
 

@@ -15,7 +15,7 @@ import torch
 
 from . import Handle
 
-PAIRS = {"fp64_tc": 45, "fp32": 15, "mixed_bf16": 1, "fp64": None}
+PAIRS = {"fp64_tc": 28, "fp32": 10, "mixed_bf16": 1, "fp64": None}
 
 
 def main():

@@ -45,6 +45,25 @@ def assert_close(got, ref, tol):
     assert rel(got, ref) <= tol
 
 
+# -------------------------------------------------------------------------- products
+
+@pytest.mark.parametrize("M,N,K", [(48, 48, 64), (200, 136, 300), (512, 512, 64), (520, 300, 100),
+                                   (2048, 2048, 64)])
+@pytest.mark.parametrize("ta,tb", [(False, False), (True, True)])
+def test_dmma_tiles_against_extended_precision(handle, M, N, K, ta, tb):
+    """The FP64 kernel picks a 16, 32 or 64 CTA tile by the grid it would fill
+    (these shapes reach all three on a 152-SM part); every tile keeps the
+    sequential FP64 bound |C - AB| <= K u (|A| |B|) elementwise."""
+    rng = np.random.default_rng(M + 3 * N + 7 * K)
+    A = rng.standard_normal((K, M) if ta else (M, K))
+    B = rng.standard_normal((N, K) if tb else (K, N))
+    opA, opB = (A.T if ta else A), (B.T if tb else B)
+    ref = opA.astype(np.longdouble) @ opB.astype(np.longdouble)
+    C = host(handle.gemm(dev(A), dev(B), trans_a=ta, trans_b=tb, prec="fp64"))
+    err = (np.abs(C - ref) / (np.abs(opA) @ np.abs(opB))).astype(np.float64).max()
+    assert err <= K * 2.0 ** -53
+
+
 # -------------------------------------------------------------------------- one loop
 
 @pytest.mark.parametrize("m,n", [(64, 48), (48, 64), (1, 1), (200, 136), (136, 200), (130, 130),

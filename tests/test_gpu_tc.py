@@ -2,11 +2,12 @@
 pinv_solve) against extended-precision references and the oracle.
 
 Error bounds, per element, relative to (|op(A)| |op(B)|)_ij:
-* FP64-class (9 exact slices, 45 products): 4e-16 (native FP64 rounding is
-  about K u / sqrt(K) ~ 1e-16 here; the dropped slice products are 2^-60);
-* FP32-class (5 slices, 15 products): 5e-9 (the dropped products with
-  s + t = 5 are each up to 2^-36 of the row/column maxima; the slices hold
-  30 bits);
+* FP64-class (7 exact base-256 slices, 28 products): 4e-16 (native FP64
+  rounding is about K u / sqrt(K) ~ 1e-16 here; the slices hold 55 bits and
+  the dropped products with s + t = 7 are each at most 2^-56 of the row and
+  column maxima);
+* FP32-class (4 slices, 10 products): 5e-9 (31 bits; the dropped products
+  with s + t = 4 are each at most 2^-32 of the row/column maxima);
 * BF16 (one round-to-nearest slice, FP32 accumulation): 2^-7.
 """
 
