@@ -8,9 +8,9 @@
 // F and cut into S balanced base-256 digits: slice s holds q_s 2^(8(S-1-s) - T)
 // with |q_s| <= 128, which bf16 (8 significant bits) holds exactly.  Every
 // product q q' is an integer below 2^14 in magnitude times the power of two of
-// its diagonal d = s + t, so a K-chunk of <= 512 products sums to an integer
-// multiple of that power below 2^23 -- the FP32 tensor-core accumulation is
-// exact.  Each (pair, chunk) accumulator is drained from TMEM and summed
+// its diagonal d = s + t, so every partial sum of a K-chunk of <= 1024 products
+// is an integer multiple of that power of magnitude <= 2^24, which FP32 holds
+// exactly -- the FP32 tensor-core accumulation is exact.  Each (pair, chunk) accumulator is drained from TMEM and summed
 // exactly per diagonal in the epilogue, which adds each diagonal once in FP64
 // and finally applies 2^(e_i + f_j); the only rounding is the FP64 sum of the
 // diagonals, the rounding of F and the truncation of pairs with s + t > L.
@@ -201,17 +201,40 @@ __device__ __forceinline__ void mma_commit(uint64_t* bar) {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
+// 32 columns of this warp's 32 TMEM lanes; the load and its wait are one asm
+// statement, so no use of r[] can be scheduled before the data has arrived.
 __device__ __forceinline__ void tmem_ld32_raw(uint32_t taddr, uint32_t* r) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
           "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
           "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
           "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        : "r"(taddr)
+        : "memory");
+}
+// 64 columns in one load (the whole drain of an epilogue warp), then the wait.
+__device__ __forceinline__ void tmem_ld64_raw(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
+        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
+        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
+          "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
+          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
+          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
+          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
+        : "r"(taddr)
+        : "memory");
 }
 __device__ __forceinline__ void tmem_st32_raw(uint32_t taddr, const uint32_t* r) {
     asm volatile(
@@ -360,10 +383,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         // ---------------------------------------------------------- epilogue (warps 2..9)
         // Drained accumulators of one slice diagonal d = s + t share the unit
         // 2^-(14+8d) (the slices are integer digits times powers of two), so in
-        // the exact modes they are summed exactly as int32: each drain is below
-        // 2^23 units, and at most 255 drains are summed before the int32 sums
-        // are added to the running sums of the tile in TMEM columns [2BN, 4BN)
-        // (once per diagonal, or every 255 drains).  Diagonals 0..dint go into
+        // the exact modes they are summed exactly as int32: each drain is at
+        // most 2^24 units, and at most 127 drains are summed before the int32
+        // sums are added to the running sums of the tile in TMEM columns
+        // [2BN, 4BN) (once per diagonal, or every 127 drains).  Diagonals 0..dint go into
         // an exact int64 by Horner's rule (C <- 256 C + I_d on the integer
         // pipe; the host picks dint so that |C| < 2^62); at the end of diagonal
         // dint C becomes one FP64 value, and later (tiny) diagonals are added in
@@ -413,23 +436,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 const uint32_t taddr = lane_base + buf * BN + half * EPI_COLS;
                 const int uexp = 14 + 8 * d;   // slice products q q' 2^-(14+8d): accumulator / unit
                 const float unit = P.exact ? ldexpf(1.0f, uexp) : 1.0f;
+                {
+                    // the whole drain in one load; the accumulator goes back to the
+                    // MMA issuer before the conversion work
+                    uint32_t r[EPI_COLS];
+                    tmem_ld64_raw(taddr, r);
+                    tc_fence_before();
+                    mbar_arrive(&acce[buf]);
 #pragma unroll
-                for (int c = 0; c < EPI_COLS; c += 32) {
-                    uint32_t r[32];
-                    tmem_ld32_raw(taddr + c, r);
-#pragma unroll
-                    for (int j = 0; j < 32; ++j) {
-                        if (P.exact) iacc[c + j] += __float2int_rn(__uint_as_float(r[j]) * unit);
-                        else iacc[c + j] = (int)r[j];   // one drain only: keep the FP32 bits
+                    for (int j = 0; j < EPI_COLS; ++j) {
+                        if (P.exact) iacc[j] += __float2int_rn(__uint_as_float(r[j]) * unit);
+                        else iacc[j] = (int)r[j];   // one drain only: keep the FP32 bits
                     }
                 }
-                tc_fence_before();
-                mbar_arrive(&acce[buf]);
                 accphase[buf] ^= 1;
                 buf ^= 1;
                 const bool diag_done =
                     (u + 1 == units) || (P.pair_s[(u + 1) / kchunks] + P.pair_t[(u + 1) / kchunks] != d);
-                if (diag_done || ++ndrain == 255) {   // add the int32 sums to the tile sums in TMEM
+                if (diag_done || ++ndrain == 127) {   // add the int32 sums to the tile sums in TMEM
                     ndrain = 0;
                     const bool horner = P.exact && d <= P.dint;
                     const bool shift = horner && have64 && d != hdiag;       // first flush of diagonal d > 0
@@ -778,7 +802,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.S = mode.S;
     P.batch = batch;
     P.stride = stride;
-    P.chunk = mode.exact ? 512 : ((K + BK - 1) / BK) * BK;   // 512 * 2^14 = 2^23
+    P.chunk = mode.exact ? 1024 : ((K + BK - 1) / BK) * BK;   // 1024 * 2^14 = 2^24
     // Horner in int64 up to the last diagonal d with |C| <= 1.01 K 2^(14+8d) < 2^62
     P.dint = -1;
     if (mode.exact)
