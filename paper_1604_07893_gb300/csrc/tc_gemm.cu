@@ -603,76 +603,101 @@ __global__ void col_absmax_kernel(int rows, int K, const double* X, int ld, unsi
     }
 }
 
-// out[s][i][k] (bf16, row length Kp) for 32 x 32 tiles of op(X); zero beyond K.
-// exact = 1: base-256 digit slices of the row-normalised value (slice s holds
-// q_s 2^(8(S-1-s) - T), T = 8S - 1); exact = 0: one round-to-nearest slice.
-__global__ void slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans,
-                             const unsigned long long* mx, int S, int exact, __nv_bfloat16* out,
-                             long long stride) {
-    __shared__ double t[32][33];
+// out[s][i][k] (bf16, row length Kp, Kp a multiple of 8) for 32 x 64 tiles of
+// op(X); zero beyond K.  Each of the 256 threads turns 8 consecutive k of one
+// row into one 16-byte store per slice plane.  exact = 1: base-256 digit
+// slices of the row-normalised value (slice s holds q_s 2^(8(S-1-s) - T),
+// T = 8S - 1); exact = 0: one round-to-nearest slice.
+__global__ void __launch_bounds__(256)
+slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans, const unsigned long long* mx, int S,
+             int exact, __nv_bfloat16* out, long long stride) {
+    __shared__ double t[64][33];   // transposed staging: t[k_local][i_local]
     X += (long long)blockIdx.z * stride;                  // instance blockIdx.z
     out += (size_t)blockIdx.z * S * rows * Kp;
     if (mx) mx += (size_t)blockIdx.z * rows;
-    const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 32;
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-    for (int r = ty; r < 32; r += 8) {
-        double v = 0.0;
-        if (trans) {  // X is K x rows: read along i (contiguous)
-            const int k = k0 + r, i = i0 + tx;
-            if (k < K && i < rows) v = X[(size_t)k * ld + i];
-            t[tx][r] = v;      // t[i_local][k_local]
-        } else {
-            const int i = i0 + r, k = k0 + tx;
-            if (k < K && i < rows) v = X[(size_t)i * ld + k];
-            t[r][tx] = v;
+    const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+    const int tid = threadIdx.x;
+    const int il = tid >> 3, kb = k0 + (tid & 7) * 8;   // row in the tile, first of 8 k
+    const int i = i0 + il;
+    double v[8];
+    if (trans) {   // X is K x rows: coalesced along i into shared memory, then 8 k per thread
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const int kr = (tid >> 5) + 8 * r, ic = tid & 31;
+            const int k = k0 + kr, ii = i0 + ic;
+            t[kr][ic] = (k < K && ii < rows) ? X[(size_t)k * ld + ii] : 0.0;
         }
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = t[(tid & 7) * 8 + j][il];
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = (i < rows && kb + j < K) ? X[(size_t)i * ld + kb + j] : 0.0;
     }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int i = i0 + r, k = k0 + tx;
-        if (i >= rows || k >= Kp) continue;
-        double x = (k < K) ? t[r][tx] : 0.0;
-        const size_t plane = (size_t)rows * Kp;
-        if (!exact) {
-            out[(size_t)i * Kp + k] = __double2bfloat16(x);
-            for (int s = 1; s < S; ++s) out[s * plane + (size_t)i * Kp + k] = __double2bfloat16(0.0);
-            continue;
-        }
-        // 2^ei > max |row i| (max = f 2^ei, 1/2 <= f < 1)
-        const int ei = exponent_of(mx[i]);
-        // Integer digit extraction (GB300's FP64 pipe is narrow): x = m 2^E with
-        // a 53-bit integer m; U = round(|x| / 2^(ei - T)) <= 2^T is a fixed-point
-        // integer; its bytes u_s (most significant first) become balanced
-        // digits from the least significant up (u_s + carry >= 128: digit
-        // u_s + carry - 256, carry 1); the top digit takes the last carry and
-        // stays <= 128 because U <= 2^T.  Then q_s = +-digit, |q_s| <= 128.
-        const long long bits = __double_as_longlong(x);
+    if (i >= rows || kb >= Kp) return;
+    const size_t plane = (size_t)rows * Kp;
+    uint4* dst = reinterpret_cast<uint4*>(out + (size_t)i * Kp + kb);   // 16-byte aligned: Kp, kb multiples of 8
+    const size_t pstep = plane / 8;                                       // planes apart, in uint4
+    auto pack = [](__nv_bfloat16 a, __nv_bfloat16 b) {
+        return (uint32_t)__bfloat16_as_ushort(a) | ((uint32_t)__bfloat16_as_ushort(b) << 16);
+    };
+    if (!exact) {   // one slice, FP64 rounded to nearest bf16 directly
+        uint4 w;
+        w.x = pack(__double2bfloat16(v[0]), __double2bfloat16(v[1]));
+        w.y = pack(__double2bfloat16(v[2]), __double2bfloat16(v[3]));
+        w.z = pack(__double2bfloat16(v[4]), __double2bfloat16(v[5]));
+        w.w = pack(__double2bfloat16(v[6]), __double2bfloat16(v[7]));
+        dst[0] = w;
+        const uint4 zero = make_uint4(0, 0, 0, 0);
+        for (int s = 1; s < S; ++s) dst[s * pstep] = zero;
+        return;
+    }
+    // 2^ei > max |row i| (max = f 2^ei, 1/2 <= f < 1)
+    const int ei = exponent_of(mx[i]);
+    const int T = 8 * S - 1;
+    // Integer digit extraction (GB300's FP64 pipe is narrow): x = m 2^E with a
+    // 53-bit integer m; U = round(|x| / 2^(ei - T)) <= 2^T is a fixed-point
+    // integer; its bytes (most significant first) become balanced digits from
+    // the least significant up (byte + carry >= 128: digit byte + carry - 256,
+    // carry 1); the top digit takes the last carry and stays <= 128 because
+    // U <= 2^T.  Then q_s = +-digit, |q_s| <= 128.  A NaN or infinity poisons
+    // every slice so that the product reports it.
+    uint32_t lo[8], hi[8];
+    int sgn[8], carry[8];
+    bool bad[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const long long bits = __double_as_longlong(v[j]);
         const int bexp = (int)((bits >> 52) & 0x7FF);
-        if (bexp == 0x7FF) {   // NaN/Inf: poison every slice so the product reports it
-            for (int s = 0; s < S; ++s) out[s * plane + (size_t)i * Kp + k] = __float2bfloat16_rn(NAN);
-            continue;
-        }
+        bad[j] = bexp == 0x7FF;
         const long long mant = (bits & 0xFFFFFFFFFFFFFLL) | (bexp ? (1LL << 52) : 0LL);
-        const int E = (bexp ? bexp : 1) - 1075;             // x = mant * 2^E
-        const int T = 8 * S - 1;
-        const int shift = E - (ei - T);                     // U = mant * 2^shift
+        const int E = (bexp ? bexp : 1) - 1075;         // x = mant * 2^E
+        const int shift = E - (ei - T);                 // U = mant * 2^shift
         unsigned long long U;
         if (shift >= 0) U = (unsigned long long)mant << shift;   // <= 2^T <= 2^55 since |x| < 2^ei
         else if (shift > -62) U = (unsigned long long)((mant + (1LL << (-shift - 1))) >> (-shift));
         else U = 0;
-        const unsigned lo = (unsigned)U, hi = (unsigned)(U >> 32);
-        const int sgn = bits < 0 ? -1 : 1;
-        int carry = 0;
-        for (int s = S - 1; s >= 0; --s) {
-            const int b = S - 1 - s;                         // byte index from the bottom
-            int v = (int)(((b < 4 ? lo >> (8 * b) : hi >> (8 * (b - 4)))) & 0xFFu) + carry;
-            if (s > 0 && v >= 128) { v -= 256; carry = 1; } else carry = 0;
-            // row-normalised: the slice holds q 2^(w - T); 2^ei is applied in the
-            // GEMM epilogue, so no product leaves the FP32 range whatever the row scale
-            const float p2 = __int_as_float((127 + 8 * b - T) << 23);   // 2^(w - T), w = 8b
-            const float piece = (float)(sgn * v) * p2;       // exact: |q| <= 2^7
-            out[s * plane + (size_t)i * Kp + k] = __float2bfloat16_rn(piece);
+        lo[j] = (uint32_t)U;
+        hi[j] = (uint32_t)(U >> 32);
+        sgn[j] = bits < 0 ? -1 : 1;
+        carry[j] = 0;
+    }
+    for (int s = S - 1; s >= 0; --s) {
+        const int b = S - 1 - s;                                     // byte index from the bottom
+        const float p2 = __int_as_float((127 + 8 * b - T) << 23);   // 2^(8b - T)
+        float f[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            int d = (int)(((b < 4 ? lo[j] >> (8 * b) : hi[j] >> (8 * (b - 4)))) & 0xFFu) + carry[j];
+            if (s > 0 && d >= 128) { d -= 256; carry[j] = 1; } else carry[j] = 0;
+            f[j] = bad[j] ? __int_as_float(0x7FC00000) : (float)(sgn[j] * d) * p2;   // exact: |q| <= 2^7
         }
+        uint4 w;   // every value is exact in bf16
+        w.x = pack(__float2bfloat16_rn(f[0]), __float2bfloat16_rn(f[1]));
+        w.y = pack(__float2bfloat16_rn(f[2]), __float2bfloat16_rn(f[3]));
+        w.z = pack(__float2bfloat16_rn(f[4]), __float2bfloat16_rn(f[5]));
+        w.w = pack(__float2bfloat16_rn(f[6]), __float2bfloat16_rn(f[7]));
+        dst[s * pstep] = w;
     }
 }
 
@@ -773,11 +798,10 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
         *kernels += 2;
     }
     {
-        dim3 blk(32, 8);
-        dim3 ga((Kp + 31) / 32, (M + 31) / 32, batch), gb((Kp + 31) / 32, (N + 31) / 32, batch);
-        slice_kernel<<<ga, blk, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, mode.exact ? ea : nullptr,
+        dim3 ga((Kp + 63) / 64, (M + 31) / 32, batch), gb((Kp + 63) / 64, (N + 31) / 32, batch);
+        slice_kernel<<<ga, 256, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, mode.exact ? ea : nullptr,
                                          mode.S, mode.exact, sa, stride);
-        slice_kernel<<<gb, blk, 0, st>>>(N, K, Kp, B, ldb, transB ? 0 : 1, mode.exact ? eb : nullptr,
+        slice_kernel<<<gb, 256, 0, st>>>(N, K, Kp, B, ldb, transB ? 0 : 1, mode.exact ? eb : nullptr,
                                          mode.S, mode.exact, sb, stride);
         *kernels += 2;
     }

@@ -142,6 +142,23 @@ def test_gemm_fp64_tc_wide_dynamic_range(handle):
     assert check_gemm(handle, A, B, False, False, "fp64_tc") <= BOUND["fp64_tc"]
 
 
+@pytest.mark.parametrize("K", [20000, 70000])
+def test_gemm_long_k_guards(handle, K):
+    """Long inner dimensions exercise the epilogue's guards: at K = 20000 a
+    diagonal has more than 127 drains of 1024-deep chunks (the int32 sums are
+    flushed mid-diagonal); at K = 70000 the exact int64 Horner sum stops one
+    diagonal earlier (|C| must stay below 2^62) and the rest is added in FP64.
+    Extremal digits: every entry +-1 times a power of two, so slice products
+    reach their bound 2^14."""
+    rng = np.random.default_rng(K)
+    M, N = 24, 40
+    A = rng.choice([-1.0, 1.0], (M, K)) * (1.0 - 2.0 ** -53)
+    B = rng.standard_normal((K, N))
+    B[:, 0] = 1.0 - 2.0 ** -53   # a column of equal extremal entries: long same-sign runs
+    A[0, :] = 1.0 - 2.0 ** -53
+    assert check_gemm(handle, A, B, False, False, "fp64_tc") <= BOUND["fp64_tc"]
+
+
 def test_low_precision_on_rectangular_requires_the_finish(handle):
     """Theorem 6.2: on m != n the block the loop does not contract keeps the
     BF16/FP32 rounding; the library refuses such a schedule without the finish."""
