@@ -1025,7 +1025,9 @@ int group_complete(Group& G) {
 
 // The finish step for every instance that ended with PINV_OK: restore its kept
 // iterate, project, run one more loop, copy out.
-int group_finish(Group& G) {
+// Issue the finish step of a group on its stream (no synchronisation; see
+// group_finish).
+int group_finish_issue(Group& G) {
     if (!G.finish || G.err) return G.err;
     Ctx& c = G.c;
     std::vector<int> mask(G.batch, 0);
@@ -1041,7 +1043,13 @@ int group_finish(Group& G) {
     cleanup_f64(c, &d0, c.X[0], c.X[1]);
     if (pm_loop_f64(c, c.X[1], c.X[0]) < 0) return G.err = PINV_ERR_CUDA;
     scatter_out(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[0], G.M, c.stride, G.st);
-    CK(cudaStreamSynchronize(G.st));
+    CK(cudaPeekAtLastError());
+    return PINV_OK;
+}
+
+int group_finish(Group& G) {
+    if (group_finish_issue(G)) return G.err;
+    if (G.finish) CK(cudaStreamSynchronize(G.st));
     return PINV_OK;
 }
 
@@ -1063,8 +1071,11 @@ int run_groups(std::vector<std::unique_ptr<Group>>& groups) {
         for (auto& g : groups)
             if (!g->err && g->active() && g->k < g->max_iter) { if (group_complete(*g)) rc = g->err; }
     }
+    // the finishes of all groups overlap on their streams, then each is waited for
+    for (auto& g : groups)
+        if (int r = group_finish_issue(*g)) { if (!g->err) g->err = r; rc = r; }
     for (auto& g : groups) {
-        if (group_finish(*g)) rc = g->err;
+        if (!g->err && g->finish && cudaStreamSynchronize(g->st) != cudaSuccess) rc = g->err = PINV_ERR_CUDA;
         for (auto& I : g->info) if (g->err && I.status == PINV_OK) I.status = g->err;
         g->release();
     }
