@@ -42,17 +42,17 @@ inline Epilogue epi_none() {
 // sym_out (M == N, no partials): the product is known to be symmetric; only
 // tiles on or above the diagonal are computed, off-diagonal ones also written
 // transposed.
-// tile: the CTA tile edge, 64, 32 or 16 (gemm_f64_pick_tile chooses).
+// tile: the CTA tile edge, 64, 32, 16 or 8 (gemm_f64_pick_tile chooses).
 // Returns the pair partials per instance (the CTA count) or -1 on a launch error.
 int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
              const double* B, int ldb, bool transB, const Epilogue& epi, cudaStream_t st,
              int batch = 1, long long stride = 0, bool sym_out = false, int tile = 64);
 int gemm_f64_ctas(int M, int N, int tile);
-// The largest tile whose grid (times the batch) still covers `sms` CTAs, else 16.
+// The largest tile whose grid (times the batch) still covers `sms` CTAs, else 8.
 int gemm_f64_pick_tile(int M, int N, int batch, int sms);
 // Pair partials a product may need per instance, over every engine and tile:
-// at most 16 per 64 x 64 block of the output (the 16 x 16 DMMA tile).
-inline size_t partial_pairs_bound(size_t rows, size_t cols) { return 16 * ((rows + 63) / 64) * ((cols + 63) / 64); }
+// at most 64 per 64 x 64 block of the output (the 8 x 8 DMMA tile).
+inline size_t partial_pairs_bound(size_t rows, size_t cols) { return 64 * ((rows + 63) / 64) * ((cols + 63) / 64); }
 
 // Deterministic sum of `count` (pair) partials into out[0..1] (device); with
 // batch > 1, instance b sums partials[2*count*b ...] into out[2b], out[2b+1].

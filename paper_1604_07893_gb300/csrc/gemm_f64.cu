@@ -49,18 +49,22 @@ __device__ __forceinline__ double loadB(const GemmArgs& g, int k, int j) {
 }
 
 // BM x BN CTA tile (BM == BN); each of the four warps owns a (BM/2) x (BN/2)
-// quadrant of (BM/16) x (BN/16) 8x8 accumulators.
+// quadrant of (BM/16) x (BN/16) 8x8 accumulators.  BM = 8: one 8x8 tile per
+// CTA whose four warps split each K-slab (one k-group of 4 each) and add
+// their accumulators through shared memory at the end.
 template <int BM, int BN>
 __global__ void __launch_bounds__(THREADS)
 gemm_f64_kernel(GemmArgs g, Epilogue epi) {
-    constexpr int FM = BM / 16, FN = BN / 16;          // 8x8 fragments per warp
+    constexpr bool KS = BM == 8;                        // K split across the warps
+    constexpr int FM = KS ? 1 : BM / 16, FN = KS ? 1 : BN / 16;   // 8x8 fragments per warp
     constexpr int NA = BM * BK / THREADS, NB = BK * BN / THREADS;   // slab elements per thread
     __shared__ double As[BM][BK + APAD];
     __shared__ double Bs[BK][BN + BPAD];
     __shared__ double red[2][THREADS / 32];
+    __shared__ double ksum[KS ? 4 : 1][32][2];
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int wm = warp >> 1, wn = warp & 1;
+    const int wm = KS ? 0 : warp >> 1, wn = KS ? 0 : warp & 1;
     const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
     if (g.sym && blockIdx.y > blockIdx.x) return;   // lower triangle: mirrored by its partner
     const bool mirror = g.sym && blockIdx.y != blockIdx.x;
@@ -127,7 +131,7 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
         __syncthreads();
         if (kt + 1 < ktiles) fetch((kt + 1) * BK);
 #pragma unroll
-        for (int kk = 0; kk < BK; kk += 4) {
+        for (int kk = KS ? 4 * warp : 0; kk < BK; kk += KS ? BK : 4) {
             double af[FM], bf[FN];
 #pragma unroll
             for (int i = 0; i < FM; ++i) af[i] = As[wm * (BM / 2) + i * 8 + (lane >> 2)][kk + (lane & 3)];
@@ -140,10 +144,18 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
         }
     }
 
+    if constexpr (KS) {   // add the four warps' partial sums; warp 0 runs the epilogue
+        ksum[warp][lane][0] = acc[0][0][0];
+        ksum[warp][lane][1] = acc[0][0][1];
+        __syncthreads();
+        if (warp == 0)
+            for (int w = 1; w < 4; ++w) { acc[0][0][0] += ksum[w][lane][0]; acc[0][0][1] += ksum[w][lane][1]; }
+    }
+
     // ---- fused epilogue
     double sd = 0.0, sx = 0.0;
 #pragma unroll
-    for (int i = 0; i < FM; ++i) {
+    for (int i = 0; i < FM && (!KS || warp == 0); ++i) {
         const int row = m0 + wm * (BM / 2) + i * 8 + (lane >> 2);
 #pragma unroll
         for (int j = 0; j < FN; ++j) {
@@ -198,9 +210,9 @@ gemm_f64_kernel(GemmArgs g, Epilogue epi) {
 int gemm_f64_ctas(int M, int N, int tile) { return ((N + tile - 1) / tile) * ((M + tile - 1) / tile); }
 
 int gemm_f64_pick_tile(int M, int N, int batch, int sms) {
-    for (int tile : {64, 32})
+    for (int tile : {64, 32, 16})
         if ((long long)gemm_f64_ctas(M, N, tile) * batch >= sms) return tile;
-    return 16;
+    return 8;
 }
 
 int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
@@ -212,6 +224,7 @@ int gemm_f64(int M, int N, int K, const double* A, int lda, bool transA,
     if (tile == 64) gemm_f64_kernel<64, 64><<<grid, THREADS, 0, st>>>(g, epi);
     else if (tile == 32) gemm_f64_kernel<32, 32><<<grid, THREADS, 0, st>>>(g, epi);
     else if (tile == 16) gemm_f64_kernel<16, 16><<<grid, THREADS, 0, st>>>(g, epi);
+    else if (tile == 8) gemm_f64_kernel<8, 8><<<grid, THREADS, 0, st>>>(g, epi);
     else return -1;
     if (cudaPeekAtLastError() != cudaSuccess) return -1;
     return grid.x * grid.y;   // pair partials per instance

@@ -47,13 +47,14 @@ def assert_close(got, ref, tol):
 
 # -------------------------------------------------------------------------- products
 
-@pytest.mark.parametrize("M,N,K", [(48, 48, 64), (200, 136, 300), (512, 512, 64), (520, 300, 100),
-                                   (2048, 2048, 64)])
+@pytest.mark.parametrize("M,N,K", [(48, 48, 64), (200, 136, 300), (256, 200, 96), (512, 512, 64),
+                                   (520, 300, 100), (2048, 2048, 64), (7, 5, 3)])
 @pytest.mark.parametrize("ta,tb", [(False, False), (True, True)])
 def test_dmma_tiles_against_extended_precision(handle, M, N, K, ta, tb):
-    """The FP64 kernel picks a 16, 32 or 64 CTA tile by the grid it would fill
-    (these shapes reach all three on a 152-SM part); every tile keeps the
-    sequential FP64 bound |C - AB| <= K u (|A| |B|) elementwise."""
+    """The FP64 kernel picks an 8 (K split over the warps), 16, 32 or 64 CTA
+    tile by the grid it would fill (these shapes reach all four on a 152-SM
+    part); every tile keeps the FP64 bound |C - AB| <= K u (|A| |B|)
+    elementwise."""
     rng = np.random.default_rng(M + 3 * N + 7 * K)
     A = rng.standard_normal((K, M) if ta else (M, K))
     B = rng.standard_normal((N, K) if tb else (K, N))
