@@ -16,7 +16,7 @@ import pytest
 
 from oracle import hyperpower as H
 from paper_1604_07893_gb300 import workloads as W
-from tests.helpers import pinv_closed_form, rel
+from tests.helpers import drazin_closed_form, pinv_closed_form, rel
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -232,3 +232,20 @@ def test_autotune_routes_small_products_and_keeps_parity():
             assert max(info["penrose"]) <= 1e-9
     finally:
         h.close()
+
+
+def test_drazin_order18_finish_parity(handle):
+    """The Drazin family with the order-18 stop (step < 1e-2) and the finish
+    A^l X^{2l+1} A^l + one loop, FP64-class products: same loop count as the
+    oracle, result within 1e-9 of the oracle and of the closed form."""
+    d = W.drazin_index2(256, 64, seed=2)
+    alpha = 1.0 / np.trace(np.linalg.matrix_power(d.A, 3))
+    ref, oinfo = H.solve(d.A, H.x0_drazin(d.A, 2, alpha), tol=1e-2, stop=H.STOP_ORDER18, alpha=alpha,
+                         finish="drazin", drazin_index=2)
+    X, info = handle.solve(dev(d.A), kind="drazin", drazin_index=2, alpha=0.0, tol=1e-2, stop="order18",
+                           finish="clean", prec="fp64_tc", check=True)
+    assert info["status"] == 0
+    assert info["iters"] == oinfo.iters
+    assert rel(X.cpu().numpy(), ref) <= 1e-9
+    assert rel(X.cpu().numpy(), drazin_closed_form(d)) <= 1e-9
+    assert max(info["drazin"]) <= 1e-9
