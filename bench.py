@@ -167,28 +167,49 @@ def solve_kwargs(prec, alpha):
                 switch_tol=0.5, finish="clean")
 
 
-def cpu_oracle_sample(A, alpha, loops_per_solve, budget_s=30.0):
+# Loops of one solve of the headline workload with the bench's settings, as the
+# oracle itself runs them (order-18 stop at 1e-2, stabilised after a step
+# below 0.5, cleanup finish): 8 loops, one of them stabilised.  The GPU solve
+# reports the same counts.
+ORACLE_LOOPS, ORACLE_STAB_LOOPS = 8, 1
+
+
+def cpu_oracle_sample(A, alpha, loops_per_solve=ORACLE_LOOPS, stab_loops=ORACLE_STAB_LOOPS, budget_s=30.0):
     """Time the FP64 oracle as it stands on a bounded sample of the workload:
-    its naive order-18 loop (17 products + the update) and the cleanup
-    projection on the full 4096 x 3072 matrix, then extrapolate to the loops of
-    one solve."""
+    its naive order-18 loop (17 products + the update), its stabilised loop
+    (the naive loop, then X A X) and the cleanup projection on the full
+    4096 x 3072 matrix, then extrapolate to the loops of one solve."""
     from oracle import hyperpower as H
     X0 = H.x0_moore_penrose(A, alpha)
     t0 = time.perf_counter()
     X1 = H.hyperpower_step(A, X0, side="left")
     t_loop = time.perf_counter() - t0
-    t_clean = None
-    if t_loop < budget_s / 2:
+    t_stab = t_clean = None
+    if t_loop < budget_s / 3:
+        t0 = time.perf_counter()
+        H.stabilised_step(A, X0, side="left")
+        t_stab = time.perf_counter() - t0
         t0 = time.perf_counter()
         H.cleanup_moore_penrose(A, X1)
         t_clean = time.perf_counter() - t0
-    per_solve = t_loop * loops_per_solve + (t_clean if t_clean is not None else t_loop)
+    t_stab_ = t_stab if t_stab is not None else t_loop
+    per_solve = (t_loop * (loops_per_solve - stab_loops) + t_stab_ * stab_loops
+                 + (t_clean if t_clean is not None else t_loop))
     cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
     return {"value": 1.0 / per_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"one naive loop ({t_loop:.2f} s) and one cleanup projection "
-                       f"({(t_clean or float('nan')):.2f} s) of the full 4096x3072 problem, "
-                       f"extrapolated to {loops_per_solve} loops + finish per solve"),
+            "sample": (f"one naive loop ({t_loop:.2f} s), one stabilised loop ({t_stab_:.2f} s) and one "
+                       f"cleanup projection ({(t_clean or float('nan')):.2f} s) of the full 4096x3072 "
+                       f"problem, extrapolated to {loops_per_solve} loops ({stab_loops} stabilised) "
+                       f"+ the cleanup per solve"),
             "s_per_solve": per_solve}
+
+
+def bench_config(prec, world):
+    """The `config` of the headline line, shared by both arms."""
+    return {"workload": WORKLOAD, "m": M, "n": N, "rank": RANK, "s_range": [S_MIN, 1.0],
+            "prec": prec, "variant": "stabilized", "switch_tol": 0.5, "stop": "order18",
+            "tol": 1e-2, "finish": "clean",
+            "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (A 100 MB, workspace 0.8 GB)"}
 
 
 def run_reference(args):
@@ -196,10 +217,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     w, alpha = workload()
-    loops = 9   # loops of one solve on this workload (8 loops + the finish loop)
     times = []
     for i in range(args.warmup + args.steps):
-        s = cpu_oracle_sample(w.A, alpha, loops)
+        s = cpu_oracle_sample(w.A, alpha)
         if i >= args.warmup:
             times.append(s["s_per_solve"])
     per = statistics.mean(times)
@@ -207,8 +227,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "m": M, "n": N, "rank": RANK,
-                                            "inputs": "larger than L2"},
+            "data": "synthetic", "config": bench_config(args.prec, world),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": s["cores"], "kind": "oracle",
                              "sample": s["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -322,11 +341,9 @@ def run_ours(args):
     sorted_ms = sorted(per_step)
     p50 = statistics.median(per_step)
     p99 = sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(0.99 * len(sorted_ms))) - 1)]
-    loops_per_solve = infos[-1]["loops_run"] + 1
-
     cpu = None
-    if not args.no_cpu and world == 1:
-        cpu = cpu_oracle_sample(w.A, alpha, loops_per_solve)
+    if not args.no_cpu and world == 1:   # the loop counts this solve ran (the oracle runs the same)
+        cpu = cpu_oracle_sample(w.A, alpha, infos[-1]["iters"], infos[-1]["stabilized_loops"])
         cpu.pop("s_per_solve", None)
 
     line = {
@@ -336,10 +353,7 @@ def run_ours(args):
         "dtype": {"fp64": "f64", "fp64_tc": "bf16 slices (fp64-class)", "fp32": "bf16 slices (fp32-class)",
                   "mixed_bf16": "bf16 + bf16 slices"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M, "n": N, "rank": RANK, "s_range": [S_MIN, 1.0],
-                   "prec": args.prec, "variant": "stabilized", "switch_tol": 0.5, "stop": "order18",
-                   "tol": 1e-2, "finish": "clean",
-                   "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (A 100 MB, workspace 0.8 GB)"},
+        "config": bench_config(args.prec, world),
         "latency_ms": {"p50": p50, "p99": p99},
         "accuracy": {"penrose_max": penrose, "sampled_rows_rel_err": row_err, "meets_1e-9": ok,
                      "loops": infos[-1]["iters"], "stabilized_loops": infos[-1]["stabilized_loops"]},
