@@ -252,7 +252,13 @@ STOP_ORDER18 = 2   # relative step < tol (tol = delta, e.g. 1e-2): keep X_{k+1},
 
 
 def stop_measure(Xn: np.ndarray, X: np.ndarray, k: int, alpha: float, mode: int) -> float:
+    """Stop measure of loop k (Eq. stopreliable, or the relative step).  A loop
+    that leaves X unchanged is at the fixed point of Theorem 3.1's iteration
+    and measures 0 under every rule (the relative step would be 0/0 at X = 0,
+    the answer when A = 0 or G = 0)."""
     d = float(fro(Xn - X))
+    if d == 0.0:
+        return 0.0
     if mode in (STOP_REL_FRO, STOP_ORDER18):
         nx = float(fro(X))
         return d / nx if nx > 0 else math.inf

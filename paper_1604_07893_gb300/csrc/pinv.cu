@@ -569,7 +569,11 @@ int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
     return PINV_OK;
 }
 
+// A loop that leaves X unchanged has reached the fixed point of the iteration
+// (X_{k+1} = X_k); its measure is 0 under every rule (the relative rule would
+// otherwise be 0/0 when X = 0, e.g. A = 0 or G = 0, where X = 0 is the answer).
 double stop_measure(const pinv_desc* d, double dx2, double x2, int k, double alpha) {
+    if (dx2 == 0.0) return 0.0;
     const double dx = std::sqrt(dx2);
     if (d->stop == PINV_STOP_PAPER) return dx / (std::pow(18.0, k) * alpha);
     return x2 > 0 ? dx / std::sqrt(x2) : INFINITY;
@@ -649,7 +653,7 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         if (stalled && final_class) { status = PINV_OK; reason = 1; info->iters = k; info->rel_step = prev; break; }
         // divergence guard on the relative step: a convergent loop grows X by at
         // most a factor 18 (|p(r)| <= 18 for |r| <= 1)
-        const double rel = x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY;
+        const double rel = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
         if (rel > 1e3 && k > 0) { status = PINV_ERR_DIVERGED; info->iters = k; break; }
         if (d->variant == PINV_VARIANT_STABILIZED && e < switch_tol && prec_k == fp64_class) stabilise = true;
         prev2 = prev;
@@ -773,7 +777,7 @@ size_t group_bytes(int batch, int M, int N, int prec, bool big2, bool g) {
     return b + 4096;
 }
 
-int group_begin(Group& G) {
+int group_begin_impl(Group& G) {
     pinv_handle* h = G.h;
     const pinv_desc& d0 = G.d[0];
     G.batch = (int)G.d.size();
@@ -892,7 +896,7 @@ int group_begin(Group& G) {
 }
 
 // Issue loop k for every instance (asynchronous; norms land in pinned memory).
-int group_issue(Group& G) {
+int group_issue_impl(Group& G) {
     Ctx& c = G.c;
     double maxprev = 0.0, maxprev2 = 0.0;
     for (int b = 0; b < G.batch; ++b)
@@ -942,6 +946,24 @@ int group_issue(Group& G) {
             if (graph) cudaGraphDestroy(graph);
             return G.err = PINV_ERR_CUDA;
         }
+        // kernel nodes carry the group's stream priority explicitly, so replayed
+        // loops of small problems keep overtaking the CTAs of large ones
+        int prio = 0;
+        if (cudaStreamGetPriority(G.st, &prio) == cudaSuccess && prio != 0) {
+            size_t nn = 0;
+            if (cudaGraphGetNodes(graph, nullptr, &nn) == cudaSuccess && nn) {
+                std::vector<cudaGraphNode_t> nodes(nn);
+                if (cudaGraphGetNodes(graph, nodes.data(), &nn) == cudaSuccess)
+                    for (cudaGraphNode_t node : nodes) {
+                        cudaGraphNodeType type;
+                        if (cudaGraphNodeGetType(node, &type) != cudaSuccess || type != cudaGraphNodeTypeKernel)
+                            continue;
+                        cudaLaunchAttributeValue v{};
+                        v.priority = prio;
+                        cudaGraphKernelNodeSetAttribute(node, cudaLaunchAttributePriority, &v);
+                    }
+            }
+        }
         cudaGraphExec_t exec = nullptr;
         const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
         cudaGraphDestroy(graph);
@@ -960,7 +982,7 @@ int group_issue(Group& G) {
 }
 
 // Wait for loop k, apply the stop rule per instance, copy out stopped instances.
-int group_complete(Group& G) {
+int group_complete_impl(Group& G) {
     CK(cudaEventSynchronize(G.ev));
     G.in_flight = false;
     int derr;
@@ -977,9 +999,7 @@ int group_complete(Group& G) {
         pinv_info& I = G.info[b];
         const pinv_desc& x = G.d[b];
         const double dx2 = G.pinned[2 * b], x2 = G.pinned[2 * b + 1];
-        double e = std::sqrt(dx2);
-        if (x.stop == PINV_STOP_PAPER) e /= std::pow(18.0, k) * I.alpha;
-        else e = x2 > 0 ? e / std::sqrt(x2) : INFINITY;
+        const double e = stop_measure(&x, dx2, x2, k, I.alpha);
         I.loops_run = k + 1;
         if (k < PINV_HISTORY) { I.history[k] = e; I.precision[k] = (signed char)prec_k; }
         if (G.stabilise) ++I.stabilized_loops;
@@ -992,7 +1012,7 @@ int group_complete(Group& G) {
         else {
             const double pv = G.prev[b];
             const bool stalled = G.stabilise ? (e >= pv) : (pv < 1e-3 && e >= pv * pv);
-            const double rel = x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY;
+            const double rel = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
             if (stalled && final_class) { I.status = PINV_OK; I.stop_reason = 1; I.iters = k; I.rel_step = pv; stop = 1; }
             else if (rel > 1e3 && k > 0) { I.status = PINV_ERR_DIVERGED; I.iters = k; stop = 1; }
             else if (k + 1 >= maxit) { I.status = PINV_ERR_MAXITER; I.stop_reason = 2; I.iters = k + 1; stop = 2; }
@@ -1027,7 +1047,7 @@ int group_complete(Group& G) {
 // iterate, project, run one more loop, copy out.
 // Issue the finish step of a group on its stream (no synchronisation; see
 // group_finish).
-int group_finish_issue(Group& G) {
+int group_finish_issue_impl(Group& G) {
     if (!G.finish || G.err) return G.err;
     Ctx& c = G.c;
     std::vector<int> mask(G.batch, 0);
@@ -1046,6 +1066,18 @@ int group_finish_issue(Group& G) {
     CK(cudaPeekAtLastError());
     return PINV_OK;
 }
+
+// The group steps record their first failure in G.err (a failing CUDA call
+// returns its code through CK without touching the group), so callers that
+// look only at G.err, like the serving rounds, see every error.
+int group_record(Group& G, int r) {
+    if (r && !G.err) G.err = r;
+    return r;
+}
+int group_begin(Group& G) { return group_record(G, group_begin_impl(G)); }
+int group_issue(Group& G) { return group_record(G, group_issue_impl(G)); }
+int group_complete(Group& G) { return group_record(G, group_complete_impl(G)); }
+int group_finish_issue(Group& G) { return group_record(G, group_finish_issue_impl(G)); }
 
 int group_finish(Group& G) {
     if (group_finish_issue(G)) return G.err;
@@ -1171,7 +1203,8 @@ int serve_round(pinv_handle* h) {
     for (size_t i = 0; i < h->running.size();) {
         auto& r = h->running[i];
         Group& G = *r->g;
-        if (G.in_flight || (G.active() && G.k < G.max_iter && !G.err)) { ++i; continue; }
+        // a failed group retires at once (its memory is freed in stream order)
+        if (!G.err && (G.in_flight || (G.active() && G.k < G.max_iter))) { ++i; continue; }
         group_finish(G);
         const auto now = clock::now();
         for (size_t j = 0; j < r->ids.size(); ++j) {

@@ -732,15 +732,49 @@ bool make_map(CUtensorMap* map, const __nv_bfloat16* base, int S, int rows, int 
     return r == CUDA_SUCCESS;
 }
 
+// Per-device state of the engine: SM count and whether the kernel attributes
+// (dynamic shared memory) have been set in that device's context.
+constexpr int kMaxDevices = 64;
+struct DeviceState {
+    int sms = 0;
+    bool attr = false;
+};
+std::mutex g_dev_mu;
+DeviceState g_dev[kMaxDevices];
+
+int current_device() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) dev = 0;
+    return dev;
+}
+
 int num_sms() {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (!g_dev[dev].sms) {
+        int sms = 0;
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
+        g_dev[dev].sms = sms > 0 ? sms : 1;
     }
-    return sms;
+    return g_dev[dev].sms;
+}
+
+// Set the kernels' shared-memory attribute once per device; false if the
+// kernel cannot launch with its block size there.
+bool prepare_kernels() {
+    const int dev = current_device();
+    std::lock_guard<std::mutex> lk(g_dev_mu);
+    if (g_dev[dev].attr) return true;
+    cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+    cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+    cudaFuncAttributes fa;
+    if (cudaFuncGetAttributes(&fa, tc_gemm_kernel<false>) == cudaSuccess && fa.maxThreadsPerBlock < THREADS) {
+        std::fprintf(stderr, "tc_gemm: kernel uses %d registers; at most %d threads per block fit\n",
+                     fa.numRegs, fa.maxThreadsPerBlock);
+        return false;
+    }
+    g_dev[dev].attr = true;
+    return true;
 }
 
 }  // namespace
@@ -840,18 +874,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.rmax = mode.exact ? ea : nullptr;
     P.cmax = mode.exact ? eb : nullptr;
     const int tiles = sym_out ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;   // per instance
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
-        cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
-        cudaFuncAttributes fa;
-        if (cudaFuncGetAttributes(&fa, tc_gemm_kernel<false>) == cudaSuccess && fa.maxThreadsPerBlock < THREADS) {
-            std::fprintf(stderr, "tc_gemm: kernel uses %d registers; at most %d threads per block fit\n",
-                         fa.numRegs, fa.maxThreadsPerBlock);
-            return -1;
-        }
-        attr = true;
-    }
+    if (!prepare_kernels()) return -1;
     if (ev_begin) cudaEventRecord(ev_begin, st);
     if (mc) {
         // one work item per cluster: a vertical pair of tiles

@@ -313,3 +313,36 @@ def test_drazin_normal_on_the_full_annulus(handle, prec):
     assert rel(host(X), drazin_closed_form(d)) < 1e-9
     assert rel(host(X), ref) < 1e-9
     assert max(info["drazin"]) < 1e-9
+
+
+# -------------------------------------------------------------------------- degenerate inputs
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_tc"])
+def test_zero_matrix(handle, prec):
+    """A = 0: X = A^dagger = 0 exactly, found in one loop like the oracle."""
+    A = np.zeros((6, 4))
+    ref, oinfo = H.solve(A, H.x0_moore_penrose(A, 1.0), tol=1e-12, alpha=1.0)
+    X, info = handle.solve(dev(A), alpha=1.0, tol=1e-12, prec=prec)
+    assert info["status"] == 0 and info["iters"] == oinfo.iters == 1
+    assert np.array_equal(host(X), ref)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_tc"])
+@pytest.mark.parametrize("case", ["rank_one", "identity", "scalar", "singular_diagonal"])
+def test_degenerate_closed_forms(handle, prec, case):
+    rng = np.random.default_rng(7)
+    if case == "rank_one":
+        u, v = rng.standard_normal(9), rng.standard_normal(5)
+        A, exact = np.outer(u, v), np.outer(v, u) / (u @ u) / (v @ v)
+    elif case == "identity":
+        A, exact = np.eye(5), np.eye(5)
+    elif case == "scalar":
+        A, exact = np.array([[-4.0]]), np.array([[-0.25]])
+    else:
+        A, exact = np.diag([2.0, 0.5, 0.0]), np.diag([0.5, 2.0, 0.0])
+    alpha = 1.0 / (H.norm_inf(A) * H.norm_inf(A.T))
+    ref, _ = H.solve(A, H.x0_moore_penrose(A, alpha), tol=1e-12, alpha=alpha)
+    X, info = handle.solve(dev(A), alpha=alpha, tol=1e-12, prec=prec)
+    assert info["status"] == 0
+    assert rel(host(X), ref) < 1e-12
+    assert rel(host(X), exact) < 1e-12

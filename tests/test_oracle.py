@@ -407,3 +407,38 @@ def test_drazin_normal_initial_value_for_any_spectrum():
     assert info.status == "converged"
     assert rel(X, drazin_closed_form(d)) < 1e-10
     assert H.drazin_residuals(d.A, X, 2).max() < 1e-10
+
+
+# --------------------------------------------------------------------------
+# degenerate inputs (closed forms)
+# --------------------------------------------------------------------------
+
+def test_zero_matrix_is_a_fixed_point():
+    """A = 0: X0 = alpha A^T = 0 is already A^dagger = 0; the first loop leaves
+    it unchanged and the solve stops there (a zero step measures 0)."""
+    A = np.zeros((6, 4))
+    X, info = H.solve(A, H.x0_moore_penrose(A, 1.0), tol=1e-12, alpha=1.0)
+    assert info.status == "converged" and info.iters == 1
+    assert np.array_equal(X, np.zeros((4, 6)))
+
+
+def test_rank_one_closed_form():
+    """A = u v^T has A^dagger = v u^T / (|u|^2 |v|^2)."""
+    rng = np.random.default_rng(7)
+    u, v = rng.standard_normal(9), rng.standard_normal(5)
+    A = np.outer(u, v)
+    exact = np.outer(v, u) / (u @ u) / (v @ v)
+    alpha = 1.0 / ((u @ u) * (v @ v))          # 1 / sigma_1^2
+    X, info = H.solve(A, H.x0_moore_penrose(A, alpha), tol=1e-12, alpha=alpha)
+    assert info.status in ("converged", "minimum")
+    assert rel(X, exact) < 1e-13
+
+
+@pytest.mark.parametrize("A,exact", [(np.eye(5), np.eye(5)), (np.array([[-4.0]]), np.array([[-0.25]])),
+                                     (np.diag([2.0, 0.5, 0.0]), np.diag([0.5, 2.0, 0.0]))])
+def test_identity_scalar_and_diagonal(A, exact):
+    """Inverses with obvious closed forms: I, a 1 x 1 matrix, a singular diagonal."""
+    alpha = 1.0 / (H.norm_inf(A) * H.norm_inf(A.T))
+    X, info = H.solve(A, H.x0_moore_penrose(A, alpha), tol=1e-12, alpha=alpha)
+    assert info.status in ("converged", "minimum")
+    assert rel(X, exact) < 1e-13
