@@ -213,7 +213,12 @@ int  pinv_solve_batched(pinv_handle *h, int count, const pinv_desc *descs, void 
  * id.  The descriptor is copied; A, G and X must stay valid until pinv_poll
  * reports a final status.  Moore-Penrose and general-G problems with device
  * buffers (PINV_ERR_ARG otherwise); PINV_ERR_BUDGET if the problem's device
- * memory alone exceeds the handle's HBM budget.  Thread-safe with pinv_poll. */
+ * memory alone exceeds the handle's HBM budget.  Thread-safe with pinv_poll.
+ * Each group of requests runs on its own stream (by priority: smaller problems
+ * first).  With the CUDA default of eight hardware queues, streams beyond
+ * eight share queues and a small group's kernels can wait behind a large
+ * group's; a serving process should set CUDA_DEVICE_MAX_CONNECTIONS=32 in its
+ * environment before CUDA is initialised. */
 int  pinv_submit(pinv_handle *h, const pinv_desc *desc, uint64_t *request_id);
 
 /* Drive the serving loop one round and report request `id`.  A round admits

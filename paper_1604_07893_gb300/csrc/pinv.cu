@@ -747,6 +747,9 @@ struct Group {
         if (st) { cudaStreamSynchronize(st); cudaStreamDestroy(st); }
         mem = nullptr; pinned = nullptr; ev = nullptr; st = nullptr;
     }
+    // copy-out masks in the pinned block, after the norms and the error word
+    int* loop_mask() const { return (int*)((char*)pinned + sizeof(double) * 2 * batch + 64); }
+    int* finish_mask() const { return loop_mask() + 2 * batch; }
     bool active() const {
         if (err) return false;
         for (int b = 0; b < batch; ++b)
@@ -817,7 +820,9 @@ int group_begin_impl(Group& G) {
         h->pool_ready = true;
     }
     CK(cudaMallocAsync((void**)&G.mem, bytes, G.st));
-    const size_t pin_bytes = sizeof(double) * 2 * G.batch + sizeof(int) * 2 * G.batch + 64;
+    // pinned block: norms (2 doubles per instance), the error word, then the
+    // copy-out masks of the loops and, separately, of the finish
+    const size_t pin_bytes = sizeof(double) * 2 * G.batch + 64 + 2 * sizeof(int) * 2 * G.batch;
     if (pin_bytes <= kPinnedBlock && !h->pinned_blocks.empty()) {
         G.pinned = (double*)h->pinned_blocks.back();
         h->pinned_blocks.pop_back();
@@ -891,7 +896,11 @@ int group_begin_impl(Group& G) {
     CK(cudaMemcpyAsync(G.dalpha, alpha.data(), sizeof(double) * G.batch, cudaMemcpyHostToDevice, G.st));
     if (gk) scale_copy_batched(G.N, G.M, c.Gd, G.M, G.dalpha, c.X[0], G.M, slab, G.batch, G.st);
     else transpose_scale_batched(G.M, G.N, c.Ad, G.N, G.dalpha, c.X[0], G.M, slab, G.batch, G.st);
-    CK(cudaStreamSynchronize(G.st));
+    // no wait here: the tables and alphas come from pageable host memory, which
+    // cudaMemcpyAsync has consumed when it returns, and everything else is
+    // ordered on the group's stream (a wait would hold the host -- and every
+    // other group -- while this stream queues behind other work)
+    CK(cudaPeekAtLastError());
     return PINV_OK;
 }
 
@@ -1032,11 +1041,13 @@ int group_complete_impl(Group& G) {
     if (G.d[0].variant == PINV_VARIANT_STABILIZED && prec_k == G.fp64_class && all_below_switch) G.stabilise = true;
     G.prev_prec = prec_k;
     if (any_copy) {
-        std::memcpy(G.pinned, mask.data(), sizeof(int) * 2 * G.batch);   // norms already consumed
-        CK(cudaMemcpyAsync(G.dmask, G.pinned, sizeof(int) * 2 * G.batch, cudaMemcpyHostToDevice, G.st));
+        // The host rewrites this mask only after the next loop's event, which the
+        // stream orders after this copy, so no wait is needed.
+        int* pm = G.loop_mask();
+        std::memcpy(pm, mask.data(), sizeof(int) * 2 * G.batch);
+        CK(cudaMemcpyAsync(G.dmask, pm, sizeof(int) * 2 * G.batch, cudaMemcpyHostToDevice, G.st));
         scatter_out(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[G.cur], G.M, c.stride, G.st);
         scatter_out(G.tabX, G.dmask + G.batch, G.batch, G.N, G.M, c.X[G.cur ^ 1], G.M, c.stride, G.st);
-        CK(cudaStreamSynchronize(G.st));   // the masks live in pinned memory reused next loop
     }
     G.cur ^= 1;
     G.k = k + 1;
@@ -1055,8 +1066,9 @@ int group_finish_issue_impl(Group& G) {
     for (int b = 0; b < G.batch; ++b)
         if (G.info[b].status == PINV_OK) { mask[b] = 1; any = true; }
     if (!any) return PINV_OK;
-    std::memcpy(G.pinned, mask.data(), sizeof(int) * G.batch);
-    CK(cudaMemcpyAsync(G.dmask, G.pinned, sizeof(int) * G.batch, cudaMemcpyHostToDevice, G.st));
+    int* pm = G.finish_mask();   // its own block: the last loop's mask copy may still be queued
+    std::memcpy(pm, mask.data(), sizeof(int) * G.batch);
+    CK(cudaMemcpyAsync(G.dmask, pm, sizeof(int) * G.batch, cudaMemcpyHostToDevice, G.st));
     scatter_in(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[0], G.M, c.stride, G.st);
     c.prec_k = G.prec == PINV_PREC_FP64 ? 0 : TC_FP64;   // the finish is FP64-class
     pinv_desc d0 = G.d[0];

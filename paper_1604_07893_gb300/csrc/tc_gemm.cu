@@ -10,24 +10,29 @@
 // product q q' is an integer below 2^14 in magnitude times the power of two of
 // its diagonal d = s + t, so every partial sum of a K-chunk of <= 1024 products
 // is an integer multiple of that power of magnitude <= 2^24, which FP32 holds
-// exactly -- the FP32 tensor-core accumulation is exact.  Each (pair, chunk) accumulator is drained from TMEM and summed
-// exactly per diagonal in the epilogue, which adds each diagonal once in FP64
-// and finally applies 2^(e_i + f_j); the only rounding is the FP64 sum of the
-// diagonals, the rounding of F and the truncation of pairs with s + t > L.
+// exactly -- the FP32 tensor-core accumulation is exact.  Each (pair, chunk)
+// accumulator is drained from TMEM and summed exactly per diagonal in the
+// epilogue, which combines the diagonals (exactly in int64 while the range
+// allows, then in FP64) and finally applies 2^(e_i + f_j); the only rounding is
+// the conversion to FP64 and the FP64 sum of the smallest diagonals, the
+// rounding of F and the truncation of pairs with s + t > L.
 //   FP64-class: 7 slices per operand (55 bits), s + t <= 6 (28 products)
 //   FP32-class: 4 slices (31 bits), s + t <= 3 (10 products)
 //   BF16:       1 slice rounded to nearest (no grid), one product
 //
-// Kernel layout (one persistent CTA per SM, 6 warps):
+// Kernel layout (persistent, one CTA per SM, 10 warps; vertically adjacent
+// tiles run as two-CTA clusters sharing the B tile by TMA multicast):
 //   warp 0      TMA producer: 3-D tensor maps [slice][row][k], 128B swizzle,
 //               ragged edges zero-filled by the TMA unit
 //   warp 1      TMEM allocator + single-thread tcgen05.mma issuer
 //               (M = 128, N = BN, K = 16 per instruction, kind::f16, BF16 in,
 //               FP32 accumulate), two TMEM accumulators so the epilogue drains
 //               one while the next (pair, chunk) accumulates
-//   warps 2..5  epilogue: tcgen05.ld 32x32b, FP64 accumulation in registers,
-//               then the fused combination of Eq. PM (identity, side inputs,
-//               up to three outputs) and the stop-norm partials
+//   warps 2..9  epilogue (two per TMEM lane quarter, 64 columns each): one
+//               tcgen05.ld per drain, exact int32 sums per diagonal, int64
+//               Horner / FP64 tile sums in TMEM, then the fused combination of
+//               Eq. PM (identity, side inputs, up to three outputs) and the
+//               stop-norm partials
 // Every mbarrier wait is bounded; on timeout the kernel records an error code,
 // releases its TMEM and returns.
 
@@ -841,7 +846,10 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     }
     // clusters of two when there are at least two m-blocks to pair (not in symmetric mode)
     const int tiles_m_ = (M + BM - 1) / BM;
-    const bool mc = !sym_out && tiles_m_ >= 2;
+    // (not for launches that release their SMs after every tile: those share the
+    // GPU with other streams by priority, and a CTA pair needs two SMs of one
+    // GPC free at once, which lower-priority single CTAs keep taking)
+    const bool mc = !sym_out && tiles_m_ >= 2 && !one_tile_per_cta;
     CUtensorMap ma, mb;
     if (!make_map(&ma, sa, batch * mode.S, M, Kp, BM) ||
         !make_map(&mb, sb, batch * mode.S, N, Kp, mc ? BN / 2 : BN))
