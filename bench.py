@@ -450,7 +450,7 @@ def run_mp64(args):
 def run_drazin(args):
     """Drazin inverse of a 2048 x 2048 index-2 matrix (C 1536 x 1536, 256 2x2
     Jordan blocks), X0 = A^2 / Tr(A^3), FP64-class products on the tensor cores,
-    order-18 stop (step < 1e-2), finish A^2 X^5 A^2 + one loop; native FP64
+    order-18 stop (step < 1e-2), finish A^2 X^5 A^2 + one order-2 step; native FP64
     beside it."""
     import torch
     from oracle import hyperpower as H
@@ -573,7 +573,7 @@ def run_batched(args):
     _emit({"metric": "pseudoinverses/s, 4096 uneven problems", "value": count / t, "unit": "solves/s",
            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "bf16 + bf16 slices",
            "config": {"workload": f"uneven_batch_{count}", "m": [32, 512], "n": [16, "m"],
-                      "prec": "bf16_fp32 (BF16 growth loops, FP32-class finish, FP64-class projection + loop)",
+                      "prec": "bf16_fp32 (BF16 growth loops, FP32-class loops, FP64-class projection + order-18 loop)",
                       "tol": 1e-6,
                       "finish": "clean",
                       "steps": args.steps},

@@ -107,7 +107,11 @@ typedef enum {
     PINV_FINISH_NONE  = 0,
     PINV_FINISH_CLEAN = 1    /* after the loops: projection X <- (XA)^T X (AX)^T
                                 (Moore-Penrose) or A^l X^{2l+1} A^l (Drazin),
-                                then one more FP64 loop                           */
+                                then one FP64-class order-2 step of the same
+                                family, X <- X + (I - XA) X (Eq. hyper, p = 2),
+                                which squares the projection's rounding (after
+                                schedules with low-precision loops: one
+                                FP64-class order-18 loop instead)              */
 } pinv_finish;
 
 /* --------------------------------------------------------------- structs */

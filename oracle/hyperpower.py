@@ -274,7 +274,7 @@ class SolveInfo:
     stabilised_loops: int = 0
     status: str = "maxiter"           # 'converged' | 'minimum' | 'maxiter' | 'nonfinite'
     history: list = field(default_factory=list)   # stop measure of every loop
-    finished: bool = False            # cleanup + one loop applied
+    finished: bool = False            # cleanup + one order-2 step applied
 
 
 def solve(A: np.ndarray, X0: np.ndarray, tol: float = 1e-12, stop: int = STOP_REL_FRO,
@@ -300,9 +300,10 @@ def solve(A: np.ndarray, X0: np.ndarray, tol: float = 1e-12, stop: int = STOP_RE
     * Stabilised variant: loops after the first one with e < switch_tol use
       the extra X A X (the Pan-Schreiber switch closing Section 7).
     * ``finish`` ('moore_penrose' or 'drazin'): after the loop ends, apply the
-      cleanup projection and one more plain loop.  The projection removes the
-      blocks Theorem 6.2 shows are not contracted (E12, E21 persist, E22
-      grows); the loop after it contracts the range block again.
+      cleanup projection and one order-2 step of the hyperpower family
+      (X <- X(I + R), R = I - AX).  The projection removes the blocks Theorem
+      6.2 shows are not contracted (E12, E21 persist, E22 grows); its own
+      rounding error is first order, which one order-2 step squares.
     max_iter defaults to the paper's 100 (Section 8).
     """
     X, info = _iterate(A, X0, tol, stop, alpha, max_iter, variant, switch_tol, floor_guard,
@@ -314,7 +315,7 @@ def solve(A: np.ndarray, X0: np.ndarray, tol: float = 1e-12, stop: int = STOP_RE
             Xc = cleanup_drazin(A, X, drazin_index)
         else:
             raise ValueError(finish)
-        X = hyperpower_step(A, Xc, p, side or choose_side(*A.shape))
+        X = hyperpower_step(A, Xc, 2, side or choose_side(*A.shape))
         info.finished = True
     return X, info
 

@@ -274,6 +274,26 @@ int read_norms(Ctx& c, int count, double* dx2, double* x2) {
 
 // One loop of Eq. PM in FP64: Xout = Xin (I + R)(T S + mu R2 + psi R4).
 // Returns the number of pair partials written for ||Xout - Xin||, ||Xin||, or < 0.
+// One order-2 step of the hyperpower family (p = 2): X' = X + R X (left) or
+// X + X R, R = I - XA | I - AX; it squares the residual with two products.
+// The finish uses it after the projection when every loop was FP64-class: the
+// projection's error is then first-order rounding, which one squaring removes.
+// After low-precision loops the projection leaves the second-order remainder
+// of their persistent off-diagonal blocks (up to ~1e-2), and a full order-18
+// loop follows instead.
+bool finish_order2(int prec) { return prec == PINV_PREC_FP64 || prec == PINV_PREC_FP64_TC; }
+
+int ns_step_f64(Ctx& c, const double* Xin, double* Xout) {
+    const int s = c.s, m = c.m, n = c.n;
+    double* R = c.sq[0];
+    if (c.left) gemm(c, s, s, m, Xin, m, false, c.A, c.lda, false, epi1(term(R, s, -1, 0, 0, 1)));
+    else        gemm(c, s, s, n, c.A, c.lda, false, Xin, m, false, epi1(term(R, s, -1, 0, 0, 1)));
+    Epilogue e = epi1(term(Xout, m, 1, 1), Xin, m);
+    e.partials = c.partials;
+    if (c.left) return gemm(c, n, m, s, R, s, false, Xin, m, false, e);
+    return gemm(c, n, m, s, Xin, m, false, R, s, false, e);
+}
+
 int pm_loop_f64(Ctx& c, const double* Xin, double* Xout) {
     const int s = c.s, m = c.m, n = c.n;
     double *R = c.sq[0], *R2 = c.sq[1], *R4 = c.sq[2], *L1 = c.sq[3], *L2 = c.sq[4], *T = c.sq[5],
@@ -666,10 +686,13 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
     info->stop_reason = reason;
     c.prec_k = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;   // the finish is FP64-class
     if (status == PINV_OK && d->finish == PINV_FINISH_CLEAN) {
-        // projection, then one FP64 loop (Theorems 6.2 / 7.1: the blocks the
-        // loop does not contract are removed, the range block is re-contracted)
+        // projection, then one order-2 step (Theorems 6.2 / 7.1: the blocks the
+        // loop does not contract are removed; the step squares the projection's
+        // first-order rounding in the range block) -- or one order-18 loop
+        // after low-precision loops
         cleanup_f64(c, d, c.X[cur], c.X[cur ^ 1]);
-        int parts = pm_loop_f64(c, c.X[cur ^ 1], c.X[cur]);
+        int parts = finish_order2(d->prec) ? ns_step_f64(c, c.X[cur ^ 1], c.X[cur])
+                                           : pm_loop_f64(c, c.X[cur ^ 1], c.X[cur]);
         if (parts < 0) return info->status = PINV_ERR_CUDA;
     }
     const double* Xfinal = c.X[cur];
@@ -1073,7 +1096,8 @@ int group_finish_issue_impl(Group& G) {
     c.prec_k = G.prec == PINV_PREC_FP64 ? 0 : TC_FP64;   // the finish is FP64-class
     pinv_desc d0 = G.d[0];
     cleanup_f64(c, &d0, c.X[0], c.X[1]);
-    if (pm_loop_f64(c, c.X[1], c.X[0]) < 0) return G.err = PINV_ERR_CUDA;
+    const int parts = finish_order2(G.prec) ? ns_step_f64(c, c.X[1], c.X[0]) : pm_loop_f64(c, c.X[1], c.X[0]);
+    if (parts < 0) return G.err = PINV_ERR_CUDA;
     scatter_out(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[0], G.M, c.stride, G.st);
     CK(cudaPeekAtLastError());
     return PINV_OK;

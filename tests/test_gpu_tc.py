@@ -236,7 +236,7 @@ def test_autotune_routes_small_products_and_keeps_parity():
 
 def test_drazin_order18_finish_parity(handle):
     """The Drazin family with the order-18 stop (step < 1e-2) and the finish
-    A^l X^{2l+1} A^l + one loop, FP64-class products: same loop count as the
+    A^l X^{2l+1} A^l + one order-2 step, FP64-class products: same loop count as the
     oracle, result within 1e-9 of the oracle and of the closed form."""
     d = W.drazin_index2(256, 64, seed=2)
     alpha = 1.0 / np.trace(np.linalg.matrix_power(d.A, 3))
