@@ -69,6 +69,11 @@ struct TcParams {
     int M, N, K;          // K = logical length (the tensor maps are zero-padded beyond it)
     int npairs;
     int pair_s[64], pair_t[64];
+    // units of work: groups of consecutive pairs of one diagonal that share an
+    // accumulator (more than one pair only when the whole K fits one chunk and
+    // the group's products still sum exactly), times the K-chunks
+    int ngroups;
+    int grp_pair0[64], grp_npair[64];
     int chunk;            // K elements per exact accumulation
     int dint;             // diagonals 0..dint are summed exactly in int64 (Horner), -1: none
     int ubase;            // the tile sums in TMEM are in units of 2^-ubase (row-normalised)
@@ -293,7 +298,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         else tile_coords(tt, P.tiles_m, P.sym, mb, nb);
     };
     const int kchunks = (P.K + P.chunk - 1) / P.chunk;
-    const int units = P.npairs * kchunks;
+    const int units = P.ngroups * kchunks;
 
     if (threadIdx.x == 0) {
         for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], MC ? 2 : 1); }
@@ -323,22 +328,25 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 locate(tile, b, mb, nb);
                 const int m0 = mb * BM, n0 = nb * BN;
                 for (int u = 0; u < units && !*abort_flag; ++u) {
-                    const int pr = u / kchunks, ch = u % kchunks;
+                    const int grp = u / kchunks, ch = u % kchunks;
                     const int k_begin = ch * P.chunk;
                     const int k_end = min(P.K, k_begin + P.chunk);
-                    for (int k = k_begin; k < k_end; k += BK) {
-                        if (!mbar_wait(&empty[stage], phase ^ 1)) {
-                            record_error(P.err, 1); *abort_flag = 1; break;
+                    for (int q = 0; q < P.grp_npair[grp] && !*abort_flag; ++q) {
+                        const int pr = P.grp_pair0[grp] + q;
+                        for (int k = k_begin; k < k_end; k += BK) {
+                            if (!mbar_wait(&empty[stage], phase ^ 1)) {
+                                record_error(P.err, 1); *abort_flag = 1; break;
+                            }
+                            uint8_t* sa = smem + stage * STAGE_BYTES;
+                            mbar_expect_tx(&full[stage], STAGE_BYTES);
+                            tma_load_3d(sa, &mapA, &full[stage], k, m0, b * P.S + P.pair_s[pr]);
+                            if (MC)   // my half of the B tile, to both CTAs (8 KiB = 64 rows)
+                                tma_load_3d_mc(sa + A_TILE_BYTES + crank * (B_TILE_BYTES / 2), &mapB, &full[stage],
+                                               k, n0 + (int)crank * (BN / 2), b * P.S + P.pair_t[pr], (uint16_t)3);
+                            else
+                                tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, b * P.S + P.pair_t[pr]);
+                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
                         }
-                        uint8_t* sa = smem + stage * STAGE_BYTES;
-                        mbar_expect_tx(&full[stage], STAGE_BYTES);
-                        tma_load_3d(sa, &mapA, &full[stage], k, m0, b * P.S + P.pair_s[pr]);
-                        if (MC)   // my half of the B tile, to both CTAs (8 KiB = 64 rows)
-                            tma_load_3d_mc(sa + A_TILE_BYTES + crank * (B_TILE_BYTES / 2), &mapB, &full[stage], k,
-                                           n0 + (int)crank * (BN / 2), b * P.S + P.pair_t[pr], (uint16_t)3);
-                        else
-                            tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, b * P.S + P.pair_t[pr]);
-                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                 }
             }
@@ -353,7 +361,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             uint32_t accphase[2] = {0, 0};
             for (int tile = work0; tile < ntiles && !*abort_flag; tile += wstep) {
                 for (int u = 0; u < units && !*abort_flag; ++u) {
-                    const int ch = u % kchunks;
+                    const int grp = u / kchunks, ch = u % kchunks;
                     const int k_begin = ch * P.chunk;
                     const int k_end = min(P.K, k_begin + P.chunk);
                     if (!mbar_wait(&acce[buf], accphase[buf] ^ 1)) {
@@ -361,22 +369,24 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     }
                     tc_fence_after();
                     const uint32_t d = tmem + buf * BN;
-                    uint32_t acc = 0;
-                    for (int k = k_begin; k < k_end; k += BK) {
-                        if (!mbar_wait(&full[stage], phase)) {
-                            record_error(P.err, 3); *abort_flag = 1; break;
-                        }
-                        tc_fence_after();
-                        const uint32_t a0 = smem_u32(smem + stage * STAGE_BYTES);
-                        const uint32_t b0 = a0 + A_TILE_BYTES;
+                    uint32_t acc = 0;   // the group's pairs all add into one accumulator
+                    for (int q = 0; q < P.grp_npair[grp] && !*abort_flag; ++q) {
+                        for (int k = k_begin; k < k_end; k += BK) {
+                            if (!mbar_wait(&full[stage], phase)) {
+                                record_error(P.err, 3); *abort_flag = 1; break;
+                            }
+                            tc_fence_after();
+                            const uint32_t a0 = smem_u32(smem + stage * STAGE_BYTES);
+                            const uint32_t b0 = a0 + A_TILE_BYTES;
 #pragma unroll
-                        for (int kk = 0; kk < BK / 16; ++kk) {
-                            mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc, acc);
-                            acc = 1;
+                            for (int kk = 0; kk < BK / 16; ++kk) {
+                                mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc, acc);
+                                acc = 1;
+                            }
+                            if (MC) mma_commit_mc(&empty[stage], (uint16_t)3);   // release in both CTAs
+                            else mma_commit(&empty[stage]);
+                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
                         }
-                        if (MC) mma_commit_mc(&empty[stage], (uint16_t)3);   // release in both CTAs
-                        else mma_commit(&empty[stage]);
-                        if (++stage == STAGES) { stage = 0; phase ^= 1; }
                     }
                     mma_commit(&accf[buf]);
                     accphase[buf] ^= 1;
@@ -428,7 +438,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             bool have64 = false;
             bool ok = true;
             for (int u = 0; u < units; ++u) {
-                const int pr = u / kchunks;
+                const int pr = P.grp_pair0[u / kchunks];   // every pair of the group has this diagonal
                 const int d = P.pair_s[pr] + P.pair_t[pr];
                 if (ndrain == 0) {
 #pragma unroll
@@ -457,7 +467,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 accphase[buf] ^= 1;
                 buf ^= 1;
                 const bool diag_done =
-                    (u + 1 == units) || (P.pair_s[(u + 1) / kchunks] + P.pair_t[(u + 1) / kchunks] != d);
+                    (u + 1 == units) || (P.pair_s[P.grp_pair0[(u + 1) / kchunks]] +
+                                         P.pair_t[P.grp_pair0[(u + 1) / kchunks]] != d);
                 if (diag_done || ++ndrain == 127) {   // add the int32 sums to the tile sums in TMEM
                     ndrain = 0;
                     const bool horner = P.exact && d <= P.dint;
@@ -869,6 +880,27 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.batch = batch;
     P.stride = stride;
     P.chunk = mode.exact ? 1024 : ((K + BK - 1) / BK) * BK;   // 1024 * 2^14 = 2^24
+    // Pairs of one diagonal share an accumulator in groups of g when the whole
+    // (padded) K is one chunk: g * K_padded <= 1024 keeps every partial sum of
+    // the group's products within 2^24 units.  Short products then drain once
+    // per group instead of once per pair (for K = 64 once per diagonal).
+    {
+        const int kchunks = (K + P.chunk - 1) / P.chunk;
+        const int klen = kchunks == 1 ? ((K + BK - 1) / BK) * BK : P.chunk;
+        const int g = mode.exact ? std::max(1, 1024 / klen) : 1;
+        P.ngroups = 0;
+        for (int p0 = 0; p0 < P.npairs;) {
+            const int d = P.pair_s[p0] + P.pair_t[p0];
+            int p1 = p0;
+            while (p1 < P.npairs && P.pair_s[p1] + P.pair_t[p1] == d) ++p1;
+            for (int p = p0; p < p1; p += g) {
+                P.grp_pair0[P.ngroups] = p;
+                P.grp_npair[P.ngroups] = std::min(g, p1 - p);
+                ++P.ngroups;
+            }
+            p0 = p1;
+        }
+    }
     // Horner in int64 up to the last diagonal d with |C| <= 1.01 K 2^(14+8d) < 2^62
     P.dint = -1;
     if (mode.exact)

@@ -142,14 +142,16 @@ def test_gemm_fp64_tc_wide_dynamic_range(handle):
     assert check_gemm(handle, A, B, False, False, "fp64_tc") <= BOUND["fp64_tc"]
 
 
-@pytest.mark.parametrize("K", [20000, 70000])
-def test_gemm_long_k_guards(handle, K):
-    """Long inner dimensions exercise the epilogue's guards: at K = 20000 a
-    diagonal has more than 127 drains of 1024-deep chunks (the int32 sums are
-    flushed mid-diagonal); at K = 70000 the exact int64 Horner sum stops one
-    diagonal earlier (|C| must stay below 2^62) and the rest is added in FP64.
-    Extremal digits: every entry +-1 times a power of two, so slice products
-    reach their bound 2^14."""
+@pytest.mark.parametrize("K", [64, 200, 500, 20000, 70000])
+def test_gemm_k_guards(handle, K):
+    """Inner dimensions that exercise the engine's accumulation rules: at
+    K <= 512 several pairs of a diagonal share one accumulator (g pairs with
+    g * K <= 1024); at K = 20000 a diagonal has more than 127 drains of
+    1024-deep chunks (the int32 sums are flushed mid-diagonal); at K = 70000
+    the exact int64 Horner sum stops one diagonal earlier (|C| must stay below
+    2^62) and the rest is added in FP64.  Extremal digits: entries of
+    magnitude 1 - 2^-53 have a leading digit 128, so slice products reach
+    their bound 2^14."""
     rng = np.random.default_rng(K)
     M, N = 24, 40
     A = rng.choice([-1.0, 1.0], (M, K)) * (1.0 - 2.0 ** -53)
