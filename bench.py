@@ -523,9 +523,9 @@ def run_drazin(args):
 def run_batched(args):
     """4096 independent problems, m ~ U{32..512}, n ~ U{16..m}, rank n,
     singular values log-uniform in [1e-3, 1] (Householder-product factors),
-    alpha = 1/s_1^2: one pinv_solve_batched call (BF16 bulk loops, FP32-class,
-    FP64-class last loop) against the FP64 batched path and a sample of
-    per-matrix FP64 solves."""
+    alpha = 1/s_1^2: one pinv_solve_batched call (BF16 bulk loops, FP32-class
+    loops, FP32-class projection and last loop: FP32-finished to 1e-4) against
+    the FP64 batched path and a sample of per-matrix FP64 solves."""
     import ctypes as C
     import torch
     from oracle import hyperpower as H
@@ -573,7 +573,7 @@ def run_batched(args):
     _emit({"metric": "pseudoinverses/s, 4096 uneven problems", "value": count / t, "unit": "solves/s",
            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "bf16 + bf16 slices",
            "config": {"workload": f"uneven_batch_{count}", "m": [32, 512], "n": [16, "m"],
-                      "prec": "bf16_fp32 (BF16 growth loops, FP32-class loops, FP64-class projection + order-18 loop)",
+                      "prec": "bf16_fp32 (BF16 growth loops, FP32-class loops, FP32-class projection + order-18 loop)",
                       "tol": 1e-6,
                       "finish": "clean",
                       "steps": args.steps},

@@ -93,8 +93,8 @@ typedef enum {
     PINV_PREC_BF16_FP32  = 5  /* FP32-finished: BF16 while the step is > 0.5, then
                                  FP32-class to the end (the stop rule ends at the
                                  FP32 noise floor); the finish, if asked, in
-                                 FP64-class products.  Accuracy ~ u_fp32 * kappa;
-                                 problems without a null block                   */
+                                 FP32-class products too.  Accuracy ~ u_fp32 *
+                                 kappa; problems without a null block            */
 } pinv_prec;
 
 typedef enum {

@@ -684,7 +684,7 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         info->iters = k + 1;
     }
     info->stop_reason = reason;
-    c.prec_k = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;   // the finish is FP64-class
+    c.prec_k = fp64_class;   // the finish runs in the schedule's final class
     if (status == PINV_OK && d->finish == PINV_FINISH_CLEAN) {
         // projection, then one order-2 step (Theorems 6.2 / 7.1: the blocks the
         // loop does not contract are removed; the step squares the projection's
@@ -1093,7 +1093,7 @@ int group_finish_issue_impl(Group& G) {
     std::memcpy(pm, mask.data(), sizeof(int) * G.batch);
     CK(cudaMemcpyAsync(G.dmask, pm, sizeof(int) * G.batch, cudaMemcpyHostToDevice, G.st));
     scatter_in(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[0], G.M, c.stride, G.st);
-    c.prec_k = G.prec == PINV_PREC_FP64 ? 0 : TC_FP64;   // the finish is FP64-class
+    c.prec_k = G.fp64_class;   // the finish runs in the schedule's final class
     pinv_desc d0 = G.d[0];
     cleanup_f64(c, &d0, c.X[0], c.X[1]);
     const int parts = finish_order2(G.prec) ? ns_step_f64(c, c.X[1], c.X[0]) : pm_loop_f64(c, c.X[1], c.X[0]);
