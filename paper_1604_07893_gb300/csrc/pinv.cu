@@ -79,6 +79,16 @@ struct pinv_handle {
     int tc_crossover = 0;      // pinv_autotune: FP64-class products below this size use DMMA
     int sms = 1;               // streaming multiprocessors of the device
     std::vector<cudaEvent_t> events;  // profiling pool (pairs), created on demand
+    // small single solves replay their loop as a captured CUDA graph; the graph
+    // refers to workspace buffers only, so it is reused by every later solve
+    // whose loop touches the same buffers (key: those pointers, shapes, flags)
+    struct LoopGraph {
+        std::vector<long long> key;
+        cudaGraphExec_t exec = nullptr;
+        int kernels = 0, gemms = 0;
+    };
+    std::vector<LoopGraph> loop_graphs;
+    cudaStream_t capture_stream = nullptr;    // graphs are captured here, replayed on the caller's stream
     // pinned readback blocks for groups, reused (pinned allocation can
     // synchronise the device, so it happens only when the pool is empty)
     std::vector<void*> pinned_blocks;
@@ -137,6 +147,7 @@ struct Ctx {
     void* tcws = nullptr;   // slice workspace of the tensor-core engine
     size_t tcws_bytes = 0;
     int gemms = 0;
+    bool replay = false;    // loops replayed from cached graphs (A copied into the workspace)
     int kernels = 0;
     bool profile = false;
     int ev_used = 0;        // event pairs recorded since the last harvest
@@ -196,6 +207,8 @@ size_t workspace_bytes(int m, int n, bool drazin, bool host, bool check, int pre
 int ensure_workspace(pinv_handle* h, size_t bytes) {
     if (h->budget && bytes > h->budget) return PINV_ERR_BUDGET;
     if (bytes <= h->ws_bytes) return PINV_OK;
+    for (auto& g : h->loop_graphs) cudaGraphExecDestroy(g.exec);   // they refer to the old workspace
+    h->loop_graphs.clear();
     if (h->ws) {
         CK(cudaDeviceSynchronize());
         CK(cudaFree(h->ws));
@@ -484,6 +497,9 @@ int validate(const pinv_desc* d) {
     return PINV_OK;
 }
 
+// Largest side of a single solve whose loops are replayed from cached graphs.
+constexpr int kReplayMaxDim = 512;
+
 int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
     c.h = h;
     c.st = st;
@@ -495,10 +511,12 @@ int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
     const bool drazin = d->kind == PINV_DRAZIN || d->kind == PINV_DRAZIN_NORMAL;
     const bool host = d->host_buffers != 0;
     const bool check = d->check != 0 || d->finish == PINV_FINISH_CLEAN;
-    size_t bytes = workspace_bytes(d->m, d->n, drazin, host, check, d->prec);
+    c.replay = !c.profile && std::max(d->m, d->n) <= kReplayMaxDim;
+    const bool own_a = host || c.replay;   // A (and G) live in the workspace
+    size_t bytes = workspace_bytes(d->m, d->n, drazin, own_a, check, d->prec);
     int rc = ensure_workspace(h, bytes);
     if (rc) return rc;
-    carve(c, drazin, host, check, d->prec);
+    carve(c, drazin, own_a, check, d->prec);
     c.prec_k = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;
     c.symmetric = iterates_symmetric(d);
     if (host) {
@@ -510,6 +528,11 @@ int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
             CK(cudaMemcpy2DAsync(c.Gd, sizeof(double) * d->m, d->G, sizeof(double) * d->ldg,
                                  sizeof(double) * d->m, d->n, cudaMemcpyHostToDevice, st));
         }
+    } else if (c.replay) {   // device copy, so the cached loop graph never refers to caller memory
+        CK(cudaMemcpy2DAsync(c.Ad, sizeof(double) * d->n, d->A, sizeof(double) * d->lda,
+                             sizeof(double) * d->n, d->m, cudaMemcpyDeviceToDevice, st));
+        c.A = c.Ad;
+        c.lda = d->n;
     } else {
         c.A = d->A;
         c.lda = d->lda;
@@ -599,6 +622,73 @@ double stop_measure(const pinv_desc* d, double dx2, double x2, int k, double alp
     return x2 > 0 ? dx / std::sqrt(x2) : INFINITY;
 }
 
+// Small solves are bound by launch and host overhead: their loop (seven or nine
+// products, the norm reduction and the readback) runs as one cached graph.
+int replay_loop(Ctx& c, int cur, bool stab, double* dx2, double* x2) {
+    pinv_handle* h = c.h;
+    const double* Xk = c.X[cur];
+    double* Xn = c.X[cur ^ 1];
+    std::vector<long long> key = {c.m, c.n, c.left, c.symmetric, c.prec_k, stab, h->tc_crossover,
+                                  (long long)c.A, c.lda, (long long)Xk, (long long)Xn, (long long)c.X[2],
+                                  (long long)c.sq[0], (long long)c.partials, (long long)c.tcws,
+                                  (long long)c.tcws_bytes};
+    pinv_handle::LoopGraph* lg = nullptr;
+    for (auto& g : h->loop_graphs)
+        if (g.key == key) { lg = &g; break; }
+    if (!lg) {
+        if (!h->capture_stream) CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+        if (h->loop_graphs.size() >= 32) {   // bounded cache: drop the oldest
+            cudaGraphExecDestroy(h->loop_graphs.front().exec);
+            h->loop_graphs.erase(h->loop_graphs.begin());
+        }
+        cudaStream_t user = c.st;
+        c.st = h->capture_stream;
+        const int k0 = c.kernels, g0 = c.gemms;
+        CK(cudaStreamBeginCapture(c.st, cudaStreamCaptureModeThreadLocal));
+        int parts = pm_loop_f64(c, Xk, stab ? c.X[2] : Xn);
+        if (stab && parts >= 0) parts = stabilise_f64(c, c.X[2], Xk, Xn);
+        if (parts >= 0) {
+            reduce_pairs(c.partials, parts, h->dsmall, c.st);
+            cudaMemcpyAsync(h->pinned, h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st);
+            cudaMemcpyAsync(h->pinned + 2, h->derr, sizeof(int), cudaMemcpyDeviceToHost, c.st);
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ce = cudaStreamEndCapture(c.st, &graph);
+        c.st = user;
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ie = (parts >= 0 && ce == cudaSuccess && graph) ? cudaGraphInstantiate(&exec, graph, 0)
+                                                                          : cudaErrorUnknown;
+        if (graph) cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+            std::fprintf(stderr, "pinv: loop graph capture failed (%s)\n", cudaGetErrorString(ce != cudaSuccess ? ce : ie));
+            return PINV_ERR_CUDA;
+        }
+        pinv_handle::LoopGraph g;
+        g.key = key;
+        g.exec = exec;
+        g.kernels = c.kernels - k0 + 1;   // + the reduction
+        g.gemms = c.gemms - g0;
+        c.kernels = k0;
+        c.gemms = g0;
+        h->loop_graphs.push_back(std::move(g));
+        lg = &h->loop_graphs.back();
+    }
+    CK(cudaGraphLaunch(lg->exec, c.st));
+    c.kernels += lg->kernels;
+    c.gemms += lg->gemms;
+    CK(cudaStreamSynchronize(c.st));
+    *dx2 = h->pinned[0];
+    *x2 = h->pinned[1];
+    int derr;
+    std::memcpy(&derr, h->pinned + 2, sizeof(int));
+    if (derr) {
+        std::fprintf(stderr, "pinv: tensor-core kernel wait timed out (code %d)\n", derr);
+        cudaMemsetAsync(h->derr, 0, sizeof(int), c.st);
+        return PINV_ERR_TIMEOUT;
+    }
+    return PINV_OK;
+}
+
 int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* info) {
     auto t0 = std::chrono::steady_clock::now();
     std::memset(info, 0, sizeof(*info));
@@ -616,6 +706,9 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
 
     const int max_iter = d->max_iter ? d->max_iter : 100;
     const double switch_tol = d->switch_tol > 0 ? d->switch_tol : 1e-3;
+    // small problems replay each loop from a cached graph (the matrix is in the
+    // workspace then, so the graph serves any later solve of the same shape)
+    const bool replay = c.replay;
     const double floor_guard = 1e-3;
     int cur = 0;              // X[cur] = X_k
     double prev = INFINITY;
@@ -646,16 +739,19 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         if (level == TC_FP32 && (prev <= 1e-4 || (prev < 1e-2 && prev >= 0.25 * prev2))) level = fp64_class;
         const int prec_k = level;
         c.prec_k = prec_k;
-        double* target = stab_now ? c.X[2] : Xn;
-        parts = pm_loop_f64(c, Xk, target);
-        if (stab_now) {
-            parts = stabilise_f64(c, c.X[2], Xk, Xn);
-            ++info->stabilized_loops;
-        }
-        if (parts < 0) return info->status = PINV_ERR_CUDA;
         double dx2, x2;
-        rc = read_norms(c, parts, &dx2, &x2);
-        if (rc) return info->status = rc;
+        if (stab_now) ++info->stabilized_loops;
+        if (replay) {
+            rc = replay_loop(c, cur, stab_now, &dx2, &x2);
+            if (rc) return info->status = rc;
+        } else {
+            double* target = stab_now ? c.X[2] : Xn;
+            parts = pm_loop_f64(c, Xk, target);
+            if (stab_now) parts = stabilise_f64(c, c.X[2], Xk, Xn);
+            if (parts < 0) return info->status = PINV_ERR_CUDA;
+            rc = read_norms(c, parts, &dx2, &x2);
+            if (rc) return info->status = rc;
+        }
         const double e = stop_measure(d, dx2, x2, k, alpha);
         info->loops_run = k + 1;
         if (k < PINV_HISTORY) {
@@ -1289,6 +1385,9 @@ void pinv_destroy(pinv_handle* h) {
     cudaSetDevice(h->device);
     cudaDeviceSynchronize();
     h->running.clear();
+    for (auto& g : h->loop_graphs) cudaGraphExecDestroy(g.exec);
+    h->loop_graphs.clear();
+    if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
     for (void* p : h->pinned_blocks) cudaFreeHost(p);
     h->pinned_blocks.clear();
     if (h->derr) cudaFree(h->derr);

@@ -346,3 +346,19 @@ def test_degenerate_closed_forms(handle, prec, case):
     assert info["status"] == 0
     assert rel(host(X), ref) < 1e-12
     assert rel(host(X), exact) < 1e-12
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_tc"])
+def test_replayed_loops_serve_new_matrices_of_the_same_shape(handle, prec):
+    """Small solves replay their loop from a graph cached in the handle; the
+    matrix is copied into the workspace first, so solving a different matrix
+    of the same shape (and shapes in between) reuses the graph correctly."""
+    cases = [W.rectangular(64, 48, None, 1.0, 1e-2, seed=s) for s in (0, 1)]
+    other = W.rectangular(40, 72, None, 1.0, 1e-2, seed=3)
+    for w in (cases[0], other, cases[1], cases[0]):
+        alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+        ref, oinfo = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+        X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, prec=prec)
+        assert info["status"] == 0 and info["iters"] == oinfo.iters
+        assert rel(host(X), ref) < 1e-12
+        assert rel(host(X), pinv_closed_form(w)) < 1e-12
