@@ -183,6 +183,22 @@ def x0_general(G: np.ndarray, alpha) -> np.ndarray:
     return alpha * G
 
 
+def drazin_index(A: np.ndarray, max_index: int = 16):
+    """ind(A): the smallest nonnegative l with rank(A^{l+1}) = rank(A^l) (the
+    definition given with the Drazin initial value in Section 4).  Ranks by
+    numpy.linalg.matrix_rank (SVD, its default tolerance).  Returns (l, ranks)
+    with ranks[k] = rank(A^k) for k = 0 .. l + 1; l = -1 if it exceeds max_index."""
+    n = A.shape[0]
+    ranks = [n]
+    P = _eye(n, A)
+    for k in range(1, max_index + 2):
+        P = P @ A
+        ranks.append(int(np.linalg.matrix_rank(P)))
+        if ranks[k] == ranks[k - 1]:
+            return k - 1, ranks
+    return -1, ranks
+
+
 def x0_drazin(A: np.ndarray, l: int, alpha=None) -> np.ndarray:
     """X0 = A^l / Tr(A^{l+1}) (Section 4), or alpha A^l when alpha is given."""
     Al = matpow(A, l)

@@ -442,3 +442,35 @@ def test_identity_scalar_and_diagonal(A, exact):
     X, info = H.solve(A, H.x0_moore_penrose(A, alpha), tol=1e-12, alpha=alpha)
     assert info.status in ("converged", "minimum")
     assert rel(X, exact) < 1e-13
+
+
+# --------------------------------------------------------------------------
+# the index of a matrix (Section 4)
+# --------------------------------------------------------------------------
+
+def test_drazin_index_of_example1_is_the_printed_3():
+    """Section 8, Example 1 states l = ind(A) = 3 for the printed matrix."""
+    l, ranks = H.drazin_index(example1())
+    assert l == 3
+    assert ranks[3] == ranks[4] < ranks[2]
+
+
+@pytest.mark.parametrize("case,expected", [("nonsingular", 0), ("diagonal_singular", 1), ("jordan4", 4),
+                                           ("family", 2)])
+def test_drazin_index_by_construction(case, expected):
+    """Index 0 for a nonsingular matrix, 1 for a singular diagonalizable one,
+    k for a nilpotent Jordan block of size k, 2 for the generator's family
+    (2 x 2 Jordan blocks)."""
+    rng = np.random.default_rng(3)
+    if case == "nonsingular":
+        A = rng.standard_normal((6, 6)) + 6 * np.eye(6)
+    elif case == "diagonal_singular":
+        Q = np.linalg.qr(rng.standard_normal((5, 5)))[0]
+        A = Q @ np.diag([2.0, -1.0, 0.5, 0.0, 0.0]) @ Q.T
+    elif case == "jordan4":
+        A = np.diag(np.ones(3), 1)
+    else:
+        A = W.drazin_index2(64, 16, seed=2).A
+    l, ranks = H.drazin_index(A)
+    assert l == expected
+    assert ranks[l] == ranks[l + 1] and (l == 0 or ranks[l - 1] > ranks[l])
