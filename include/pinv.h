@@ -259,6 +259,22 @@ int  pinv_gemm(pinv_handle *h, int M, int N, int K, const double *A, int lda, in
                const double *B, int ldb, int trans_b, double *C, int ldc, pinv_prec prec,
                void *stream);
 
+/* The index of a square matrix, ind(A): the smallest l >= 0 with
+ * rank(A^{l+1}) = rank(A^l) (the definition given with the Drazin initial
+ * value in Section 4), for choosing drazin_index.  rank(A^k) is computed as
+ * trace(A^k (A^k)^dagger) with this library's own Moore-Penrose solve
+ * (FP64-class products, stabilised loops, finish), rounded to the nearest
+ * integer; it counts the singular values the iteration resolves, so nonzero
+ * singular values of A^k must stand well clear of rounding (above ~1e-8 of
+ * the largest).  A (n x n, lda) is a device pointer; ranks (host, may be NULL)
+ * receives rank(A^k) for k = 0 .. ind(A) + 1 and needs max_index + 2 entries.
+ * *index = -1 and PINV_ERR_MAXITER when ind(A) > max_index (at most 64).
+ * Device memory: three n x n matrices, stream-ordered, freed before return.
+ * For a nonsingular A the index is 0; PINV_DRAZIN then needs drazin_index 1
+ * (any l >= ind(A) gives A^D). */
+int  pinv_drazin_index(pinv_handle *h, int n, const double *A, int lda, int max_index, void *stream,
+                       int *index, int *ranks);
+
 /* Autotune the product engine for FP64-class products on this device: time one
  * n x n x n product with the native FP64 (DMMA) kernel and with the tensor-core
  * slice engine for n = 64 ... 1024, and route FP64-class products whose largest

@@ -25,7 +25,7 @@ FINISH = {None: 0, "none": 0, "clean": 1}
 HISTORY = 128
 
 EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_batched", "pinv_submit",
-           "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_autotune",
+           "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_autotune", "pinv_drazin_index",
            "pinv_step_noalloc")
 NOALLOC_MAX_DIM = 128
 
@@ -94,6 +94,8 @@ def load() -> C.CDLL:
     lib.pinv_gemm.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int,
                               C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p]
     lib.pinv_autotune.argtypes = [C.c_void_p, C.c_void_p, P(C.c_int)]
+    lib.pinv_drazin_index.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_int, C.c_void_p, P(C.c_int),
+                                      P(C.c_int)]
     lib.pinv_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
     for name in EXPORTS:
@@ -254,6 +256,20 @@ class Handle:
         if rc != PINV_OK:
             raise PinvError(rc, "pinv_gemm")
         return C
+
+    def drazin_index(self, A, *, max_index: int = 16, stream=None):
+        """pinv_drazin_index: ind(A) of a square device matrix and the ranks of
+        A^0 .. A^(ind+1); raises PinvError if the index exceeds max_index."""
+        n = A.shape[0]
+        if A.shape[1] != n:
+            raise ValueError("square matrix required")
+        idx = C.c_int()
+        ranks = (C.c_int * (max_index + 2))()
+        rc = self._lib.pinv_drazin_index(self._h, n, C.c_void_p(_dev_ptr(A)), A.stride(0), max_index,
+                                         C.c_void_p(_stream_ptr(stream)), C.byref(idx), ranks)
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_drazin_index")
+        return idx.value, [ranks[k] for k in range(idx.value + 2)]
 
     def autotune(self, stream=None) -> int:
         """pinv_autotune: measure the DMMA / tensor-core crossover for FP64-class

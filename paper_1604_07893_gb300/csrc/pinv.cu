@@ -1540,6 +1540,71 @@ int pinv_step(pinv_handle* h, int m, int n, const double* A, int lda, const doub
     return PINV_OK;
 }
 
+int pinv_drazin_index(pinv_handle* h, int n, const double* A, int lda, int max_index, void* stream, int* index,
+                      int* ranks) {
+    if (!h || n < 1 || !A || lda < n || max_index < 0 || max_index > 64 || !index) return PINV_ERR_ARG;
+    if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;
+    cudaStream_t st = (cudaStream_t)stream;
+    *index = -1;
+    const size_t nn = (size_t)n * n;
+    const size_t bytes = sizeof(double) * (3 * nn + 2 * 256);
+    if (h->budget && bytes > h->budget) return PINV_ERR_BUDGET;
+    double* buf = nullptr;
+    CK(cudaMallocAsync((void**)&buf, bytes, st));
+    double *P = buf, *Q = buf + nn, *X = buf + 2 * nn, *scratch = buf + 3 * nn;
+    int rc = PINV_OK;
+    if (cudaMemcpy2DAsync(P, sizeof(double) * n, A, sizeof(double) * lda, sizeof(double) * n, n,
+                          cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+        rc = PINV_ERR_CUDA;
+    int prev = n;   // rank(A^0)
+    if (ranks) ranks[0] = n;
+    for (int k = 1; k <= max_index + 1 && rc == PINV_OK; ++k) {
+        // rank(A^k) = trace(A^k (A^k)^dagger), the pseudoinverse by this library
+        int r = 0;
+        pinv_desc d{};
+        d.m = d.n = n; d.A = P; d.lda = n; d.X = X; d.ldx = n;
+        d.kind = PINV_MOORE_PENROSE;
+        double alpha = 0.0;
+        const int ra = pinv_alpha_estimate(h, &d, stream, &alpha);
+        if (ra == PINV_ERR_NONFINITE) {
+            r = 0;   // A^k = 0
+        } else if (ra != PINV_OK) {
+            rc = ra;
+            break;
+        } else {
+            d.alpha = alpha;
+            d.tol = 1e-12;
+            d.stop = PINV_STOP_REL_FRO;
+            d.prec = PINV_PREC_FP64_TC;
+            d.variant = PINV_VARIANT_STABILIZED;
+            d.finish = PINV_FINISH_CLEAN;
+            pinv_info info;
+            rc = solve_one(h, &d, st, &info);
+            if (rc) break;
+            trace_of_product(n, P, n, X, n, h->dsmall, scratch, st);
+            if (cudaMemcpyAsync(h->pinned, h->dsmall, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                rc = PINV_ERR_CUDA;
+                break;
+            }
+            const double tr = h->pinned[0];
+            if (!std::isfinite(tr)) { rc = PINV_ERR_NONFINITE; break; }
+            r = (int)std::llround(tr);
+        }
+        if (ranks) ranks[k] = r;
+        if (r == prev) { *index = k - 1; break; }
+        prev = r;
+        if (k <= max_index) {   // P <- P A
+            rc = pinv_gemm(h, n, n, n, P, n, 0, A, lda, 0, Q, n, PINV_PREC_FP64_TC, stream);
+            std::swap(P, Q);
+        }
+    }
+    cudaFreeAsync(buf, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == PINV_OK) rc = PINV_ERR_CUDA;
+    if (rc == PINV_OK && *index < 0) rc = PINV_ERR_MAXITER;
+    return rc;
+}
+
 int pinv_autotune(pinv_handle* h, void* stream, int* crossover) {
     if (!h) return PINV_ERR_ARG;
     if (cudaSetDevice(h->device) != cudaSuccess) return PINV_ERR_CUDA;

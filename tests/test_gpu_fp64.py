@@ -362,3 +362,25 @@ def test_replayed_loops_serve_new_matrices_of_the_same_shape(handle, prec):
         assert info["status"] == 0 and info["iters"] == oinfo.iters
         assert rel(host(X), ref) < 1e-12
         assert rel(host(X), pinv_closed_form(w)) < 1e-12
+
+
+@pytest.mark.parametrize("case", ["example1", "family", "nonsingular", "diagonal_singular", "jordan4"])
+def test_drazin_index_matches_the_oracle(handle, case):
+    """pinv_drazin_index (ranks from this library's own pseudoinverses) gives
+    the oracle's ind(A) and rank sequence (SVD ranks)."""
+    rng = np.random.default_rng(3)
+    if case == "example1":
+        A = example1()
+    elif case == "family":
+        A = W.drazin_index2(256, 64, seed=2).A
+    elif case == "nonsingular":
+        A = rng.standard_normal((6, 6)) + 6 * np.eye(6)
+    elif case == "diagonal_singular":
+        Q = np.linalg.qr(rng.standard_normal((5, 5)))[0]
+        A = Q @ np.diag([2.0, -1.0, 0.5, 0.0, 0.0]) @ Q.T
+    else:
+        A = np.diag(np.ones(3), 1)
+    l_ref, ranks_ref = H.drazin_index(A)
+    l, ranks = handle.drazin_index(dev(A))
+    assert l == l_ref
+    assert ranks == ranks_ref

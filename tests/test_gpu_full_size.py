@@ -105,3 +105,11 @@ def test_serving_sizes_256_to_8192(handle):
         assert status[rid] == 0
         rows = np.random.default_rng(n).choice(n, 16, replace=False)
         assert rel(X.cpu().numpy()[rows], (Q[rows] / lam) @ Q.T) <= 1e-4
+
+
+def test_drazin_index_of_the_2048_workload(handle):
+    """ind(A) = 2 for the 2048 workload (256 2x2 Jordan blocks): ranks 2048,
+    1792, 1536, 1536."""
+    d = W.drazin_index2(2048, 512, seed=2)
+    l, ranks = handle.drazin_index(dev(d.A))
+    assert l == 2 and ranks == [2048, 1792, 1536, 1536]
