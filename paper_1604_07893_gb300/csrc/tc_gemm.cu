@@ -226,6 +226,17 @@ __device__ __forceinline__ void tmem_ld32_raw(uint32_t taddr, uint32_t* r) {
         : "r"(taddr)
         : "memory");
 }
+// 16 columns (8 doubles of the tile sums) and the wait, in one asm statement.
+__device__ __forceinline__ void tmem_ld16_raw(uint32_t taddr, uint32_t* r) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\t"
+        "tcgen05.wait::ld.sync.aligned;"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr)
+        : "memory");
+}
 // 64 columns in one load (the whole drain of an epilogue warp), then the wait.
 __device__ __forceinline__ void tmem_ld64_raw(uint32_t taddr, uint32_t* r) {
     asm volatile(
@@ -268,7 +279,85 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 // tile and half of the shared B tile, multicast to both, so every CTA reads 24
 // instead of 32 KiB from L2 per stage; a stage is released only when both CTAs'
 // MMAs are done with it (the commit is multicast to both empty barriers).
-template <bool MC>
+// Lean final pass of one epilogue warp for one tile (used when each pair has a
+// single K-chunk: few units per tile, so this pass weighs most): its 32 rows
+// (one per lane) x EPI_COLS columns of the tile sums in TMEM (units 2^-ubase)
+// become out = a_acc acc 2^(e_i + f_j) + a_s1 s1 + a_s2 s2 + a_id I for up to
+// three outputs, plus the stop-norm partials of output 0 against s1.  It is
+// bound by instruction issue, so per element it does little: the column
+// exponents of the tile are computed once per warp (shared memory), the scale
+// is one product with the power of two 2^(e_i + f_j) formed from them, terms
+// are chosen per output, and the identity is tested only where the diagonal
+// crosses.
+__device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogue& E, uint32_t acc64, int row,
+                                                int col0, int row0w, const unsigned long long* rmax,
+                                                const unsigned long long* cmax, int ew, bool mirror, int lane,
+                                                double& sd, double& sx) {
+    // the column exponents of this warp's half tile (static shared memory of
+    // the lean kernels only, so the other kernels keep their footprint)
+    __shared__ int ecol_all[EPI_WARPS][EPI_COLS];
+    int* ecol = ecol_all[ew];
+    if (rmax) {
+        for (int cc = lane; cc < EPI_COLS; cc += 32) ecol[cc] = (col0 + cc < P.N) ? grid_exponent(cmax, col0 + cc) : 0;
+        __syncwarp();
+    }
+    const bool rowok = row < P.M;
+    const int erow = ((rmax && rowok) ? grid_exponent(rmax, row) : 0) - P.ubase;
+    const double* s1 = (E.s1 && rowok) ? E.s1 + (size_t)row * E.ld1 : nullptr;
+    const double* s2 = (E.s2 && rowok) ? E.s2 + (size_t)row * E.ld2 : nullptr;
+    const bool norms = E.partials != nullptr;
+#pragma unroll 1
+    for (int c = 0; c < EPI_COLS; c += 8) {   // 8 columns per TMEM load
+        uint32_t r[16];
+        tmem_ld16_raw(acc64 + 2 * c, r);
+        if (!rowok) continue;
+        const int cb = col0 + c;                   // first column of the group
+        const int ncol = min(8, P.N - cb);         // its valid columns
+        if (ncol <= 0) continue;
+        double a[8], v1[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            a[j] = __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]);
+            if (rmax) {
+                const int e = erow + ecol[c + j];
+                a[j] = (e >= -1022 && e <= 1023) ? a[j] * __longlong_as_double((long long)(e + 1023) << 52)
+                                                 : ldexp(a[j], e);
+            }
+            v1[j] = (s1 && j < ncol) ? s1[cb + j] : 0.0;
+        }
+        const bool diag = cb < row0w + 32 && cb + 8 > row0w;   // the diagonal crosses this group
+        const int dg = row - cb;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            if (o < E.nout) {
+                const EpiTerm& t = E.o[o];
+                double* out = t.out ? t.out + (size_t)row * t.ld + cb : nullptr;
+                const bool use_s1 = t.a_s1 != 0.0, use_s2 = t.a_s2 != 0.0 && s2 != nullptr;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    if (j < ncol) {
+                        double v = t.a_acc == 1.0 ? a[j] : t.a_acc * a[j];
+                        if (use_s1) v = fma(t.a_s1, v1[j], v);
+                        if (use_s2) v = fma(t.a_s2, s2[cb + j], v);
+                        if (diag && j == dg) v += t.a_id;
+                        if (out) {
+                            out[j] = v;
+                            if (mirror) t.out[(size_t)(cb + j) * t.ld + row] = v;   // warp-coalesced
+                        }
+                        if (o == 0 && norms) {
+                            const double dd = v - v1[j];
+                            sd = fma(dd, dd, sd);
+                            sx = fma(v1[j], v1[j], sx);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (rmax) __syncwarp();   // ecol is rewritten for the next tile
+}
+
+template <bool MC, bool LEAN>
 __global__ void __launch_bounds__(THREADS, 1)   // 10 warps: 3 share a sub-partition (16K registers): <= 168 each
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                const __grid_constant__ TcParams P) {
@@ -510,42 +599,47 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 }
             }
             if (!ok) break;
-            // fused FP64 epilogue for this row of the tile, 16 columns at a time
-            const int row = m0 + row_in_tile;
-            const int ei = (rmax && row < P.M) ? grid_exponent(rmax, row) : 0;
             double sd = 0.0, sx = 0.0;
-            const double* s1 = (E.s1 && row < P.M) ? E.s1 + (size_t)row * E.ld1 : nullptr;
-            const double* s2 = (E.s2 && row < P.M) ? E.s2 + (size_t)row * E.ld2 : nullptr;
-            // FP64 instructions are scarce: terms with a zero coefficient are
-            // skipped (warp-uniform branches), the identity is added on the
-            // diagonal only, the norms only when asked for
-            const bool norms = E.partials != nullptr;
-#pragma unroll 1
-            for (int c = 0; c < EPI_COLS; c += 16) {
-                uint32_t r[32];
-                tmem_ld32_raw(acc64 + 2 * c, r);
-                if (row >= P.M) continue;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int col = n0 + half * EPI_COLS + c + j;
-                    if (col < P.N) {
-                        double a = __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]);
-                        if (rmax) a = scale_pow2(a, ei + grid_exponent(cmax, col) - P.ubase);
-                        const double v1 = s1 ? s1[col] : 0.0;
-                        const double v2 = s2 ? s2[col] : 0.0;
-#pragma unroll
-                        for (int o = 0; o < 3; ++o) {
-                            if (o < E.nout) {
-                                const EpiTerm& t = E.o[o];
-                                double v = t.a_acc * a;
-                                if (t.a_s1 != 0.0) v = fma(t.a_s1, v1, v);
-                                if (t.a_s2 != 0.0) v = fma(t.a_s2, v2, v);
-                                if (row == col) v += t.a_id;
-                                if (t.out) {
-                                    t.out[(size_t)row * t.ld + col] = v;
-                                    if (mirror) t.out[(size_t)col * t.ld + row] = v;   // warp-coalesced
+            if constexpr (LEAN) {
+                lean_final_pass(P, E, acc64, m0 + row_in_tile, n0 + half * EPI_COLS, m0 + lg * 32, rmax, cmax,
+                                ew, mirror, lane, sd, sx);
+            } else {
+                // fused FP64 epilogue for this row of the tile, 16 columns at a time
+                const int row = m0 + row_in_tile;
+                const int ei = (rmax && row < P.M) ? grid_exponent(rmax, row) : 0;
+                const double* s1 = (E.s1 && row < P.M) ? E.s1 + (size_t)row * E.ld1 : nullptr;
+                const double* s2 = (E.s2 && row < P.M) ? E.s2 + (size_t)row * E.ld2 : nullptr;
+                // FP64 instructions are scarce: terms with a zero coefficient are
+                // skipped (warp-uniform branches), the identity is added on the
+                // diagonal only, the norms only when asked for
+                const bool norms = E.partials != nullptr;
+    #pragma unroll 1
+                for (int c = 0; c < EPI_COLS; c += 16) {
+                    uint32_t r[32];
+                    tmem_ld32_raw(acc64 + 2 * c, r);
+                    if (row >= P.M) continue;
+    #pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int col = n0 + half * EPI_COLS + c + j;
+                        if (col < P.N) {
+                            double a = __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]);
+                            if (rmax) a = scale_pow2(a, ei + grid_exponent(cmax, col) - P.ubase);
+                            const double v1 = s1 ? s1[col] : 0.0;
+                            const double v2 = s2 ? s2[col] : 0.0;
+    #pragma unroll
+                            for (int o = 0; o < 3; ++o) {
+                                if (o < E.nout) {
+                                    const EpiTerm& t = E.o[o];
+                                    double v = t.a_acc * a;
+                                    if (t.a_s1 != 0.0) v = fma(t.a_s1, v1, v);
+                                    if (t.a_s2 != 0.0) v = fma(t.a_s2, v2, v);
+                                    if (row == col) v += t.a_id;
+                                    if (t.out) {
+                                        t.out[(size_t)row * t.ld + col] = v;
+                                        if (mirror) t.out[(size_t)col * t.ld + row] = v;   // warp-coalesced
+                                    }
+                                    if (o == 0 && norms) { const double dd = v - v1; sd = fma(dd, dd, sd); sx = fma(v1, v1, sx); }
                                 }
-                                if (o == 0 && norms) { const double dd = v - v1; sd = fma(dd, dd, sd); sx = fma(v1, v1, sx); }
                             }
                         }
                     }
@@ -781,13 +875,16 @@ bool prepare_kernels() {
     const int dev = current_device();
     std::lock_guard<std::mutex> lk(g_dev_mu);
     if (g_dev[dev].attr) return true;
-    cudaFuncSetAttribute(tc_gemm_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
-    cudaFuncSetAttribute(tc_gemm_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
-    cudaFuncAttributes fa;
-    if (cudaFuncGetAttributes(&fa, tc_gemm_kernel<false>) == cudaSuccess && fa.maxThreadsPerBlock < THREADS) {
-        std::fprintf(stderr, "tc_gemm: kernel uses %d registers; at most %d threads per block fit\n",
-                     fa.numRegs, fa.maxThreadsPerBlock);
-        return false;
+    const void* kernels[4] = {(const void*)tc_gemm_kernel<false, false>, (const void*)tc_gemm_kernel<false, true>,
+                              (const void*)tc_gemm_kernel<true, false>, (const void*)tc_gemm_kernel<true, true>};
+    for (const void* k : kernels) {
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.maxThreadsPerBlock < THREADS) {
+            std::fprintf(stderr, "tc_gemm: kernel uses %d registers; at most %d threads per block fit\n",
+                         fa.numRegs, fa.maxThreadsPerBlock);
+            return false;
+        }
     }
     g_dev[dev].attr = true;
     return true;
@@ -914,6 +1011,9 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.rmax = mode.exact ? ea : nullptr;
     P.cmax = mode.exact ? eb : nullptr;
     const int tiles = sym_out ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;   // per instance
+    // one K-chunk per pair (short products, or BF16 with its single pair): few
+    // units per tile, so the final epilogue pass weighs most -- the lean one
+    const bool lean = (K + P.chunk - 1) / P.chunk == 1;
     if (!prepare_kernels()) return -1;
     if (ev_begin) cudaEventRecord(ev_begin, st);
     if (mc) {
@@ -932,7 +1032,9 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        if (cudaError_t e = cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true>, ma, mb, P); e != cudaSuccess) {
+        if (cudaError_t e = lean ? cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true, true>, ma, mb, P)
+                                 : cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true, false>, ma, mb, P);
+            e != cudaSuccess) {
             std::fprintf(stderr, "tc_gemm: cluster launch failed: %s\n", cudaGetErrorString(e));
             return -1;
         }
@@ -941,7 +1043,8 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
         // persistent (one CTA per SM walking the tiles) unless the caller wants
         // the SMs released after every tile (so higher-priority streams get in)
         const int grid = (one_tile_per_cta || all_tiles < num_sms()) ? all_tiles : num_sms();
-        tc_gemm_kernel<false><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+        if (lean) tc_gemm_kernel<false, true><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+        else tc_gemm_kernel<false, false><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
     }
     if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;
