@@ -68,6 +68,15 @@ Epilogue epi1(EpiTerm t0, const double* s1 = nullptr, int ld1 = 0, const double*
 
 }  // namespace
 
+// State of a solve whose loop runs on the device (a graph WHILE node): the
+// stop rule's inputs and outputs, written by the host before the launch and
+// read back after it.
+struct DeviceLoopState {
+    int k, max_iter, stop_mode, status, reason, iters, loops_run, copy;
+    double alpha, tol, prev, prev2, rel_step;
+    double history[PINV_HISTORY];
+};
+
 struct pinv_handle {
     int device = 0;
     size_t budget = 0;
@@ -89,6 +98,9 @@ struct pinv_handle {
     };
     std::vector<LoopGraph> loop_graphs;
     cudaStream_t capture_stream = nullptr;    // graphs are captured here, replayed on the caller's stream
+    DeviceLoopState* dstate = nullptr;        // device-driven loops: state on the device
+    DeviceLoopState* hstate = nullptr;        // and its pinned host copy
+    bool device_loop_off = false;             // set if such a graph could not be built here
     // pinned readback blocks for groups, reused (pinned allocation can
     // synchronise the device, so it happens only when the pool is empty)
     std::vector<void*> pinned_blocks;
@@ -624,6 +636,174 @@ double stop_measure(const pinv_desc* d, double dx2, double x2, int k, double alp
 
 // Small solves are bound by launch and host overhead: their loop (seven or nine
 // products, the norm reduction and the readback) runs as one cached graph.
+// The stop rule of a plain loop at one precision, on the device (one thread):
+// the same arithmetic and decisions as the host loop in solve_one, reading the
+// loop's reduced norms.  It always ends the WHILE loop by k = max_iter, so the
+// device loop terminates whatever the data.
+__global__ void loop_decide_kernel(cudaGraphConditionalHandle cond, const double* norms, const int* derr,
+                                   DeviceLoopState* st) {
+    if (threadIdx.x != 0) return;
+    const int k = st->k;
+    const double dx2 = norms[0], x2 = norms[1];
+    double e;
+    if (dx2 == 0.0) {
+        e = 0.0;
+    } else if (st->stop_mode == PINV_STOP_PAPER) {
+        double p18 = 1.0;
+        for (int i = 0; i < k; ++i) p18 *= 18.0;
+        e = sqrt(dx2) / (p18 * st->alpha);
+    } else {
+        e = x2 > 0 ? sqrt(dx2) / sqrt(x2) : INFINITY;
+    }
+    if (k < PINV_HISTORY) st->history[k] = e;
+    st->loops_run = k + 1;
+    int stop = 0, copy = 0;
+    if (*derr) {
+        st->status = PINV_ERR_TIMEOUT; stop = 1;
+    } else if (!isfinite(e)) {
+        st->status = PINV_ERR_NONFINITE; st->iters = k; stop = 1;
+    } else if (e < st->tol) {
+        st->status = PINV_OK; st->reason = 0; st->iters = k + 1; st->rel_step = e; stop = 1; copy = 1;
+    } else {
+        const double prev = st->prev;
+        const bool stalled = k >= 1 && prev < 1e-3 && e >= prev * prev;
+        const double rel = dx2 == 0.0 ? 0.0 : (x2 > 0 ? sqrt(dx2 / x2) : INFINITY);
+        if (stalled) {
+            st->status = PINV_OK; st->reason = 1; st->iters = k; st->rel_step = prev; stop = 1;
+        } else if (rel > 1e3 && k > 0) {
+            st->status = PINV_ERR_DIVERGED; st->iters = k; stop = 1;
+        } else {
+            st->prev2 = prev;
+            st->prev = e;
+            st->rel_step = e;
+            st->iters = k + 1;
+            copy = 1;
+            if (k + 1 >= st->max_iter) { st->status = PINV_ERR_MAXITER; st->reason = 2; stop = 1; }
+        }
+    }
+    st->k = k + 1;
+    st->copy = copy;
+    cudaGraphSetConditional(cond, stop ? 0u : 1u);
+}
+
+// X0 <- X1 when the decision kept the new iterate (device loop ping-pong).
+__global__ void loop_copy_kernel(const DeviceLoopState* st, const double* src, double* dst, size_t count) {
+    if (!st->copy) return;
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+constexpr int kDeviceLoopUnavailable = 1000;   // not a PINV code: fall back to the host loop
+
+// Whole solve loop on the device for small plain solves at one precision: a
+// graph with a WHILE node whose body is the loop, the norm reduction, the stop
+// decision and the ping-pong copy; one launch and one readback per solve.
+int device_loop(Ctx& c, const pinv_desc* d, double alpha, int max_iter, pinv_info* info) {
+    pinv_handle* h = c.h;
+    if (!h->dstate) {
+        CK(cudaMalloc((void**)&h->dstate, sizeof(DeviceLoopState)));
+        CK(cudaMallocHost((void**)&h->hstate, sizeof(DeviceLoopState)));
+    }
+    std::vector<long long> key = {-1, c.m, c.n, c.left, c.symmetric, c.prec_k, h->tc_crossover,
+                                  (long long)c.A, c.lda, (long long)c.X[0], (long long)c.X[1],
+                                  (long long)c.sq[0], (long long)c.partials, (long long)c.tcws,
+                                  (long long)c.tcws_bytes};
+    pinv_handle::LoopGraph* lg = nullptr;
+    for (auto& g : h->loop_graphs)
+        if (g.key == key) { lg = &g; break; }
+    if (!lg) {
+        if (!h->capture_stream) CK(cudaStreamCreateWithFlags(&h->capture_stream, cudaStreamNonBlocking));
+        if (h->loop_graphs.size() >= 32) {
+            cudaGraphExecDestroy(h->loop_graphs.front().exec);
+            h->loop_graphs.erase(h->loop_graphs.begin());
+        }
+        cudaGraph_t graph = nullptr;
+        CK(cudaGraphCreate(&graph, 0));
+        cudaGraphConditionalHandle cond;
+        cudaGraphNodeParams np = {};
+        cudaGraphNode_t node;
+        cudaError_t e = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) {
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = cond;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            e = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+        }
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            std::fprintf(stderr, "pinv: device loop graph: %s (host loop used)\n", cudaGetErrorString(e));
+            h->device_loop_off = true;
+            return kDeviceLoopUnavailable;
+        }
+        cudaGraph_t body = np.conditional.phGraph_out[0];
+        cudaStream_t user = c.st;
+        c.st = h->capture_stream;
+        const int k0 = c.kernels, g0 = c.gemms;
+        e = cudaStreamBeginCaptureToGraph(c.st, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+        int parts = -1;
+        if (e == cudaSuccess) {
+            parts = pm_loop_f64(c, c.X[0], c.X[1]);
+            if (parts >= 0) {
+                reduce_pairs(c.partials, parts, h->dsmall, c.st);
+                loop_decide_kernel<<<1, 32, 0, c.st>>>(cond, h->dsmall, h->derr, h->dstate);
+                loop_copy_kernel<<<64, 256, 0, c.st>>>(h->dstate, c.X[1], c.X[0], (size_t)c.n * c.m);
+            }
+            cudaGraph_t captured = nullptr;
+            e = cudaStreamEndCapture(c.st, &captured);
+        }
+        c.st = user;
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess && parts >= 0) e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess || parts < 0) {
+            std::fprintf(stderr, "pinv: device loop graph: %s (host loop used)\n", cudaGetErrorString(e));
+            c.kernels = k0;
+            c.gemms = g0;
+            cudaGetLastError();
+            h->device_loop_off = true;
+            return kDeviceLoopUnavailable;
+        }
+        pinv_handle::LoopGraph g;
+        g.key = key;
+        g.exec = exec;
+        g.kernels = c.kernels - k0 + 3;   // + reduction, decision, copy
+        g.gemms = c.gemms - g0;
+        c.kernels = k0;
+        c.gemms = g0;
+        h->loop_graphs.push_back(std::move(g));
+        lg = &h->loop_graphs.back();
+    }
+    DeviceLoopState& hs = *h->hstate;
+    std::memset(&hs, 0, sizeof(hs));
+    hs.max_iter = max_iter;
+    hs.stop_mode = d->stop;
+    hs.alpha = alpha;
+    hs.tol = d->tol;
+    hs.prev = hs.prev2 = INFINITY;
+    hs.status = PINV_ERR_MAXITER;
+    hs.reason = 2;
+    CK(cudaMemcpyAsync(h->dstate, &hs, sizeof(hs), cudaMemcpyHostToDevice, c.st));
+    CK(cudaGraphLaunch(lg->exec, c.st));
+    CK(cudaMemcpyAsync(&hs, h->dstate, sizeof(hs), cudaMemcpyDeviceToHost, c.st));
+    CK(cudaStreamSynchronize(c.st));
+    c.kernels += lg->kernels * hs.loops_run;
+    c.gemms += lg->gemms * hs.loops_run;
+    info->loops_run = hs.loops_run;
+    info->iters = hs.iters;
+    info->rel_step = hs.rel_step;
+    info->stop_reason = hs.reason;
+    for (int k = 0; k < std::min(hs.loops_run, PINV_HISTORY); ++k) {
+        info->history[k] = hs.history[k];
+        info->precision[k] = (signed char)c.prec_k;
+    }
+    if (hs.status == PINV_ERR_TIMEOUT) {
+        std::fprintf(stderr, "pinv: tensor-core kernel wait timed out\n");
+        cudaMemsetAsync(h->derr, 0, sizeof(int), c.st);
+    }
+    return hs.status;
+}
+
 int replay_loop(Ctx& c, int cur, bool stab, double* dx2, double* x2) {
     pinv_handle* h = c.h;
     const double* Xk = c.X[cur];
@@ -728,7 +908,23 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
                     ? TC_BF16 : (d->prec == PINV_PREC_FP32 ? TC_FP32 : fp64_class);
     int prev_prec = -1;
     double prev2 = INFINITY;
-    for (int k = 0; k < max_iter; ++k) {
+    // Small plain solves at one precision run the whole loop on the device (a
+    // graph WHILE node with the stop rule in a kernel): one launch per solve.
+    bool on_device = replay && !h->device_loop_off && d->variant == PINV_VARIANT_PLAIN && level == fp64_class &&
+                     max_iter <= 1000;
+    if (on_device) {
+        c.prec_k = level;
+        status = device_loop(c, d, alpha, max_iter, info);
+        if (status == kDeviceLoopUnavailable) {
+            on_device = false;
+            status = PINV_ERR_MAXITER;
+        } else {
+            if (status == PINV_ERR_CUDA || status == PINV_ERR_TIMEOUT) return info->status = status;
+            reason = info->stop_reason;
+            cur = 0;   // the kept iterate is in X[0]
+        }
+    }
+    for (int k = 0; !on_device && k < max_iter; ++k) {
         const bool stab_now = stabilise;
         const double* Xk = c.X[cur];
         double* Xn = c.X[cur ^ 1];
@@ -1388,6 +1584,8 @@ void pinv_destroy(pinv_handle* h) {
     for (auto& g : h->loop_graphs) cudaGraphExecDestroy(g.exec);
     h->loop_graphs.clear();
     if (h->capture_stream) cudaStreamDestroy(h->capture_stream);
+    if (h->dstate) cudaFree(h->dstate);
+    if (h->hstate) cudaFreeHost(h->hstate);
     for (void* p : h->pinned_blocks) cudaFreeHost(p);
     h->pinned_blocks.clear();
     if (h->derr) cudaFree(h->derr);
