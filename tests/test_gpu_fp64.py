@@ -384,3 +384,22 @@ def test_drazin_index_matches_the_oracle(handle, case):
     l, ranks = handle.drazin_index(dev(A))
     assert l == l_ref
     assert ranks == ranks_ref
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp64_tc"])
+def test_device_loop_decisions_match_the_oracle(handle, prec):
+    """Small plain solves apply the stop rule on the device: the per-loop stop
+    measures, the loop count and the max_iter outcome agree with the oracle."""
+    w = W.rectangular(64, 48, None, 1.0, 1e-2, seed=0)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    ref, oinfo = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, prec=prec)
+    assert info["status"] == 0 and info["iters"] == oinfo.iters and info["loops_run"] == oinfo.loops_run
+    for got, want in zip(info["history"][:info["loops_run"]], oinfo.history):
+        if want > 1e-9:
+            assert abs(got - want) <= 1e-6 * want
+    # max_iter: two loops, then PINV_ERR_MAXITER with the second iterate
+    ref2, oinfo2 = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha, max_iter=2)
+    X2, info2 = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, prec=prec, max_iter=2, raise_on_error=False)
+    assert oinfo2.status == "maxiter" and info2["status"] == -5 and info2["iters"] == 2
+    assert rel(host(X2), ref2) < 1e-12
