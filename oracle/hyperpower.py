@@ -30,9 +30,10 @@ generalized inverse of a matrix"):
 Readings where the paper is silent or garbled are listed in the design notes
 of the repository; each is also stated where it is used below.
 
-All functions accept float64 numpy arrays.  The step, X0 and norm helpers are
-written with ``@``, ``+`` and ``abs`` only, so they also run on numpy object
-arrays of mpmath numbers (the 150-digit reproduction of Table 1).
+All functions accept float64 or complex128 numpy arrays (the paper works over
+C: A^* is the conjugate transpose, Section 1.1).  The step, X0 and norm helpers
+are written with ``@``, ``+`` and ``abs`` only, so they also run on numpy
+object arrays of mpmath numbers (the 150-digit reproduction of Table 1).
 
 Parity: every function here is pinned by ``tests/test_oracle.py`` (closed-form
 inverses from the generators' factors, the printed Table 1 values, the Penrose
@@ -64,8 +65,16 @@ def _eye(n: int, like: np.ndarray) -> np.ndarray:
     return np.eye(n, dtype=like.dtype)
 
 
+def ct(x: np.ndarray) -> np.ndarray:
+    """A^*: the conjugate (Hermitian) transpose (Section 1.1); the transpose
+    for real and object arrays."""
+    return x.conj().T if np.iscomplexobj(x) else x.T
+
+
 def fro(x: np.ndarray):
-    """Frobenius norm sqrt(sum x_ij^2)."""
+    """Frobenius norm sqrt(sum |x_ij|^2)."""
+    if np.iscomplexobj(x):
+        return float(np.sqrt((x.real * x.real + x.imag * x.imag).sum()))
     return (x * x).sum() ** 0.5
 
 
@@ -174,8 +183,8 @@ def stabilised_step(A: np.ndarray, X: np.ndarray, p: int = P_ORDER, side: str = 
 # ----------------------------------------------------------------------------
 
 def x0_moore_penrose(A: np.ndarray, alpha) -> np.ndarray:
-    """X0 = alpha A^T (real case of alpha A^*; Section 4, Theorem 6.2)."""
-    return alpha * A.T.copy()
+    """X0 = alpha A^* (Section 4, Theorem 6.2); alpha A^T for real A."""
+    return alpha * ct(A).copy()
 
 
 def x0_general(G: np.ndarray, alpha) -> np.ndarray:
@@ -200,25 +209,29 @@ def drazin_index(A: np.ndarray, max_index: int = 16):
 
 
 def x0_drazin(A: np.ndarray, l: int, alpha=None) -> np.ndarray:
-    """X0 = A^l / Tr(A^{l+1}) (Section 4), or alpha A^l when alpha is given."""
+    """X0 = A^l / Tr(A^{l+1}) (Section 4), or alpha A^l when alpha is given.
+    For complex A the trace, and so alpha, is complex as the formula stands."""
     Al = matpow(A, l)
     if alpha is None:
         tr = trace(Al @ A)
-        if not tr > 0:
+        if np.iscomplexobj(A):
+            if tr == 0:
+                raise ValueError("Tr(A^{l+1}) = 0: no trace scaling")
+        elif not tr > 0:
             raise ValueError("Tr(A^{l+1}) must be positive for the trace scaling")
         alpha = 1 / tr
     return alpha * Al
 
 
 def x0_drazin_normal(A: np.ndarray, l: int, alpha=None) -> np.ndarray:
-    """X0 = alpha G with G = A^l (A^{2l+1})^T A^l.  R(G) = R(A^l) and N(G) = N(A^l),
+    """X0 = alpha G with G = A^l (A^{2l+1})^* A^l.  R(G) = R(A^l) and N(G) = N(A^l),
     the range and null space of the Drazin inverse (Section 1.1 names A^D as the
     outer inverse with those subspaces; Theorem 3.1 takes any such G), and GA
     has a real nonnegative spectrum, so the iteration converges whatever the
     eigenvalues of A (X0 = A^l / Tr(A^{l+1}) needs them in a sector).  alpha
     defaults to 1 / sqrt(||GA||_1 ||GA||_inf) <= 1 / ||GA||_2."""
     Al = matpow(A, l)
-    G = Al @ matpow(A, 2 * l + 1).T @ Al
+    G = Al @ ct(matpow(A, 2 * l + 1)) @ Al
     if alpha is None:
         GA = G @ A
         alpha = 1.0 / math.sqrt(float(np.abs(GA).sum(axis=0).max()) * float(np.abs(GA).sum(axis=1).max()))
@@ -245,10 +258,10 @@ def alpha_rectangular(A: np.ndarray) -> float:
 # ----------------------------------------------------------------------------
 
 def cleanup_moore_penrose(A: np.ndarray, X: np.ndarray) -> np.ndarray:
-    """X <- (XA)^T X (AX)^T.  With X = A^+ + E in the SVD blocks of Theorem 6.2
+    """X <- (XA)^* X (AX)^*.  With X = A^+ + E in the SVD blocks of Theorem 6.2
     this removes the E12, E21 and E22 blocks to first order (they are the parts
     the iteration does not contract) and leaves A^+ fixed."""
-    return (X @ A).T @ X @ (A @ X).T
+    return ct(X @ A) @ X @ ct(A @ X)
 
 
 def cleanup_drazin(A: np.ndarray, X: np.ndarray, l: int) -> np.ndarray:
@@ -378,14 +391,14 @@ def _iterate(A, X0, tol, stop, alpha, max_iter, variant, switch_tol, floor_guard
 
 def penrose_residuals(A: np.ndarray, X: np.ndarray) -> np.ndarray:
     """Relative Frobenius residuals of the four Penrose equations:
-    ||AXA - A||/||A||, ||XAX - X||/||X||, ||(AX)^T - AX||/||AX||, ||(XA)^T - XA||/||XA||."""
+    ||AXA - A||/||A||, ||XAX - X||/||X||, ||(AX)^* - AX||/||AX||, ||(XA)^* - XA||/||XA||."""
     AX = A @ X
     XA = X @ A
     return np.array([
         float(fro(AX @ A - A) / fro(A)),
         float(fro(X @ AX - X) / fro(X)),
-        float(fro(AX.T - AX) / fro(AX)),
-        float(fro(XA.T - XA) / fro(XA)),
+        float(fro(ct(AX) - AX) / fro(AX)),
+        float(fro(ct(XA) - XA) / fro(XA)),
     ])
 
 

@@ -18,6 +18,9 @@ ill-conditioned Moore-Penrose problems and preconditioning of a large matrix):
 * ``uneven_batch`` many independent rectangular problems of random shape.
 * ``poisson_arrivals`` request arrival times for the serving workload.
 * ``hilbert``      H_ij = 1/(i+j-1) (Section 8 Example 2).
+* ``rectangular_complex``, ``drazin_complex``, ``hpd_complex``: the same
+  families over C (the paper states the method for complex matrices, with
+  A^* the conjugate transpose; Section 1.1), complex128 arrays.
 
 Every function takes an integer seed and returns float64 numpy arrays plus the
 factors from which the exact answer has a closed form (the tests use those
@@ -225,3 +228,75 @@ def spd_fast(n: int, lam_min: float = 1e-3, lam_max: float = 1.0, seed: int = 5)
     Q = householder_orthogonal(rng, n)
     lam = np.logspace(math.log10(lam_max), math.log10(lam_min), n)
     return Q, lam
+
+
+# ---------------------------------------------------------------- complex families
+
+def haar_unitary(rng: np.random.Generator, n: int, k: int | None = None) -> np.ndarray:
+    """First ``k`` columns of a Haar-distributed n x n unitary matrix: QR of a
+    complex Gaussian matrix (independent N(0, 1/2) real and imaginary parts)
+    with the phases of R's diagonal folded into Q (Mezzadri's correction)."""
+    k = n if k is None else k
+    g = (rng.standard_normal((n, k)) + 1j * rng.standard_normal((n, k))) / math.sqrt(2.0)
+    q, r = np.linalg.qr(g)
+    d = np.diag(r)
+    ph = np.where(np.abs(d) > 0, d / np.where(np.abs(d) > 0, np.abs(d), 1.0), 1.0)
+    return q * ph
+
+
+def rectangular_complex(m: int, n: int, rank: int | None = None, s_max: float = 1.0,
+                        s_min: float = 1e-2, seed: int = 0) -> Rectangular:
+    """A = U diag(s) V^* with Haar unitary columns U (m x r), V (n x r) and s
+    log-spaced from s_max down to s_min."""
+    r = min(m, n) if rank is None else rank
+    if not (0 < r <= min(m, n)):
+        raise ValueError("rank must be in [1, min(m, n)]")
+    rng = np.random.default_rng(seed)
+    U = haar_unitary(rng, m, r)
+    V = haar_unitary(rng, n, r)
+    s = np.logspace(math.log10(s_max), math.log10(s_min), r)
+    A = (U * s) @ V.conj().T
+    return Rectangular(A=np.ascontiguousarray(A), U=U, s=s, V=V)
+
+
+def drazin_complex(n: int, n_nil: int, seed: int = 2, r_min: float = 0.5, r_max: float = 2.0,
+                   sector: float = math.pi / 8, p_scale: float | None = None,
+                   upper: float = 0.1) -> Drazin:
+    """A = P blockdiag(C, N) P^{-1} over C, ind(A) = 2 when n_nil > 0.
+
+    C (n - n_nil square) is upper triangular with eigenvalues r e^{i theta},
+    r uniform in area on [r_min, r_max], |theta| <= sector drawn independently
+    (the spectrum is not closed under conjugation), plus a strictly upper part of
+    complex Gaussian entries of scale ``upper/sqrt(n)``.  N: 2x2 Jordan blocks.
+    P = I + p_scale * complex Gaussian, p_scale = 0.1/sqrt(n) by default."""
+    if n_nil % 2 or n_nil > n:
+        raise ValueError("n_nil must be even and <= n")
+    rng = np.random.default_rng(seed)
+    nc = n - n_nil
+    r = np.sqrt(rng.uniform(r_min ** 2, r_max ** 2, nc))
+    th = rng.uniform(-sector, sector, nc)
+    eig = r * np.exp(1j * th)
+    g = (rng.standard_normal((nc, nc)) + 1j * rng.standard_normal((nc, nc))) / math.sqrt(2.0)
+    C = np.diag(eig) + np.triu(g, 1) * (upper / math.sqrt(max(n, 1)))
+    N = np.zeros((n_nil, n_nil), dtype=complex)
+    for j in range(0, n_nil, 2):
+        N[j, j + 1] = 1.0
+    if p_scale is None:
+        p_scale = 0.1 / math.sqrt(n)
+    gp = (rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))) / math.sqrt(2.0)
+    P = np.eye(n) + p_scale * gp
+    B = np.zeros((n, n), dtype=complex)
+    B[:nc, :nc] = C
+    B[nc:, nc:] = N
+    A = P @ B @ np.linalg.inv(P)
+    return Drazin(A=np.ascontiguousarray(A), P=P, C=C, N=N, eig=eig)
+
+
+def hpd_complex(n: int, lam_min: float = 1e-3, lam_max: float = 1.0, seed: int = 5) -> SPD:
+    """A = Q diag(lambda) Q^*, Q Haar unitary, lambda log-spaced in [lam_min, lam_max]."""
+    rng = np.random.default_rng(seed)
+    Q = haar_unitary(rng, n)
+    lam = np.logspace(math.log10(lam_max), math.log10(lam_min), n)
+    A = (Q * lam) @ Q.conj().T
+    A = 0.5 * (A + A.conj().T)
+    return SPD(A=np.ascontiguousarray(A), Q=Q, lam=lam)

@@ -19,22 +19,22 @@ def example1(kind="float"):
 
 
 def pinv_closed_form(w):
-    """A^+ = V diag(1/s) U^T from the generator's factors."""
-    return (w.V / w.s) @ w.U.T
+    """A^+ = V diag(1/s) U^* from the generator's factors."""
+    return (w.V / w.s) @ w.U.conj().T
 
 
 def drazin_closed_form(d):
     """A^D = P blockdiag(C^{-1}, 0) P^{-1} from the generator's factors."""
     n = d.A.shape[0]
     nc = d.C.shape[0]
-    B = np.zeros((n, n))
+    B = np.zeros((n, n), dtype=d.A.dtype)
     if nc:
         B[:nc, :nc] = np.linalg.inv(d.C)
     return d.P @ B @ np.linalg.inv(d.P)
 
 
 def spd_inverse(s):
-    return (s.Q / s.lam) @ s.Q.T
+    return (s.Q / s.lam) @ s.Q.conj().T
 
 
 def rel(X, Y):

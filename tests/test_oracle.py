@@ -474,3 +474,99 @@ def test_drazin_index_by_construction(case, expected):
     l, ranks = H.drazin_index(A)
     assert l == expected
     assert ranks[l] == ranks[l + 1] and (l == 0 or ranks[l - 1] > ranks[l])
+
+
+# --------------------------------------------------------------------------
+# complex matrices (Section 1.1: the method is stated over C, A^* the
+# conjugate transpose; Theorem 3.1 holds as stated)
+# --------------------------------------------------------------------------
+
+def test_complex_norm_and_conjugate_transpose_by_hand():
+    x = np.array([[3 + 4j, 0], [1j, -1]])
+    assert H.fro(x) == pytest.approx(math.sqrt(25 + 1 + 1))
+    assert np.array_equal(H.ct(x), np.array([[3 - 4j, -1j], [0, -1]]))
+    assert np.array_equal(H.x0_moore_penrose(x, 2.0), 2.0 * np.array([[3 - 4j, -1j], [0, -1]]))
+
+
+def test_complex_mp_closed_form_and_lapack():
+    w = W.rectangular_complex(40, 28, None, 1.0, 1e-2, seed=21)
+    ref = pinv_closed_form(w)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    X, info = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+    assert info.status == "converged" and X.dtype == np.complex128
+    assert rel(X, ref) < 1e-12
+    assert rel(X, np.linalg.pinv(w.A)) < 1e-12
+    assert H.penrose_residuals(w.A, X).max() < 1e-12
+    # the rectangular recipe of Section 4 with complex moduli
+    a2 = H.alpha_rectangular(w.A)
+    assert a2 == pytest.approx(1.0 / (np.abs(w.A).sum(axis=0).max() * np.abs(w.A).sum(axis=1).max()))
+    X2, _ = H.solve(w.A, H.x0_moore_penrose(w.A, a2), tol=1e-12, alpha=a2)
+    assert rel(X2, ref) < 1e-12
+    # a plausible slip: X0 = alpha A^T without the conjugate has the wrong range
+    with np.errstate(over="ignore", invalid="ignore"):
+        Xt, _ = H.solve(w.A, alpha * w.A.T, tol=1e-12, alpha=alpha, max_iter=30)
+    assert not rel(Xt, ref) < 1e-3
+    # and the Penrose residual function sees a conjugation slip in X
+    assert H.penrose_residuals(w.A, ref.conj())[0] > 1e-2
+
+
+def test_complex_mp_rank_deficient_with_finish():
+    w = W.rectangular_complex(72, 54, 40, 1.0, 1e-3, seed=22)
+    ref = pinv_closed_form(w)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    for variant in ("plain", "stabilised"):
+        X, info = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha,
+                          variant=variant, finish="moore_penrose")
+        assert info.finished
+        assert rel(X, ref) < 1e-11
+        assert H.penrose_residuals(w.A, X).max() < 1e-10
+
+
+def test_complex_solve_of_a_real_matrix_is_the_real_solve():
+    w = W.rectangular(30, 20, None, 1.0, 1e-2, seed=3)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    Xr, ir = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+    Ac = w.A.astype(np.complex128)
+    Xc, ic = H.solve(Ac, H.x0_moore_penrose(Ac, alpha), tol=1e-12, alpha=alpha)
+    assert ic.iters == ir.iters
+    assert np.abs(Xc.imag).max() == 0.0
+    assert rel(Xc.real, Xr) < 1e-14
+
+
+def test_complex_residual_powers_invariant():
+    """R_{k+1} = R_k^18 (Theorem 3.1, right form) for a Hermitian positive
+    definite A from X0 = alpha I."""
+    s = W.hpd_complex(24, 0.1, 1.0, seed=7)
+    alpha = 2.0 / 1.1
+    I = np.eye(24, dtype=np.complex128)
+    X1 = H.hyperpower_step(s.A, alpha * I)
+    R0, R1 = I - alpha * s.A, I - s.A @ X1
+    assert rel(R1, np.linalg.matrix_power(R0, 18)) < 1e-12
+
+
+def test_complex_inverse_from_identity_g():
+    s = W.hpd_complex(48, 1e-2, 1.0, seed=8)
+    alpha = 2.0 / (1.0 + 1e-2)
+    X, info = H.solve(s.A, H.x0_general(np.eye(48, dtype=np.complex128), alpha), tol=1e-13, alpha=alpha)
+    assert rel(X, spd_inverse(s)) < 1e-12
+    assert rel(X, np.linalg.inv(s.A)) < 1e-12
+
+
+def test_complex_drazin_closed_form():
+    d = W.drazin_complex(40, 10, seed=23)
+    ref = drazin_closed_form(d)
+    l, ranks = H.drazin_index(d.A)
+    assert l == 2 and ranks[:4] == [40, 35, 30, 30]
+    # Section 4's trace scaling, alpha = 1/Tr(A^3) complex as it stands
+    X, info = H.solve(d.A, H.x0_drazin(d.A, 2), tol=1e-13, alpha=1.0)
+    assert rel(X, ref) < 1e-11
+    assert H.drazin_residuals(d.A, X, 2).max() < 1e-11
+    # a real scaling 1/Re Tr(A^3)
+    tr = H.trace(H.matpow(d.A, 3))
+    X2, _ = H.solve(d.A, H.x0_drazin(d.A, 2, 1.0 / tr.real), tol=1e-13, alpha=1.0)
+    assert rel(X2, ref) < 1e-11
+    # G = A^l (A^{2l+1})^* A^l converges for a spectrum all around the annulus
+    d2 = W.drazin_complex(48, 12, seed=24, sector=np.pi)
+    X3, info3 = H.solve(d2.A, H.x0_drazin_normal(d2.A, 2), tol=1e-2, stop=H.STOP_ORDER18, alpha=1.0)
+    assert info3.status == "converged"
+    assert rel(X3, drazin_closed_form(d2)) < 1e-10
