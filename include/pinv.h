@@ -202,6 +202,26 @@ void pinv_destroy(pinv_handle *h);
  * one handle. */
 int  pinv_solve(pinv_handle *h, const pinv_desc *desc, void *stream, pinv_info *info);
 
+/* Complex matrices (the paper's setting: A in C^{m x n}, A^* the conjugate
+ * transpose, Section 1.1; Theorem 3.1 holds over C).  Same descriptor and
+ * results as pinv_solve, with A, G and X complex: interleaved (re, im) double
+ * pairs (the layout of C99 double _Complex and std::complex<double>), leading
+ * dimensions counted in complex elements, X0 = alpha A^* for Moore-Penrose.
+ * The library solves the real embedding E(Z) = [[Re Z, -Im Z], [Im Z, Re Z]]
+ * (2m x 2n; E(ZW) = E(Z)E(W), E(Z^*) = E(Z)^T, so the iterates of E(A) are
+ * the embeddings of the complex iterates) with every product formed as the
+ * left column half of E(C) -- the four real products of a complex product --
+ * and reads X off E(X).  Workspace: that of a real 2m x 2n solve.
+ *   - alpha is real.  alpha = 0 takes 1/(||A||_1 ||A||_inf) with complex
+ *     moduli (Moore-Penrose / general G) and 1/Re Tr(A^{l+1}) (Drazin: the
+ *     paper's 1/Tr(A^{l+1}) is complex in general; its real part keeps
+ *     |1 - alpha lambda^{l+1}| < 1 for the sector spectra the trace recipe
+ *     needs).
+ *   - Stop measures and residuals use complex Frobenius norms.
+ *   - desc->symmetric must be 0 (PINV_ERR_ARG).  host_buffers works as in
+ *     pinv_solve. */
+int  pinv_solve_complex(pinv_handle *h, const pinv_desc *desc, void *stream, pinv_info *info);
+
 /* Solve `count` independent Moore-Penrose or general-G problems (device
  * buffers).  Problems are grouped by shape padded to multiples of 64 and by
  * settings; each group runs the loop chain for all its problems in lockstep

@@ -24,7 +24,7 @@ VARIANT = {"plain": 0, "stabilized": 1}
 FINISH = {None: 0, "none": 0, "clean": 1}
 HISTORY = 128
 
-EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_batched", "pinv_submit",
+EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_complex", "pinv_solve_batched", "pinv_submit",
            "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_autotune", "pinv_drazin_index",
            "pinv_step_noalloc")
 NOALLOC_MAX_DIM = 128
@@ -85,6 +85,7 @@ def load() -> C.CDLL:
     lib.pinv_destroy.argtypes = [C.c_void_p]
     lib.pinv_destroy.restype = None
     lib.pinv_solve.argtypes = [C.c_void_p, P(Desc), C.c_void_p, P(Info)]
+    lib.pinv_solve_complex.argtypes = [C.c_void_p, P(Desc), C.c_void_p, P(Info)]
     lib.pinv_solve_batched.argtypes = [C.c_void_p, C.c_int, P(Desc), C.c_void_p, P(Info)]
     lib.pinv_submit.argtypes = [C.c_void_p, P(Desc), P(C.c_uint64)]
     lib.pinv_poll.argtypes = [C.c_void_p, C.c_uint64, P(Info)]
@@ -118,10 +119,11 @@ def _stream_ptr(stream) -> int | None:
     return int(getattr(stream, "cuda_stream", stream))
 
 
-def _dev_ptr(t) -> int:
+def _dev_ptr(t, cplx: bool = False) -> int:
     import torch
-    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64):
-        raise TypeError("expected a CUDA float64 tensor")
+    want = torch.complex128 if cplx else torch.float64
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == want):
+        raise TypeError(f"expected a CUDA {want} tensor")
     if t.stride(1) != 1:
         raise ValueError("matrices must be row-major (unit column stride)")
     return t.data_ptr()
@@ -154,18 +156,20 @@ class Handle:
     @staticmethod
     def make_desc(A, X, *, kind="moore_penrose", G=None, drazin_index=0, alpha=0.0, tol=1e-12,
                   stop="rel_fro", max_iter=0, prec="fp64", variant="plain", switch_tol=0.0,
-                  finish=None, check=False, host=False, profile=False, symmetric=False) -> Desc:
+                  finish=None, check=False, host=False, profile=False, symmetric=False,
+                  cplx=False) -> Desc:
         if host:
             import numpy as np
+            want = np.complex128 if cplx else np.float64
             for M in (A, X) + ((G,) if G is not None else ()):
-                if not (isinstance(M, np.ndarray) and M.dtype == np.float64 and M.flags.c_contiguous):
-                    raise TypeError("host buffers must be C-contiguous float64 numpy arrays")
+                if not (isinstance(M, np.ndarray) and M.dtype == want and M.flags.c_contiguous):
+                    raise TypeError(f"host buffers must be C-contiguous {np.dtype(want)} numpy arrays")
             a_ptr, x_ptr = A.ctypes.data, X.ctypes.data
             g_ptr = G.ctypes.data if G is not None else None
             lda, ldx, ldg = A.shape[1], X.shape[1], (G.shape[1] if G is not None else 0)
         else:
-            a_ptr, x_ptr = _dev_ptr(A), _dev_ptr(X)
-            g_ptr = _dev_ptr(G) if G is not None else None
+            a_ptr, x_ptr = _dev_ptr(A, cplx), _dev_ptr(X, cplx)
+            g_ptr = _dev_ptr(G, cplx) if G is not None else None
             lda, ldx = A.stride(0), X.stride(0)
             ldg = G.stride(0) if G is not None else 0
         m, n = A.shape
@@ -196,6 +200,25 @@ class Handle:
         rc = self._lib.pinv_solve(self._h, C.byref(d), C.c_void_p(st), C.byref(info))
         if rc != PINV_OK and raise_on_error:
             raise PinvError(rc, "pinv_solve")
+        return X, info.to_dict()
+
+    def solve_complex(self, A, X=None, *, stream=None, raise_on_error=True, **kw):
+        """pinv_solve_complex.  A: CUDA complex128 tensor (or complex128 numpy
+        with host=True).  Returns (X, info dict)."""
+        host = kw.get("host", False)
+        if X is None:
+            if host:
+                import numpy as np
+                X = np.empty((A.shape[1], A.shape[0]), dtype=np.complex128)
+            else:
+                import torch
+                X = torch.empty((A.shape[1], A.shape[0]), dtype=torch.complex128, device=A.device)
+        d = self.make_desc(A, X, cplx=True, **kw)
+        info = Info()
+        st = 0 if host and stream is None else _stream_ptr(stream)
+        rc = self._lib.pinv_solve_complex(self._h, C.byref(d), C.c_void_p(st), C.byref(info))
+        if rc != PINV_OK and raise_on_error:
+            raise PinvError(rc, "pinv_solve_complex")
         return X, info.to_dict()
 
     def solve_batched(self, As, Xs=None, *, stream=None, **kw):

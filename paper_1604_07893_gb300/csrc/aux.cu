@@ -208,6 +208,73 @@ __global__ void fill_pattern_kernel(int rows, int cols, double* X, int ld, unsig
     }
 }
 
+// ---- complex matrices as real embeddings E(Z) = [[Re Z, -Im Z], [Im Z, Re Z]]
+// (E is a *-homomorphism: E(ZW) = E(Z)E(W), E(Z^*) = E(Z)^T, so every
+// generalized inverse of Z is read off the same inverse of E(Z)).
+
+// E (2m x 2n, lde) from Z (m x n complex, interleaved re/im, ldz complex elements).
+__global__ void complex_embed_kernel(int m, int n, const double* Z, int ldz, double* E, int lde) {
+    const size_t total = (size_t)m * n;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / n, j = e % n;
+        const double re = Z[2 * (i * ldz + j)], im = Z[2 * (i * ldz + j) + 1];
+        E[i * lde + j] = re;
+        E[i * lde + n + j] = -im;
+        E[(i + m) * lde + j] = im;
+        E[(i + m) * lde + n + j] = re;
+    }
+}
+
+// Z (r x c complex, ldz) = the left column half of E (2r x 2c, lde): (E[i][j], E[r+i][j]).
+__global__ void complex_extract_kernel(int r, int c, const double* E, int lde, double* Z, int ldz) {
+    const size_t total = (size_t)r * c;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / c, j = e % c;
+        Z[2 * (i * ldz + j)] = E[i * lde + j];
+        Z[2 * (i * ldz + j) + 1] = E[(i + r) * lde + j];
+    }
+}
+
+// Right column half of an embedding from its left half [Re; Im] (M = 2r rows,
+// N2 = c columns): E[i][c+j] = -E[r+i][j], E[r+i][c+j] = E[i][j].
+__global__ void embed_mirror_kernel(int M, int N2, double* E, int ld) {
+    const int r = M / 2;
+    const size_t total = (size_t)r * N2;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = e / N2, j = e % N2;
+        const double re = E[i * ld + j], im = E[(i + r) * ld + j];
+        E[i * ld + N2 + j] = -im;
+        E[(i + r) * ld + N2 + j] = re;
+    }
+}
+
+// ||Z||_1 and ||Z||_inf partials with |z_ij| = hypot(Re, Im) read from the
+// left half of E (Z is m x n, E 2m x 2n).
+__global__ void complex_row_abs_max_kernel(int m, int n, const double* E, int lde, double* part) {
+    __shared__ double sh[32];
+    double best = 0.0;
+    for (int i = blockIdx.x; i < m; i += gridDim.x) {
+        double s = 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x)
+            s += hypot(E[(size_t)i * lde + j], E[(size_t)(i + m) * lde + j]);
+        s = block_sum(s, sh);
+        if (threadIdx.x == 0) best = fmax(best, s);
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
+}
+
+__global__ void complex_col_abs_max_kernel(int m, int n, const double* E, int lde, double* part) {
+    __shared__ double sh[32];
+    double best = 0.0;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < m; ++i) s += hypot(E[(size_t)i * lde + j], E[(size_t)(i + m) * lde + j]);
+        best = fmax(best, s);
+    }
+    best = block_max(best, sh);
+    if (threadIdx.x == 0) part[blockIdx.x] = best;
+}
+
 }  // namespace
 
 void fill_pattern(int rows, int cols, double* X, int ld, unsigned seed, cudaStream_t st) {
@@ -286,5 +353,32 @@ void diff_norms(int rows, int cols, const double* P, int ldp, const double* Q, i
 }
 
 int diff_norms_scratch_pairs() { return RED_CTAS; }
+
+namespace {
+int grid_for(size_t total) {
+    size_t blocks = (total + 255) / 256;
+    if (blocks > 152 * 8) blocks = 152 * 8;
+    return blocks < 1 ? 1 : (int)blocks;
+}
+}  // namespace
+
+void complex_embed(int m, int n, const double* Z, int ldz, double* E, int lde, cudaStream_t st) {
+    complex_embed_kernel<<<grid_for((size_t)m * n), 256, 0, st>>>(m, n, Z, ldz, E, lde);
+}
+
+void complex_extract(int r, int c, const double* E, int lde, double* Z, int ldz, cudaStream_t st) {
+    complex_extract_kernel<<<grid_for((size_t)r * c), 256, 0, st>>>(r, c, E, lde, Z, ldz);
+}
+
+void embed_mirror(int M, int N2, double* E, int ld, cudaStream_t st) {
+    embed_mirror_kernel<<<grid_for((size_t)(M / 2) * N2), 256, 0, st>>>(M, N2, E, ld);
+}
+
+void complex_norms_1_inf(int m, int n, const double* E, int lde, double* out, double* scratch, cudaStream_t st) {
+    complex_col_abs_max_kernel<<<RED_CTAS, RED_THREADS, 0, st>>>(m, n, E, lde, scratch);
+    max_kernel<<<1, RED_THREADS, 0, st>>>(scratch, RED_CTAS, out);
+    complex_row_abs_max_kernel<<<RED_CTAS, RED_THREADS, 0, st>>>(m, n, E, lde, scratch + RED_CTAS);
+    max_kernel<<<1, RED_THREADS, 0, st>>>(scratch + RED_CTAS, RED_CTAS, out + 1);
+}
 
 }  // namespace pinv

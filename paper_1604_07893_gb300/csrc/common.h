@@ -75,6 +75,17 @@ void diff_norms(int rows, int cols, const double* P, int ldp, const double* Q, i
                 bool transQ, double* out, double* scratch, cudaStream_t st);
 int diff_norms_scratch_pairs();
 
+// Complex matrices as real embeddings E(Z) = [[Re Z, -Im Z], [Im Z, Re Z]]; Z is
+// stored interleaved (re, im) with its leading dimension in complex elements.
+// E (2m x 2n, lde) = E(Z), Z m x n.
+void complex_embed(int m, int n, const double* Z, int ldz, double* E, int lde, cudaStream_t st);
+// Z (r x c) from the left column half of E (2r x 2c): Z_ij = E[i][j] + i E[r+i][j].
+void complex_extract(int r, int c, const double* E, int lde, double* Z, int ldz, cudaStream_t st);
+// Right column half of an embedding (M rows, 2 N2 columns) from its left half.
+void embed_mirror(int M, int N2, double* E, int ld, cudaStream_t st);
+// out[0] = ||Z||_1, out[1] = ||Z||_inf with complex moduli, Z m x n read from E(Z).
+void complex_norms_1_inf(int m, int n, const double* E, int lde, double* out, double* scratch, cudaStream_t st);
+
 // X[i][j] = a deterministic pseudo-random value in (-1, 1) from (i, j, seed).
 void fill_pattern(int rows, int cols, double* X, int ld, unsigned seed, cudaStream_t st);
 

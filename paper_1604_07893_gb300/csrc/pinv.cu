@@ -160,6 +160,7 @@ struct Ctx {
     size_t tcws_bytes = 0;
     int gemms = 0;
     bool replay = false;    // loops replayed from cached graphs (A copied into the workspace)
+    bool cplx = false;      // complex problem solved as its real embedding (m, n above are 2x)
     int kernels = 0;
     bool profile = false;
     int ev_used = 0;        // event pairs recorded since the last harvest
@@ -251,6 +252,16 @@ void carve(Ctx& c, bool drazin, bool host, bool check, int prec) {
 
 int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const double* B, int ldb,
          bool tB, const Epilogue& e, bool sym = false) {
+    // Complex problems: every matrix is held as its embedding E(Z) =
+    // [[Re Z, -Im Z], [Im Z, Re Z]], and E(C) = E(A) E(B).  The left column half
+    // of E(C), [Re C; Im C], needs only the left half of E(B) (the 4M complex
+    // product: half the work of the full real product); a mirror kernel writes
+    // the right half.  The epilogue sees the left half only, so its stop-norm
+    // partials are the complex Frobenius norms.
+    if (c.cplx) {
+        N /= 2;
+        sym = false;
+    }
     ++c.gemms;
     ++c.kernels;
     c.gemm_flops += 2.0 * M * N * K * c.batch;   // algorithmic work of the full product
@@ -273,6 +284,13 @@ int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const d
         r = tc_gemm(M, N, K, A, lda, tA, B, ldb, tB, e, tc_mode(c.prec_k), c.tcws, c.tcws_bytes,
                     c.h->derr, c.st, &c.kernels, prof_ev(c, slot, 0), prof_ev(c, slot, 1), c.batch,
                     c.stride, c.yield_sms, sym);
+    }
+    if (c.cplx && r >= 0) {
+        for (int o = 0; o < e.nout; ++o) {
+            if (!e.o[o].out) continue;
+            embed_mirror(M, N, e.o[o].out, e.o[o].ld, c.st);
+            ++c.kernels;
+        }
     }
     return r;
 }
@@ -512,25 +530,55 @@ int validate(const pinv_desc* d) {
 // Largest side of a single solve whose loops are replayed from cached graphs.
 constexpr int kReplayMaxDim = 512;
 
-int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c) {
+int setup_context(pinv_handle* h, const pinv_desc* d, cudaStream_t st, Ctx& c, bool cplx = false) {
     c.h = h;
     c.st = st;
-    c.m = d->m;
-    c.n = d->n;
-    c.left = d->m > d->n;  // residual on the smaller side; the paper's right form when m <= n
-    c.s = c.left ? d->n : d->m;
+    c.cplx = cplx;
+    c.m = cplx ? 2 * d->m : d->m;   // complex: the real embedding is 2m x 2n
+    c.n = cplx ? 2 * d->n : d->n;
+    c.left = c.m > c.n;  // residual on the smaller side; the paper's right form when m <= n
+    c.s = c.left ? c.n : c.m;
     c.c = pm_coefficients();
     const bool drazin = d->kind == PINV_DRAZIN || d->kind == PINV_DRAZIN_NORMAL;
     const bool host = d->host_buffers != 0;
     const bool check = d->check != 0 || d->finish == PINV_FINISH_CLEAN;
-    c.replay = !c.profile && std::max(d->m, d->n) <= kReplayMaxDim;
-    const bool own_a = host || c.replay;   // A (and G) live in the workspace
-    size_t bytes = workspace_bytes(d->m, d->n, drazin, own_a, check, d->prec);
+    c.replay = !c.profile && std::max(c.m, c.n) <= kReplayMaxDim;
+    const bool own_a = host || c.replay || cplx;   // A (and G) live in the workspace
+    size_t bytes = workspace_bytes(c.m, c.n, drazin, own_a, check, d->prec);
     int rc = ensure_workspace(h, bytes);
     if (rc) return rc;
     carve(c, drazin, own_a, check, d->prec);
     c.prec_k = d->prec == PINV_PREC_FP64 ? 0 : TC_FP64;
-    c.symmetric = iterates_symmetric(d);
+    c.symmetric = !cplx && iterates_symmetric(d);
+    if (cplx) {
+        // A (m x n complex) -> E(A) in the workspace; host inputs are staged in
+        // the half-step and pong iterates, which are free until the first loop
+        const double* Z = d->A;
+        int ldz = d->lda;
+        if (host) {
+            CK(cudaMemcpy2DAsync(c.X[2], 2 * sizeof(double) * d->n, d->A, 2 * sizeof(double) * d->lda,
+                                 2 * sizeof(double) * d->n, d->m, cudaMemcpyHostToDevice, st));
+            Z = c.X[2];
+            ldz = d->n;
+        }
+        complex_embed(d->m, d->n, Z, ldz, c.Ad, c.n, st);
+        ++c.kernels;
+        c.A = c.Ad;
+        c.lda = c.n;
+        if (d->kind == PINV_OUTER_G) {   // G (n x m complex) -> E(G), 2n x 2m
+            const double* Zg = d->G;
+            int ldg = d->ldg;
+            if (host) {
+                CK(cudaMemcpy2DAsync(c.X[1], 2 * sizeof(double) * d->m, d->G, 2 * sizeof(double) * d->ldg,
+                                     2 * sizeof(double) * d->m, d->n, cudaMemcpyHostToDevice, st));
+                Zg = c.X[1];
+                ldg = d->m;
+            }
+            complex_embed(d->n, d->m, Zg, ldg, c.Gd, c.m, st);
+            ++c.kernels;
+        }
+        return PINV_OK;
+    }
     if (host) {
         CK(cudaMemcpy2DAsync(c.Ad, sizeof(double) * d->n, d->A, sizeof(double) * d->lda,
                              sizeof(double) * d->n, d->m, cudaMemcpyHostToDevice, st));
@@ -576,7 +624,8 @@ int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
             gemm(c, n, n, n, c.Al, n, false, Wm, n, false, epi1(term(c.X[1], m, 1)));   // G
             if (a == 0.0) {   // 1 / sqrt(||GA||_1 ||GA||_inf) <= 1 / ||GA||_2
                 gemm(c, n, n, n, c.X[1], m, false, c.A, c.lda, false, epi1(term(A2, n, 1)));
-                norms_1_inf(n, n, A2, n, c.h->dsmall, c.red, c.st);
+                if (c.cplx) complex_norms_1_inf(n / 2, n / 2, A2, n, c.h->dsmall, c.red, c.st);
+                else        norms_1_inf(n, n, A2, n, c.h->dsmall, c.red, c.st);
                 c.kernels += 4;
                 CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
                 CK(cudaStreamSynchronize(c.st));
@@ -594,15 +643,17 @@ int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
             c.kernels += 2;
             CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, sizeof(double), cudaMemcpyDeviceToHost, c.st));
             CK(cudaStreamSynchronize(c.st));
-            const double tr = c.h->pinned[0];
+            // complex: Tr E(A^{l+1}) = 2 Re Tr(A^{l+1}); alpha = 1 / Re Tr(A^{l+1})
+            const double tr = c.cplx ? 0.5 * c.h->pinned[0] : c.h->pinned[0];
             if (!(tr > 0.0) || !std::isfinite(tr)) return PINV_ERR_ARG;
             a = 1.0 / tr;
         }
         scale_copy(n, n, c.Al, n, a, c.X[0], m, c.st);
         ++c.kernels;
     } else {
-        if (a == 0.0) {  // 1 / (||A||_1 ||A||_inf)
-            norms_1_inf(m, n, c.A, c.lda, c.h->dsmall, c.red, c.st);
+        if (a == 0.0) {  // 1 / (||A||_1 ||A||_inf), with complex moduli for complex A
+            if (c.cplx) complex_norms_1_inf(m / 2, n / 2, c.A, c.lda, c.h->dsmall, c.red, c.st);
+            else        norms_1_inf(m, n, c.A, c.lda, c.h->dsmall, c.red, c.st);
             c.kernels += 4;
             CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
             CK(cudaStreamSynchronize(c.st));
@@ -614,8 +665,9 @@ int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
             transpose_scale(m, n, c.A, c.lda, a, c.X[0], m, c.st);
             ++c.kernels;
         } else {
-            const double* G = d->host_buffers ? c.Gd : d->G;
-            const int ldg = d->host_buffers ? m : d->ldg;
+            const bool own_g = d->host_buffers || c.cplx;
+            const double* G = own_g ? c.Gd : d->G;
+            const int ldg = own_g ? m : d->ldg;
             scale_copy(n, m, G, ldg, a, c.X[0], m, c.st);
             ++c.kernels;
         }
@@ -704,7 +756,7 @@ int device_loop(Ctx& c, const pinv_desc* d, double alpha, int max_iter, pinv_inf
         CK(cudaMalloc((void**)&h->dstate, sizeof(DeviceLoopState)));
         CK(cudaMallocHost((void**)&h->hstate, sizeof(DeviceLoopState)));
     }
-    std::vector<long long> key = {-1, c.m, c.n, c.left, c.symmetric, c.prec_k, h->tc_crossover,
+    std::vector<long long> key = {-1, c.m, c.n, c.left, c.symmetric, c.cplx, c.prec_k, h->tc_crossover,
                                   (long long)c.A, c.lda, (long long)c.X[0], (long long)c.X[1],
                                   (long long)c.sq[0], (long long)c.partials, (long long)c.tcws,
                                   (long long)c.tcws_bytes};
@@ -808,7 +860,7 @@ int replay_loop(Ctx& c, int cur, bool stab, double* dx2, double* x2) {
     pinv_handle* h = c.h;
     const double* Xk = c.X[cur];
     double* Xn = c.X[cur ^ 1];
-    std::vector<long long> key = {c.m, c.n, c.left, c.symmetric, c.prec_k, stab, h->tc_crossover,
+    std::vector<long long> key = {c.m, c.n, c.left, c.symmetric, c.cplx, c.prec_k, stab, h->tc_crossover,
                                   (long long)c.A, c.lda, (long long)Xk, (long long)Xn, (long long)c.X[2],
                                   (long long)c.sq[0], (long long)c.partials, (long long)c.tcws,
                                   (long long)c.tcws_bytes};
@@ -869,14 +921,15 @@ int replay_loop(Ctx& c, int cur, bool stab, double* dx2, double* x2) {
     return PINV_OK;
 }
 
-int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* info) {
+int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* info, bool cplx = false) {
     auto t0 = std::chrono::steady_clock::now();
     std::memset(info, 0, sizeof(*info));
     int rc = validate(d);
+    if (!rc && cplx && d->symmetric) rc = PINV_ERR_ARG;
     if (rc) return info->status = rc;
     Ctx c{};
     c.profile = d->profile != 0;
-    rc = setup_context(h, d, st, c);
+    rc = setup_context(h, d, st, c, cplx);
     if (rc) return info->status = rc;
     info->side = c.left ? 1 : 0;
     double alpha = 0.0;
@@ -992,7 +1045,17 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         rc = residual_checks(c, d, Xfinal, info);
         if (rc) return info->status = rc;
     }
-    if (d->host_buffers) {
+    if (c.cplx) {   // X (n x m complex) from the left half of E(X)
+        if (d->host_buffers) {
+            double* Z = c.X[cur ^ 1];
+            complex_extract(d->n, d->m, Xfinal, c.m, Z, d->m, st);
+            CK(cudaMemcpy2DAsync(d->X, 2 * sizeof(double) * d->ldx, Z, 2 * sizeof(double) * d->m,
+                                 2 * sizeof(double) * d->m, d->n, cudaMemcpyDeviceToHost, st));
+        } else {
+            complex_extract(d->n, d->m, Xfinal, c.m, d->X, d->ldx, st);
+        }
+        ++c.kernels;
+    } else if (d->host_buffers) {
         CK(cudaMemcpy2DAsync(d->X, sizeof(double) * d->ldx, Xfinal, sizeof(double) * c.m,
                              sizeof(double) * c.m, c.n, cudaMemcpyDeviceToHost, st));
     } else {
@@ -1602,6 +1665,14 @@ int pinv_solve(pinv_handle* h, const pinv_desc* desc, void* stream, pinv_info* i
     pinv_info* out = info ? info : &local;
     if (cudaSetDevice(h->device) != cudaSuccess) return out->status = PINV_ERR_CUDA;
     return solve_one(h, desc, (cudaStream_t)stream, out);
+}
+
+int pinv_solve_complex(pinv_handle* h, const pinv_desc* desc, void* stream, pinv_info* info) {
+    if (!h) return PINV_ERR_ARG;
+    pinv_info local;
+    pinv_info* out = info ? info : &local;
+    if (cudaSetDevice(h->device) != cudaSuccess) return out->status = PINV_ERR_CUDA;
+    return solve_one(h, desc, (cudaStream_t)stream, out, true);
 }
 
 int pinv_solve_batched(pinv_handle* h, int count, const pinv_desc* descs, void* stream,
