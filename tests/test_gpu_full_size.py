@@ -45,6 +45,19 @@ def test_moore_penrose_4096x3072_as_benchmarked(handle):
     assert max(info["penrose"]) <= 1e-9
 
 
+def test_complex_moore_penrose_2048x1536_as_benchmarked(handle):
+    """Complex rank 1152, s log-spaced in [1e-4, 1] (the complex workload of the
+    benchmark: its embedding has the headline's 4096 x 3072 shape)."""
+    w = W.rectangular_complex(2048, 1536, 1152, 1.0, 1e-4, seed=1)
+    alpha = 2.0 / (w.s[0] ** 2 + w.s[-1] ** 2)
+    X, info = handle.solve_complex(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp64_tc",
+                                   variant="stabilized", switch_tol=0.5, finish="clean", check=True)
+    assert info["status"] == 0
+    rows = np.random.default_rng(0).choice(1536, 32, replace=False)
+    assert rel(X.cpu().numpy()[rows], (w.V[rows] / w.s) @ w.U.conj().T) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9
+
+
 def test_drazin_2048_as_benchmarked(handle):
     """Index 2 (256 2x2 Jordan blocks), X0 = A^2 / Tr(A^3), order-18 stop,
     finish A^2 X^5 A^2 + one order-2 step."""
