@@ -24,6 +24,8 @@ generalized inverse of a matrix"):
   iteration is not self-correcting for generalized inverses);
 * initial values of Section 4: alpha*A^T, A^l/Tr(A^{l+1}), alpha*G, with
   alpha = 2/(sigma_1^2 + sigma_r^2) or 1/(||A||_1 ||A||_inf);
+* the approximate-inverse preconditioner of Section 8, Example 3: loops of
+  the step from the Jacobi X0 = diag(1/a_ii), each followed by a chop;
 * residual checks: the Penrose equations and the Drazin equations;
 * the computational order of convergence of Eq. COC (Section 8).
 
@@ -238,6 +240,15 @@ def x0_drazin_normal(A: np.ndarray, l: int, alpha=None) -> np.ndarray:
     return alpha * G
 
 
+def x0_jacobi(A: np.ndarray, alpha=1.0) -> np.ndarray:
+    """X0 = alpha diag(1/a_11, ..., 1/a_nn), the initial matrix of Section 8's
+    preconditioning example (Eq. choice3); alpha = 1 as printed."""
+    d = np.diag(A)
+    if np.any(d == 0):
+        raise ValueError("a zero diagonal entry: no Jacobi initial value")
+    return alpha * np.diag(1.0 / d)
+
+
 def alpha_pan_schreiber(sigma_1: float, sigma_r: float) -> float:
     """alpha = 2 / (sigma_1^2 + sigma_r^2) (Section 4), sigma_1 >= sigma_r > 0 the
     extreme nonzero singular values of A (reading of 'eigenvalues of GA' for
@@ -269,6 +280,36 @@ def cleanup_drazin(A: np.ndarray, X: np.ndarray, l: int) -> np.ndarray:
     projects an approximate Drazin inverse back onto R(A^l), N(A^l)."""
     Al = matpow(A, l)
     return Al @ matpow(X, 2 * l + 1) @ Al
+
+
+# ----------------------------------------------------------------------------
+# approximate-inverse preconditioners (Section 8, Example 3; the concluding
+# remark that one loop of the method already gives a preconditioner)
+# ----------------------------------------------------------------------------
+
+def chop(X: np.ndarray, eps: float) -> np.ndarray:
+    """Sparsification after each loop in Example 3: every entry of magnitude
+    below eps becomes 0; for complex entries the real and imaginary parts are
+    tested and zeroed separately (reading of the Chop command used there)."""
+    if np.iscomplexobj(X):
+        re = np.where(np.abs(X.real) < eps, 0.0, X.real)
+        im = np.where(np.abs(X.imag) < eps, 0.0, X.imag)
+        return re + 1j * im
+    return np.where(np.abs(X) < eps, 0.0, X)
+
+
+def preconditioner(A: np.ndarray, loops: int = 1, chop_eps: float = 0.0, alpha=1.0):
+    """X_k after ``loops`` loops of the order-18 step from the Jacobi X0
+    (Eq. choice3), each loop followed by the chop when chop_eps > 0.  Returns
+    (X_k, the relative step of every loop, measured before its chop)."""
+    X = x0_jacobi(A, alpha)
+    side = choose_side(*A.shape)
+    steps = []
+    for k in range(loops):
+        Xn = hyperpower_step(A, X, P_ORDER, side)
+        steps.append(stop_measure(Xn, X, k, 1.0, STOP_REL_FRO))
+        X = chop(Xn, chop_eps) if chop_eps > 0 else Xn
+    return X, steps
 
 
 # ----------------------------------------------------------------------------

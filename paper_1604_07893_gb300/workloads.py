@@ -18,6 +18,9 @@ ill-conditioned Moore-Penrose problems and preconditioning of a large matrix):
 * ``uneven_batch`` many independent rectangular problems of random shape.
 * ``poisson_arrivals`` request arrival times for the serving workload.
 * ``hilbert``      H_ij = 1/(i+j-1) (Section 8 Example 2).
+* ``grid_operator``: a shifted five-point operator on a k x k grid, real or
+  complex (the sparse-system stand-in for the preconditioning example of
+  Section 8, whose MatrixMarket matrix is not used).
 * ``rectangular_complex``, ``drazin_complex``, ``hpd_complex``: the same
   families over C (the paper states the method for complex matrices, with
   A^* the conjugate transpose; Section 1.1), complex128 arrays.
@@ -300,3 +303,31 @@ def hpd_complex(n: int, lam_min: float = 1e-3, lam_max: float = 1.0, seed: int =
     A = (Q * lam) @ Q.conj().T
     A = 0.5 * (A + A.conj().T)
     return SPD(A=np.ascontiguousarray(A), Q=Q, lam=lam)
+
+
+def grid_operator(k: int, shift: complex = 0.5 + 0.5j, jitter: float = 0.05, seed: int = 7,
+                  complex_: bool = True) -> np.ndarray:
+    """Dense n x n (n = k^2) matrix of a five-point operator on a k x k grid:
+    diagonal 4 + shift, -1 to each grid neighbour, every coupling and diagonal
+    entry perturbed by a factor (1 + jitter * g) with g standard Gaussian
+    (complex Gaussian when ``complex_``; the real part of ``shift`` otherwise).
+    Sparse (at most five nonzeros a row) but not banded."""
+    rng = np.random.default_rng(seed)
+    n = k * k
+
+    def g(size):
+        if complex_:
+            return (rng.standard_normal(size) + 1j * rng.standard_normal(size)) / math.sqrt(2.0)
+        return rng.standard_normal(size)
+
+    A = np.zeros((n, n), dtype=np.complex128 if complex_ else np.float64)
+    s = shift if complex_ else float(np.real(shift))
+    idx = np.arange(n)
+    A[idx, idx] = (4.0 + s) * (1.0 + jitter * g(n))
+    for di, dj in ((0, 1), (1, 0), (0, -1), (-1, 0)):
+        for i in range(k):
+            for j in range(k):
+                ii, jj = i + di, j + dj
+                if 0 <= ii < k and 0 <= jj < k:
+                    A[i * k + j, ii * k + jj] = -1.0 * (1.0 + jitter * g(1)[0])
+    return A

@@ -570,3 +570,59 @@ def test_complex_drazin_closed_form():
     X3, info3 = H.solve(d2.A, H.x0_drazin_normal(d2.A, 2), tol=1e-2, stop=H.STOP_ORDER18, alpha=1.0)
     assert info3.status == "converged"
     assert rel(X3, drazin_closed_form(d2)) < 1e-10
+
+
+# --------------------------------------------------------------------------
+# approximate-inverse preconditioner (Section 8, Example 3)
+# --------------------------------------------------------------------------
+
+def test_jacobi_initial_value_by_hand():
+    A = np.array([[2.0, 1.0], [3.0, -4.0]])
+    assert np.array_equal(H.x0_jacobi(A), np.array([[0.5, 0.0], [0.0, -0.25]]))
+    Z = np.array([[1 + 1j, 0], [2, 2j]])
+    assert np.allclose(H.x0_jacobi(Z), np.diag([0.5 - 0.5j, -0.5j]), rtol=0, atol=1e-16)
+    with pytest.raises(ValueError):
+        H.x0_jacobi(np.array([[0.0, 1.0], [1.0, 1.0]]))
+
+
+def test_chop_by_hand():
+    x = np.array([[1e-6, -2e-5, 3.0], [-1e-7, 0.0, 1e-5]])
+    assert np.array_equal(H.chop(x, 1e-5), np.array([[0.0, -2e-5, 3.0], [0.0, 0.0, 1e-5]]))
+    z = np.array([1.0 + 1e-6j, 1e-6 + 2j, 1e-7 - 1e-7j])
+    assert np.array_equal(H.chop(z, 1e-5), np.array([1.0 + 0j, 2j, 0j]))
+
+
+def test_jacobi_of_a_diagonal_matrix_is_its_inverse():
+    A = np.diag([2.0, -3.0, 0.5, 7.0])
+    X, steps = H.preconditioner(A, loops=1)
+    assert rel(X, np.linalg.inv(A)) < 1e-15
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_one_loop_preconditioner_residual_is_the_18th_power(complex_):
+    """X1 from X0 = D^{-1}: I - X1 A = (I - X0 A)^18 and I - A X1 = (I - A X0)^18
+    (X0 (I - A X0)^j = (I - X0 A)^j X0), so ||I - X1 A|| = ||R0^18||."""
+    A = W.grid_operator(6, seed=7, complex_=complex_)
+    n = A.shape[0]
+    I = np.eye(n)
+    X0 = H.x0_jacobi(A)
+    X1, steps = H.preconditioner(A, loops=1)
+    L0 = I - X0 @ A
+    assert rel(I - X1 @ A, np.linalg.matrix_power(L0, 18)) < 1e-12
+    assert rel(I - A @ X1, np.linalg.matrix_power(I - A @ X0, 18)) < 1e-12
+    rho = max(abs(np.linalg.eigvals(L0)))
+    assert rho < 0.95
+    assert max(abs(np.linalg.eigvals(I - X1 @ A))) == pytest.approx(rho ** 18, rel=1e-6)
+    # a second loop: the 18^2 = 324th power
+    X2, _ = H.preconditioner(A, loops=2)
+    assert np.linalg.norm(I - X2 @ A) < 10 * np.linalg.norm(np.linalg.matrix_power(L0, 324)) + 1e-13
+
+
+def test_chopped_preconditioner_stays_close_and_sparse():
+    A = W.grid_operator(8, seed=8)
+    X1, _ = H.preconditioner(A, loops=1)
+    Xc, _ = H.preconditioner(A, loops=1, chop_eps=1e-5)
+    assert np.count_nonzero(Xc) < np.count_nonzero(X1)
+    diff = Xc - X1
+    assert np.abs(diff.real).max() < 1e-5 and np.abs(diff.imag).max() < 1e-5
+    assert np.array_equal(Xc, H.chop(X1, 1e-5))
