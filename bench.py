@@ -743,6 +743,64 @@ def run_complex(args):
     h.close()
 
 
+def run_precond(args):
+    """Approximate-inverse preconditioners (Section 8, Example 3): one loop of
+    Eq. PM from the Jacobi X0 = diag(1/a_ii), chop 1e-5, for complex shifted
+    five-point grid operators -- n = 841 (a 29 x 29 grid, the size of the
+    paper's example; latency-bound) and n = 4096 (a 64 x 64 grid)."""
+    import torch
+    from oracle import hyperpower as H
+    from paper_1604_07893_gb300 import Handle, workloads as W
+    h = Handle(0)
+    st = torch.cuda.current_stream()
+    crossover = h.autotune()
+    out = {}
+    for k, precs in ((29, ("fp64_tc",)), (64, ("fp64_tc", "fp32"))):
+        A_np = W.grid_operator(k, seed=7)
+        n = k * k
+        A = torch.from_numpy(A_np).cuda()
+        X = torch.empty_like(A)
+        I = torch.eye(n, dtype=A.dtype, device=A.device)
+        for prec in precs:
+            kw = dict(loops=1, chop=1e-5, prec=prec)
+            for _ in range(args.warmup):
+                h.preconditioner(A, X, **kw)
+            torch.cuda.synchronize()
+            lat, infos = [], []
+            for _ in range(max(args.steps, 20 if n < 1000 else 3)):
+                e0, e1 = _events(st)
+                e0.record(st)
+                _, info = h.preconditioner(A, X, profile=True, **kw)
+                e1.record(st)
+                torch.cuda.synchronize()
+                lat.append(e0.elapsed_time(e1))
+                infos.append(info)
+            resid = float(torch.linalg.matrix_norm(I - X @ A).item()) / math.sqrt(n)
+            gemm_ms = sum(i["gemm_ms"] for i in infos)
+            peaks, _ = load_peaks()
+            peak, _ = dominant_peak(prec, peaks)
+            tflops = sum(i["tensor_flops"] for i in infos) / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
+            out[f"n{n}_{prec}"] = {"value": 1e3 / statistics.mean(lat), "p50_ms": statistics.median(lat),
+                                   "p99_ms": _pct(lat, 0.99), "kernels": infos[-1]["kernels"],
+                                   "fro_I_minus_XA_over_sqrt_n": resid,
+                                   "nonzero_fraction": float((torch.view_as_real(X) != 0).double().mean().item()),
+                                   "tc_tflops": tflops, "tc_frac": (tflops / peak) if tflops else None}
+    A841 = W.grid_operator(29, seed=7)
+    t0 = time.perf_counter()
+    H.preconditioner(A841, loops=1, chop_eps=1e-5)
+    t841 = time.perf_counter() - t0
+    _emit({"metric": "preconditioners/s (one PM loop from Jacobi, chop 1e-5)", "value": out["n841_fp64_tc"]["value"],
+           "unit": "preconditioners/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
+           "dtype": "bf16 slices (fp64-/fp32-class), complex as real embedding",
+           "config": {"workload": "jacobi_pm1_preconditioner_complex_grid", "sizes": [841, 4096], "loops": 1,
+                      "chop": 1e-5, "operator": "shifted five-point grid, complex, 5% jitter",
+                      "steps": args.steps, "warmup": args.warmup},
+           "engine_crossover": crossover, "results": out,
+           "cpu_baseline": {"value": 1.0 / t841, "unit": "preconditioners/s", "kind": "oracle",
+                            "cores": len(os.sched_getaffinity(0)), "sample": "full n = 841 preconditioner"}})
+    h.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -753,7 +811,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--workload", default="mp4096x3072",
-                    choices=["mp4096x3072", "mp64x48", "drazin2048", "batched4096", "serving", "complex2048x1536"])
+                    choices=["mp4096x3072", "mp64x48", "drazin2048", "batched4096", "serving", "complex2048x1536",
+                             "precond"])
     ap.add_argument("--count", type=int, default=None, help="instances (batched) or requests (serving)")
     args = ap.parse_args()
     if args.impl == "reference":
@@ -764,6 +823,8 @@ def main():
         return run_drazin(args)
     if args.workload == "complex2048x1536":
         return run_complex(args)
+    if args.workload == "precond":
+        return run_precond(args)
     if args.workload == "batched4096":
         args.count = args.count or 4096
         return run_batched(args)

@@ -157,6 +157,27 @@ typedef struct {
     int          reserved[2];
 } pinv_desc;
 
+/* Approximate-inverse preconditioner request (pinv_preconditioner). */
+typedef struct {
+    int n;                   /* A is n x n (square), X n x n                       */
+    const double *A; int lda;
+    double       *X; int ldx;/* output X_k                                          */
+    int          loops;      /* loops of Eq. PM from X0, 1 .. PINV_HISTORY (the
+                                paper's preconditioner is X_1)                     */
+    double       alpha;      /* X0 = alpha diag(1/a_11 .. 1/a_nn); 0 = 1 (Eq. choice3) */
+    double       chop;       /* > 0: after every loop, entries of magnitude < chop
+                                become 0 (complex: real and imaginary parts
+                                separately), the sparsification of Section 8,
+                                Example 3 (it used 1e-5); 0: none                  */
+    pinv_prec    prec;       /* product class: FP64 (DMMA), FP64_TC, FP32 (FP32-
+                                class), MIXED_BF16 or BF16_FP32 (BF16 products)    */
+    int          complex_matrix; /* 1: A and X are complex, interleaved (re, im)
+                                    pairs, leading dimensions in complex elements  */
+    int          host_buffers;   /* 1: A and X are host pointers (as in pinv_desc) */
+    int          profile;        /* 1: time the GEMMs (info->gemm_ms)              */
+    int          reserved[4];
+} pinv_precond_desc;
+
 #define PINV_HISTORY 128
 typedef struct {
     int    status;           /* PINV_OK or the error code                           */
@@ -201,6 +222,20 @@ void pinv_destroy(pinv_handle *h);
  * kept).  Blocks the host until the result is in desc->X.  Not re-entrant on
  * one handle. */
 int  pinv_solve(pinv_handle *h, const pinv_desc *desc, void *stream, pinv_info *info);
+
+/* Approximate-inverse preconditioner (Section 8, Example 3, and the closing
+ * remark of the paper that one full loop of a high-order method already gives
+ * one): X_k after desc->loops loops of Eq. PM (right residual I - AX) from the
+ * Jacobi initial value X0 = alpha diag(1/a_ii) (Eq. choice3), each loop
+ * followed by the chop when desc->chop > 0.  Without the chop,
+ * I - X_k A = (I - X0 A)^(18^k): the preconditioned matrix X_k A is as close
+ * to I as the 18^k-th power of the Jacobi iteration matrix allows.  There is
+ * no stop rule: the loops run as asked.  info->history holds each loop's
+ * relative step (before its chop), info->iters = loops.
+ * PINV_ERR_ARG for a bad shape, a zero diagonal entry or an unknown prec;
+ * PINV_ERR_NONFINITE if a step is not finite (X0 outside the convergence
+ * region of Theorem 3.1 grows without bound). */
+int  pinv_preconditioner(pinv_handle *h, const pinv_precond_desc *desc, void *stream, pinv_info *info);
 
 /* Complex matrices (the paper's setting: A in C^{m x n}, A^* the conjugate
  * transpose, Section 1.1; Theorem 3.1 holds over C).  Same descriptor and

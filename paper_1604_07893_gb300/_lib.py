@@ -24,7 +24,8 @@ VARIANT = {"plain": 0, "stabilized": 1}
 FINISH = {None: 0, "none": 0, "clean": 1}
 HISTORY = 128
 
-EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_complex", "pinv_solve_batched", "pinv_submit",
+EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_complex", "pinv_preconditioner",
+           "pinv_solve_batched", "pinv_submit",
            "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_autotune", "pinv_drazin_index",
            "pinv_step_noalloc")
 NOALLOC_MAX_DIM = 128
@@ -45,6 +46,13 @@ class Desc(C.Structure):
                 ("switch_tol", C.c_double), ("finish", C.c_int), ("host_buffers", C.c_int),
                 ("check", C.c_int), ("profile", C.c_int), ("symmetric", C.c_int),
                 ("reserved", C.c_int * 2)]
+
+
+class PrecondDesc(C.Structure):
+    _fields_ = [("n", C.c_int), ("A", C.c_void_p), ("lda", C.c_int), ("X", C.c_void_p), ("ldx", C.c_int),
+                ("loops", C.c_int), ("alpha", C.c_double), ("chop", C.c_double), ("prec", C.c_int),
+                ("complex_matrix", C.c_int), ("host_buffers", C.c_int), ("profile", C.c_int),
+                ("reserved", C.c_int * 4)]
 
 
 class Info(C.Structure):
@@ -86,6 +94,7 @@ def load() -> C.CDLL:
     lib.pinv_destroy.restype = None
     lib.pinv_solve.argtypes = [C.c_void_p, P(Desc), C.c_void_p, P(Info)]
     lib.pinv_solve_complex.argtypes = [C.c_void_p, P(Desc), C.c_void_p, P(Info)]
+    lib.pinv_preconditioner.argtypes = [C.c_void_p, P(PrecondDesc), C.c_void_p, P(Info)]
     lib.pinv_solve_batched.argtypes = [C.c_void_p, C.c_int, P(Desc), C.c_void_p, P(Info)]
     lib.pinv_submit.argtypes = [C.c_void_p, P(Desc), P(C.c_uint64)]
     lib.pinv_poll.argtypes = [C.c_void_p, C.c_uint64, P(Info)]
@@ -219,6 +228,40 @@ class Handle:
         rc = self._lib.pinv_solve_complex(self._h, C.byref(d), C.c_void_p(st), C.byref(info))
         if rc != PINV_OK and raise_on_error:
             raise PinvError(rc, "pinv_solve_complex")
+        return X, info.to_dict()
+
+    def preconditioner(self, A, X=None, *, loops=1, chop=0.0, alpha=0.0, prec="fp64", host=False,
+                       profile=False, stream=None, raise_on_error=True):
+        """pinv_preconditioner: X_loops from the Jacobi X0 (Section 8, Example 3).
+        A: square CUDA float64/complex128 tensor, or numpy with host=True.
+        Returns (X, info dict)."""
+        n = A.shape[0]
+        if A.shape[1] != n:
+            raise ValueError("square matrix required")
+        if host:
+            import numpy as np
+            cplx = A.dtype == np.complex128
+            if X is None:
+                X = np.empty((n, n), dtype=A.dtype)
+            for M in (A, X):
+                if not (isinstance(M, np.ndarray) and M.dtype == A.dtype and M.flags.c_contiguous and
+                        M.dtype in (np.float64, np.complex128)):
+                    raise TypeError("host buffers must be C-contiguous float64 or complex128 numpy arrays")
+            a_ptr, x_ptr, lda, ldx = A.ctypes.data, X.ctypes.data, A.shape[1], X.shape[1]
+        else:
+            import torch
+            cplx = A.dtype == torch.complex128
+            if X is None:
+                X = torch.empty((n, n), dtype=A.dtype, device=A.device)
+            a_ptr, x_ptr, lda, ldx = _dev_ptr(A, cplx), _dev_ptr(X, cplx), A.stride(0), X.stride(0)
+        d = PrecondDesc(n=n, A=a_ptr, lda=lda, X=x_ptr, ldx=ldx, loops=loops, alpha=alpha, chop=chop,
+                        prec=PREC[prec], complex_matrix=1 if cplx else 0, host_buffers=1 if host else 0,
+                        profile=1 if profile else 0)
+        info = Info()
+        st = 0 if host and stream is None else _stream_ptr(stream)
+        rc = self._lib.pinv_preconditioner(self._h, C.byref(d), C.c_void_p(st), C.byref(info))
+        if rc != PINV_OK and raise_on_error:
+            raise PinvError(rc, "pinv_preconditioner")
         return X, info.to_dict()
 
     def solve_batched(self, As, Xs=None, *, stream=None, **kw):

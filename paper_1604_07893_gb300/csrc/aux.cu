@@ -275,6 +275,47 @@ __global__ void complex_col_abs_max_kernel(int m, int n, const double* E, int ld
     if (threadIdx.x == 0) part[blockIdx.x] = best;
 }
 
+// X0 = alpha diag(1/a_11, ..., 1/a_nn) (Eq. choice3) into X, zeroed by the
+// caller.  cplx: A and X are embeddings (2n x 2n) of complex n x n matrices,
+// a_i = E[i][i] + i E[n+i][i] and 1/a_i = conj(a_i)/|a_i|^2.  One CTA;
+// out[0] = the number of zero diagonal entries (left unwritten in X).
+__global__ void jacobi_x0_kernel(int n, const double* A, int lda, double alpha, double* X, int ldx, int cplx,
+                                 double* out) {
+    __shared__ int zeros;
+    if (threadIdx.x == 0) zeros = 0;
+    __syncthreads();
+    int local = 0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        if (!cplx) {
+            const double a = A[(size_t)i * lda + i];
+            if (a == 0.0) { ++local; continue; }
+            X[(size_t)i * ldx + i] = alpha / a;
+        } else {
+            const double re = A[(size_t)i * lda + i], im = A[(size_t)(i + n) * lda + i];
+            const double d = re * re + im * im;
+            if (d == 0.0) { ++local; continue; }
+            const double xr = alpha * re / d, xi = -alpha * im / d;
+            X[(size_t)i * ldx + i] = xr;
+            X[(size_t)i * ldx + n + i] = -xi;
+            X[(size_t)(i + n) * ldx + i] = xi;
+            X[(size_t)(i + n) * ldx + n + i] = xr;
+        }
+    }
+    if (local) atomicAdd(&zeros, local);
+    __syncthreads();
+    if (threadIdx.x == 0) out[0] = (double)zeros;
+}
+
+// Entries of magnitude below eps set to 0 (on an embedding each entry is one
+// real or imaginary part, so complex parts are chopped separately).
+__global__ void chop_kernel(int rows, int cols, double* X, int ld, double eps) {
+    const size_t total = (size_t)rows * cols;
+    for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < total; e += (size_t)gridDim.x * blockDim.x) {
+        double* p = X + (e / cols) * ld + e % cols;
+        if (fabs(*p) < eps) *p = 0.0;
+    }
+}
+
 }  // namespace
 
 void fill_pattern(int rows, int cols, double* X, int ld, unsigned seed, cudaStream_t st) {
@@ -372,6 +413,15 @@ void complex_extract(int r, int c, const double* E, int lde, double* Z, int ldz,
 
 void embed_mirror(int M, int N2, double* E, int ld, cudaStream_t st) {
     embed_mirror_kernel<<<grid_for((size_t)(M / 2) * N2), 256, 0, st>>>(M, N2, E, ld);
+}
+
+void jacobi_x0(int n, const double* A, int lda, double alpha, double* X, int ldx, bool cplx, double* out,
+               cudaStream_t st) {
+    jacobi_x0_kernel<<<1, 256, 0, st>>>(n, A, lda, alpha, X, ldx, cplx ? 1 : 0, out);
+}
+
+void chop(int rows, int cols, double* X, int ld, double eps, cudaStream_t st) {
+    chop_kernel<<<grid_for((size_t)rows * cols), 256, 0, st>>>(rows, cols, X, ld, eps);
 }
 
 void complex_norms_1_inf(int m, int n, const double* E, int lde, double* out, double* scratch, cudaStream_t st) {

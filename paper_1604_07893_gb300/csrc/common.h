@@ -86,6 +86,14 @@ void embed_mirror(int M, int N2, double* E, int ld, cudaStream_t st);
 // out[0] = ||Z||_1, out[1] = ||Z||_inf with complex moduli, Z m x n read from E(Z).
 void complex_norms_1_inf(int m, int n, const double* E, int lde, double* out, double* scratch, cudaStream_t st);
 
+// X0 = alpha diag(1/a_ii) (Eq. choice3) into X (zero elsewhere already); with
+// cplx, A and X are 2n x 2n embeddings of complex n x n matrices.
+// out[0] (device) = the number of zero diagonal entries.
+void jacobi_x0(int n, const double* A, int lda, double alpha, double* X, int ldx, bool cplx, double* out,
+               cudaStream_t st);
+// X[i][j] = 0 where |X[i][j]| < eps.
+void chop(int rows, int cols, double* X, int ld, double eps, cudaStream_t st);
+
 // X[i][j] = a deterministic pseudo-random value in (-1, 1) from (i, j, seed).
 void fill_pattern(int rows, int cols, double* X, int ld, unsigned seed, cudaStream_t st);
 

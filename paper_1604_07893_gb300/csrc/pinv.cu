@@ -921,6 +921,105 @@ int replay_loop(Ctx& c, int cur, bool stab, double* dx2, double* x2) {
     return PINV_OK;
 }
 
+// The result Xfinal to the caller's X (device or host, real or complex; `spare`
+// is a free iterate buffer for staging), then the call's counters into info.
+int copy_out(Ctx& c, const pinv_desc* d, const double* Xfinal, double* spare, pinv_info* info,
+             std::chrono::steady_clock::time_point t0) {
+    cudaStream_t st = c.st;
+    if (c.cplx) {   // X (n x m complex) from the left half of E(X)
+        if (d->host_buffers) {
+            complex_extract(d->n, d->m, Xfinal, c.m, spare, d->m, st);
+            CK(cudaMemcpy2DAsync(d->X, 2 * sizeof(double) * d->ldx, spare, 2 * sizeof(double) * d->m,
+                                 2 * sizeof(double) * d->m, d->n, cudaMemcpyDeviceToHost, st));
+        } else {
+            complex_extract(d->n, d->m, Xfinal, c.m, d->X, d->ldx, st);
+        }
+        ++c.kernels;
+    } else if (d->host_buffers) {
+        CK(cudaMemcpy2DAsync(d->X, sizeof(double) * d->ldx, Xfinal, sizeof(double) * c.m,
+                             sizeof(double) * c.m, c.n, cudaMemcpyDeviceToHost, st));
+    } else {
+        CK(cudaMemcpy2DAsync(d->X, sizeof(double) * d->ldx, Xfinal, sizeof(double) * c.m,
+                             sizeof(double) * c.m, c.n, cudaMemcpyDeviceToDevice, st));
+    }
+    CK(cudaStreamSynchronize(st));
+    CK(cudaGetLastError());
+    prof_harvest(c);
+    info->gemms = c.gemms;
+    info->kernels = c.kernels;
+    info->gemm_ms = c.gemm_ms;
+    info->gemm_flops = c.gemm_flops;
+    info->tensor_flops = c.tensor_flops;
+    info->ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return PINV_OK;
+}
+
+// Approximate-inverse preconditioner (Section 8, Example 3): `loops` loops of
+// Eq. PM from the Jacobi X0 = alpha diag(1/a_ii) (Eq. choice3), each followed
+// by the chop when chop > 0.  No stop rule: the loop count is the request.
+int precond_one(pinv_handle* h, const pinv_precond_desc* p, cudaStream_t st, pinv_info* info) {
+    auto t0 = std::chrono::steady_clock::now();
+    std::memset(info, 0, sizeof(*info));
+    if (!p || p->n < 1 || !p->A || !p->X || p->lda < p->n || p->ldx < p->n || p->loops < 1 ||
+        p->loops > PINV_HISTORY || !(p->alpha >= 0.0) || !std::isfinite(p->alpha) || !(p->chop >= 0.0) ||
+        !std::isfinite(p->chop))
+        return info->status = PINV_ERR_ARG;
+    int level;
+    switch (p->prec) {
+        case PINV_PREC_FP64: level = 0; break;
+        case PINV_PREC_FP64_TC: level = TC_FP64; break;
+        case PINV_PREC_FP32: level = TC_FP32; break;
+        case PINV_PREC_MIXED_BF16:
+        case PINV_PREC_BF16_FP32: level = TC_BF16; break;
+        default: return info->status = PINV_ERR_ARG;
+    }
+    pinv_desc d{};
+    d.m = d.n = p->n;
+    d.A = p->A;
+    d.lda = p->lda;
+    d.X = p->X;
+    d.ldx = p->ldx;
+    d.kind = PINV_MOORE_PENROSE;   // no G to stage
+    d.prec = p->prec == PINV_PREC_FP64 ? PINV_PREC_FP64 : PINV_PREC_FP64_TC;   // workspace for any class
+    d.host_buffers = p->host_buffers;
+    Ctx c{};
+    c.profile = p->profile != 0;
+    const bool cplx = p->complex_matrix != 0;
+    int rc = setup_context(h, &d, st, c, cplx);
+    if (rc) return info->status = rc;
+    const int n = c.n;   // 2 p->n for a complex matrix
+    CK(cudaMemsetAsync(c.X[0], 0, sizeof(double) * (size_t)n * n, st));
+    jacobi_x0(p->n, c.A, c.lda, p->alpha > 0 ? p->alpha : 1.0, c.X[0], n, cplx, h->dsmall, st);
+    ++c.kernels;
+    CK(cudaMemcpyAsync(h->pinned, h->dsmall, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (h->pinned[0] != 0.0) return info->status = PINV_ERR_ARG;   // a zero diagonal entry
+    info->alpha = p->alpha > 0 ? p->alpha : 1.0;
+    c.prec_k = level;
+    int cur = 0;
+    for (int k = 0; k < p->loops; ++k) {
+        const int parts = pm_loop_f64(c, c.X[cur], c.X[cur ^ 1]);
+        if (parts < 0) return info->status = PINV_ERR_CUDA;
+        if (p->chop > 0) {
+            chop(n, n, c.X[cur ^ 1], n, p->chop, st);
+            ++c.kernels;
+        }
+        double dx2, x2;
+        rc = read_norms(c, parts, &dx2, &x2);
+        if (rc) return info->status = rc;
+        const double e = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
+        info->history[k] = e;
+        info->precision[k] = (signed char)level;
+        info->loops_run = info->iters = k + 1;
+        info->rel_step = e;
+        cur ^= 1;
+        if (!std::isfinite(e)) return info->status = PINV_ERR_NONFINITE;
+    }
+    info->side = c.left ? 1 : 0;
+    rc = copy_out(c, &d, c.X[cur], c.X[cur ^ 1], info, t0);
+    return info->status = rc;
+}
+
 int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* info, bool cplx = false) {
     auto t0 = std::chrono::steady_clock::now();
     std::memset(info, 0, sizeof(*info));
@@ -1045,33 +1144,8 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         rc = residual_checks(c, d, Xfinal, info);
         if (rc) return info->status = rc;
     }
-    if (c.cplx) {   // X (n x m complex) from the left half of E(X)
-        if (d->host_buffers) {
-            double* Z = c.X[cur ^ 1];
-            complex_extract(d->n, d->m, Xfinal, c.m, Z, d->m, st);
-            CK(cudaMemcpy2DAsync(d->X, 2 * sizeof(double) * d->ldx, Z, 2 * sizeof(double) * d->m,
-                                 2 * sizeof(double) * d->m, d->n, cudaMemcpyDeviceToHost, st));
-        } else {
-            complex_extract(d->n, d->m, Xfinal, c.m, d->X, d->ldx, st);
-        }
-        ++c.kernels;
-    } else if (d->host_buffers) {
-        CK(cudaMemcpy2DAsync(d->X, sizeof(double) * d->ldx, Xfinal, sizeof(double) * c.m,
-                             sizeof(double) * c.m, c.n, cudaMemcpyDeviceToHost, st));
-    } else {
-        CK(cudaMemcpy2DAsync(d->X, sizeof(double) * d->ldx, Xfinal, sizeof(double) * c.m,
-                             sizeof(double) * c.m, c.n, cudaMemcpyDeviceToDevice, st));
-    }
-    CK(cudaStreamSynchronize(st));
-    CK(cudaGetLastError());
-    prof_harvest(c);
-    info->gemms = c.gemms;
-    info->kernels = c.kernels;
-    info->gemm_ms = c.gemm_ms;
-    info->gemm_flops = c.gemm_flops;
-    info->tensor_flops = c.tensor_flops;
-    info->ms = std::chrono::duration<float, std::milli>(std::chrono::steady_clock::now() - t0).count();
-    return info->status = status;
+    rc = copy_out(c, d, Xfinal, c.X[cur ^ 1], info, t0);
+    return info->status = rc ? rc : status;
 }
 
 
@@ -1665,6 +1739,14 @@ int pinv_solve(pinv_handle* h, const pinv_desc* desc, void* stream, pinv_info* i
     pinv_info* out = info ? info : &local;
     if (cudaSetDevice(h->device) != cudaSuccess) return out->status = PINV_ERR_CUDA;
     return solve_one(h, desc, (cudaStream_t)stream, out);
+}
+
+int pinv_preconditioner(pinv_handle* h, const pinv_precond_desc* desc, void* stream, pinv_info* info) {
+    if (!h) return PINV_ERR_ARG;
+    pinv_info local;
+    pinv_info* out = info ? info : &local;
+    if (cudaSetDevice(h->device) != cudaSuccess) return out->status = PINV_ERR_CUDA;
+    return precond_one(h, desc, (cudaStream_t)stream, out);
 }
 
 int pinv_solve_complex(pinv_handle* h, const pinv_desc* desc, void* stream, pinv_info* info) {

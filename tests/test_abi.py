@@ -38,7 +38,8 @@ def test_struct_sizes_match_the_header():
     src = r'''
 #include <stdio.h>
 #include "pinv.h"
-int main(void) { printf("%zu %zu %zu\n", sizeof(pinv_config), sizeof(pinv_desc), sizeof(pinv_info)); return 0; }
+int main(void) { printf("%zu %zu %zu %zu\n", sizeof(pinv_config), sizeof(pinv_desc), sizeof(pinv_info),
+                        sizeof(pinv_precond_desc)); return 0; }
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "s.c")
@@ -47,4 +48,4 @@ int main(void) { printf("%zu %zu %zu\n", sizeof(pinv_config), sizeof(pinv_desc),
         subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     assert [int(x) for x in out] == [ctypes.sizeof(_lib.Config), ctypes.sizeof(_lib.Desc),
-                                     ctypes.sizeof(_lib.Info)]
+                                     ctypes.sizeof(_lib.Info), ctypes.sizeof(_lib.PrecondDesc)]
