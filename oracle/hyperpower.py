@@ -264,6 +264,22 @@ def alpha_rectangular(A: np.ndarray) -> float:
     return 1.0 / (n1 * ninf)
 
 
+def alpha_general(A: np.ndarray, G: np.ndarray) -> float:
+    """alpha = 1 / sqrt(||P||_1 ||P||_inf) for X0 = alpha G, P the smaller of GA
+    (n x n, when m > n) and AG (m x m): both have the nonzero eigenvalues of GA
+    that Section 4's alpha = 2/(lambda_1 + lambda_r) refers to, and the
+    spectral radius is at most min(||P||_1, ||P||_inf), so alpha lambda <= 1 for
+    every eigenvalue -- inside Theorem 3.1's region when the spectrum of GA is
+    real and nonnegative (G = A^*, G = I for A positive definite, weighted
+    Moore-Penrose and Bott-Duffin choices).  Reading for general G; Section 4
+    gives the Moore-Penrose recipe only."""
+    m, n = A.shape
+    P = G @ A if m > n else A @ G
+    n1 = float(np.abs(P).sum(axis=0).max())
+    ninf = float(np.abs(P).sum(axis=1).max())
+    return 1.0 / math.sqrt(n1 * ninf)
+
+
 # ----------------------------------------------------------------------------
 # cleanup projections (build-introduced; motivated by Theorems 6.2 and 7.1)
 # ----------------------------------------------------------------------------

@@ -18,6 +18,9 @@ ill-conditioned Moore-Penrose problems and preconditioning of a large matrix):
 * ``uneven_batch`` many independent rectangular problems of random shape.
 * ``poisson_arrivals`` request arrival times for the serving workload.
 * ``hilbert``      H_ij = 1/(i+j-1) (Section 8 Example 2).
+* ``subspace_projector`` and ``spd``/``hpd_complex`` weights: the G of the
+  weighted Moore-Penrose (G = N^{-1} A^* M) and Bott-Duffin (G = P_L)
+  inverses, outer inverses Section 1.1 lists among the A^(2)_{T,S}.
 * ``grid_operator``: a shifted five-point operator on a k x k grid, real or
   complex (the sparse-system stand-in for the preconditioning example of
   Section 8, whose MatrixMarket matrix is not used).
@@ -331,3 +334,12 @@ def grid_operator(k: int, shift: complex = 0.5 + 0.5j, jitter: float = 0.05, see
                 if 0 <= ii < k and 0 <= jj < k:
                     A[i * k + j, ii * k + jj] = -1.0 * (1.0 + jitter * g(1)[0])
     return A
+
+
+def subspace_projector(n: int, k: int, seed: int = 13, complex_: bool = False):
+    """Orthogonal projector P_L = Q Q^* onto a Haar-random k-dimensional subspace
+    L of R^n (C^n when complex_); returns (P_L, Q)."""
+    rng = np.random.default_rng(seed)
+    Q = haar_unitary(rng, n, k) if complex_ else haar_orthogonal(rng, n, k)
+    P = Q @ Q.conj().T
+    return np.ascontiguousarray(P), Q

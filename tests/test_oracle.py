@@ -626,3 +626,59 @@ def test_chopped_preconditioner_stays_close_and_sparse():
     diff = Xc - X1
     assert np.abs(diff.real).max() < 1e-5 and np.abs(diff.imag).max() < 1e-5
     assert np.array_equal(Xc, H.chop(X1, 1e-5))
+
+
+# --------------------------------------------------------------------------
+# outer inverses through G (Section 1.1): weighted Moore-Penrose, Bott-Duffin;
+# the alpha of a general G
+# --------------------------------------------------------------------------
+
+def _sqrtm_spd(s, power):
+    return (s.Q * s.lam ** power) @ s.Q.conj().T
+
+
+@pytest.mark.parametrize("complex_", [False, True])
+def test_weighted_moore_penrose_through_g(complex_):
+    """A^+_{MN} = A^(2)_{R(N^{-1}A^*M), N(N^{-1}A^*M)}: X0 = alpha N^{-1} A^* M.
+    Pinned to the closed form N^{-1/2} (M^{1/2} A N^{-1/2})^+ M^{1/2} and to the
+    four weighted Penrose equations AXA = A, XAX = X, (MAX)^* = MAX, (NXA)^* = NXA."""
+    if complex_:
+        w = W.rectangular_complex(30, 20, 14, 1.0, 1e-2, seed=31)
+        Ms, Ns = W.hpd_complex(30, 0.2, 5.0, seed=32), W.hpd_complex(20, 0.5, 2.0, seed=33)
+    else:
+        w = W.rectangular(30, 20, 14, 1.0, 1e-2, seed=31)
+        Ms, Ns = W.spd(30, 0.2, 5.0, seed=32), W.spd(20, 0.5, 2.0, seed=33)
+    A, M, N = w.A, Ms.A, Ns.A
+    G = _sqrtm_spd(Ns, -1.0) @ H.ct(A) @ M
+    a = H.alpha_general(A, G)
+    X, info = H.solve(A, H.x0_general(G, a), tol=1e-13, alpha=a, finish=None)
+    ref = _sqrtm_spd(Ns, -0.5) @ np.linalg.pinv(_sqrtm_spd(Ms, 0.5) @ A @ _sqrtm_spd(Ns, -0.5)) @ _sqrtm_spd(Ms, 0.5)
+    assert rel(X, ref) < 1e-10
+    assert rel(A @ X @ A, A) < 1e-10 and rel(X @ A @ X, X) < 1e-10
+    MAX, NXA = M @ A @ X, N @ X @ A
+    assert rel(H.ct(MAX), MAX) < 1e-10 and rel(H.ct(NXA), NXA) < 1e-10
+    # and it is not the plain pseudoinverse
+    assert rel(ref, np.linalg.pinv(A)) > 1e-3
+
+
+def test_bott_duffin_inverse_through_g():
+    """A^{(-1)}_{(L)} = P_L (A P_L + P_{L^perp})^{-1} = A^(2)_{L, L^perp} for A
+    positive definite: X0 = alpha P_L."""
+    s = W.spd(40, 0.05, 1.0, seed=34)
+    P, Q = W.subspace_projector(40, 25, seed=35)
+    a = H.alpha_general(s.A, P)
+    X, info = H.solve(s.A, H.x0_general(P, a), tol=1e-13, alpha=a)
+    ref = P @ np.linalg.inv(s.A @ P + (np.eye(40) - P))
+    assert rel(X, ref) < 1e-11
+    assert rel(P @ X, X) < 1e-11 and rel(X @ P, X) < 1e-11
+    # on L it inverts the compression Q^T A Q
+    assert rel(Q.T @ X @ Q, np.linalg.inv(Q.T @ s.A @ Q)) < 1e-11
+
+
+def test_general_alpha_bounds_the_spectrum_of_ga():
+    w = W.rectangular(50, 30, None, 1.0, 1e-2, seed=36)
+    for A, G in ((w.A, w.A.T), (w.A.T.copy(), w.A.copy()), (W.spd(30, 1e-3, 1.0, seed=37).A, np.eye(30))):
+        a = H.alpha_general(A, G)
+        lam = np.linalg.eigvals(G @ A)
+        assert a * np.abs(lam).max() <= 1.0 + 1e-12
+        assert a * np.abs(lam).max() > 0.1   # not needlessly small on these families
