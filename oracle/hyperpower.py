@@ -291,6 +291,15 @@ def cleanup_moore_penrose(A: np.ndarray, X: np.ndarray) -> np.ndarray:
     return ct(X @ A) @ X @ ct(A @ X)
 
 
+def cleanup_outer(A: np.ndarray, X: np.ndarray) -> np.ndarray:
+    """X <- X A X for a general outer inverse A^(2)_{T,S} (the product Section 7
+    appends to each loop): it fixes every outer inverse (XAX = X defines them,
+    Eq. 1) and removes the first-order error components outside R(X) on the left
+    and N(X) on the right.  The Moore-Penrose projection above would move a
+    non-Moore-Penrose outer inverse (e.g. a weighted one) away from itself."""
+    return X @ A @ X
+
+
 def cleanup_drazin(A: np.ndarray, X: np.ndarray, l: int) -> np.ndarray:
     """X <- A^l X^{2l+1} A^l; fixes A^D (A^D = A^l (A^D)^{2l+1} A^l) and
     projects an approximate Drazin inverse back onto R(A^l), N(A^l)."""
@@ -385,8 +394,9 @@ def solve(A: np.ndarray, X0: np.ndarray, tol: float = 1e-12, stop: int = STOP_RE
       step no longer decreases, e_k >= e_{k-1}; keep X_k, status 'minimum'.
     * Stabilised variant: loops after the first one with e < switch_tol use
       the extra X A X (the Pan-Schreiber switch closing Section 7).
-    * ``finish`` ('moore_penrose' or 'drazin'): after the loop ends, apply the
-      cleanup projection and one order-2 step of the hyperpower family
+    * ``finish`` ('moore_penrose', 'drazin' or 'outer' for a general G): after
+      the loop ends, apply the cleanup projection and one order-2 step of the
+      hyperpower family
       (X <- X(I + R), R = I - AX).  The projection removes the blocks Theorem
       6.2 shows are not contracted (E12, E21 persist, E22 grows); its own
       rounding error is first order, which one order-2 step squares.
@@ -399,6 +409,8 @@ def solve(A: np.ndarray, X0: np.ndarray, tol: float = 1e-12, stop: int = STOP_RE
             Xc = cleanup_moore_penrose(A, X)
         elif finish == "drazin":
             Xc = cleanup_drazin(A, X, drazin_index)
+        elif finish == "outer":
+            Xc = cleanup_outer(A, X)
         else:
             raise ValueError(finish)
         X = hyperpower_step(A, Xc, 2, side or choose_side(*A.shape))

@@ -652,7 +652,8 @@ def test_weighted_moore_penrose_through_g(complex_):
     G = _sqrtm_spd(Ns, -1.0) @ H.ct(A) @ M
     a = H.alpha_general(A, G)
     X, info = H.solve(A, H.x0_general(G, a), tol=1e-13, alpha=a, finish=None)
-    ref = _sqrtm_spd(Ns, -0.5) @ np.linalg.pinv(_sqrtm_spd(Ms, 0.5) @ A @ _sqrtm_spd(Ns, -0.5)) @ _sqrtm_spd(Ms, 0.5)
+    ref = (_sqrtm_spd(Ns, -0.5) @ np.linalg.pinv(_sqrtm_spd(Ms, 0.5) @ A @ _sqrtm_spd(Ns, -0.5), rcond=1e-10)
+           @ _sqrtm_spd(Ms, 0.5))
     assert rel(X, ref) < 1e-10
     assert rel(A @ X @ A, A) < 1e-10 and rel(X @ A @ X, X) < 1e-10
     MAX, NXA = M @ A @ X, N @ X @ A
@@ -682,3 +683,22 @@ def test_general_alpha_bounds_the_spectrum_of_ga():
         lam = np.linalg.eigvals(G @ A)
         assert a * np.abs(lam).max() <= 1.0 + 1e-12
         assert a * np.abs(lam).max() > 0.1   # not needlessly small on these families
+
+
+@pytest.mark.parametrize("m,n", [(300, 200), (200, 300)])
+def test_outer_finish_keeps_a_weighted_inverse_and_sharpens_it(m, n):
+    """Rank-deficient weighted Moore-Penrose: the plain loop ends near 1e-9
+    (Theorem 6.2's persistent blocks); X A X removes them (1e-12), while the
+    Moore-Penrose projection (XA)^T X (AX)^T would land far from A^+_{MN}."""
+    w = W.rectangular(m, n, 150, 1.0, 1e-3, seed=31)
+    Ms, Ns = W.spd(m, 0.2, 5.0, seed=32), W.spd(n, 0.5, 2.0, seed=33)
+    A = w.A
+    G = _sqrtm_spd(Ns, -1.0) @ A.T @ Ms.A
+    ref = (_sqrtm_spd(Ns, -0.5) @ np.linalg.pinv(_sqrtm_spd(Ms, 0.5) @ A @ _sqrtm_spd(Ns, -0.5), rcond=1e-10)
+           @ _sqrtm_spd(Ms, 0.5))
+    a = H.alpha_general(A, G)
+    X, _ = H.solve(A, H.x0_general(G, a), tol=1e-12, alpha=a)
+    Xf, info = H.solve(A, H.x0_general(G, a), tol=1e-12, alpha=a, finish="outer")
+    assert info.finished
+    assert rel(X, ref) > 1e-10 and rel(Xf, ref) < 3e-12
+    assert rel(H.cleanup_moore_penrose(A, X), ref) > 0.1
