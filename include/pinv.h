@@ -59,7 +59,10 @@ extern "C" {
 typedef enum {
     PINV_MOORE_PENROSE = 0,  /* G = A^T (Section 4; Theorem 6.2)                  */
     PINV_DRAZIN        = 1,  /* G = A^l, l = drazin_index >= ind(A) (Section 4)   */
-    PINV_OUTER_G       = 2,  /* caller's G (n x m): A^(2)_{R(G),N(G)} (Thm 3.1)   */
+    PINV_OUTER_G       = 2,  /* caller's G (n x m): A^(2)_{R(G),N(G)} (Thm 3.1), e.g.
+                                the weighted Moore-Penrose inverse A^+_{MN}
+                                (G = N^{-1} A^T M) or the Bott-Duffin inverse
+                                (G = P_L) of Section 1.1                          */
     PINV_DRAZIN_NORMAL = 3   /* Drazin inverse from G = A^l (A^{2l+1})^T A^l: same
                                 range and null space as A^D, GA has a real
                                 nonnegative spectrum, so it converges whatever the
@@ -106,7 +109,8 @@ typedef enum {
 typedef enum {
     PINV_FINISH_NONE  = 0,
     PINV_FINISH_CLEAN = 1    /* after the loops: projection X <- (XA)^T X (AX)^T
-                                (Moore-Penrose) or A^l X^{2l+1} A^l (Drazin),
+                                (Moore-Penrose), A^l X^{2l+1} A^l (Drazin) or
+                                X A X (general G: fixes any outer inverse),
                                 then one FP64-class order-2 step of the same
                                 family, X <- X + (I - XA) X (Eq. hyper, p = 2),
                                 which squares the projection's rounding (after
@@ -130,8 +134,15 @@ typedef struct {
     pinv_kind    kind;
     int          drazin_index;  /* l >= ind(A), required for PINV_DRAZIN            */
     double       alpha;      /* > 0: X0 = alpha * G.  0: the Section 4 recipe:
-                                1/(||A||_1 ||A||_inf) for MOORE_PENROSE/OUTER_G,
-                                1/Tr(A^{l+1}) for DRAZIN                             */
+                                1/(||A||_1 ||A||_inf) for MOORE_PENROSE,
+                                1/Tr(A^{l+1}) for DRAZIN; for OUTER_G
+                                1/sqrt(||P||_1 ||P||_inf), P = GA (m > n) or AG,
+                                which bounds the spectral radius of GA and so
+                                converges whenever GA has a real nonnegative
+                                spectrum (weighted Moore-Penrose G = N^{-1}A^T M,
+                                Bott-Duffin G = P_L with A positive definite,
+                                G = I with A positive definite); one extra
+                                product                                           */
     double       tol;        /* stop tolerance for `stop`                            */
     pinv_stop    stop;
     int          max_iter;   /* 0 = the paper's 100 (Section 8)                      */

@@ -398,8 +398,8 @@ int stabilise_f64(Ctx& c, const double* Xh, const double* Xprev, double* Xout) {
     return gemm(c, n, m, s, Xh, m, false, P, s, false, e);
 }
 
-// Projection of the finish step: (XA)^T X (AX)^T (Moore-Penrose) or
-// A^l X^{2l+1} A^l (Drazin).  Xin -> Xout.
+// Projection of the finish step: (XA)^T X (AX)^T (Moore-Penrose),
+// A^l X^{2l+1} A^l (Drazin) or X A X (general G).  Xin -> Xout.
 void cleanup_f64(Ctx& c, const pinv_desc* d, const double* X, double* Xout) {
     const int s = c.s, m = c.m, n = c.n;
     if (d->kind == PINV_DRAZIN || d->kind == PINV_DRAZIN_NORMAL) {
@@ -414,6 +414,21 @@ void cleanup_f64(Ctx& c, const pinv_desc* d, const double* X, double* Xout) {
         }
         gemm(c, n, n, n, c.Al, n, false, V[cur], n, false, epi1(term(V[cur ^ 1], n, 1)));
         gemm(c, n, n, n, V[cur ^ 1], n, false, c.Al, n, false, epi1(term(Xout, m, 1)));
+        return;
+    }
+    if (d->kind == PINV_OUTER_G) {
+        // X' = X A X: XAX = X defines every outer inverse (Eq. 1), so it fixes
+        // A^(2)_{T,S} for any G and removes the error components outside R(X)
+        // (left) and N(X) (right); the Moore-Penrose projection below would move
+        // a non-Moore-Penrose outer inverse (e.g. a weighted one) off itself.
+        double* P = c.sq[5];
+        if (c.left) {   // P = XA (n x n), X' = P X
+            gemm(c, n, n, m, X, m, false, c.A, c.lda, false, epi1(term(P, n, 1)));
+            gemm(c, n, m, n, P, n, false, X, m, false, epi1(term(Xout, m, 1)));
+        } else {        // Q = AX (m x m), X' = X Q
+            gemm(c, m, m, n, c.A, c.lda, false, X, m, false, epi1(term(P, m, 1)));
+            gemm(c, n, m, m, X, m, false, P, m, false, epi1(term(Xout, m, 1)));
+        }
         return;
     }
     // X' = P^T X Q^T with P = XA (n x n) and Q = AX (m x m): both factors are
@@ -651,23 +666,36 @@ int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
         scale_copy(n, n, c.Al, n, a, c.X[0], m, c.st);
         ++c.kernels;
     } else {
-        if (a == 0.0) {  // 1 / (||A||_1 ||A||_inf), with complex moduli for complex A
-            if (c.cplx) complex_norms_1_inf(m / 2, n / 2, c.A, c.lda, c.h->dsmall, c.red, c.st);
-            else        norms_1_inf(m, n, c.A, c.lda, c.h->dsmall, c.red, c.st);
+        const bool own_g = d->host_buffers || c.cplx;
+        const double* G = own_g ? c.Gd : d->G;
+        const int ldg = own_g ? m : d->ldg;
+        if (a == 0.0) {
+            // Moore-Penrose: 1 / (||A||_1 ||A||_inf) (Section 4).  General G:
+            // 1 / sqrt(||P||_1 ||P||_inf), P = GA (left side) or AG, the smaller
+            // square with the nonzero eigenvalues of GA, whose spectral radius
+            // it bounds.  Complex moduli for complex matrices.
+            const double* N1 = c.A;
+            int r = m, cols = n, ld = c.lda;
+            if (d->kind == PINV_OUTER_G) {
+                double* P = c.sq[0];
+                if (c.left) gemm(c, n, n, m, G, ldg, false, c.A, c.lda, false, epi1(term(P, n, 1)));
+                else        gemm(c, m, m, n, c.A, c.lda, false, G, ldg, false, epi1(term(P, m, 1)));
+                N1 = P;
+                r = cols = ld = c.s;
+            }
+            if (c.cplx) complex_norms_1_inf(r / 2, cols / 2, N1, ld, c.h->dsmall, c.red, c.st);
+            else        norms_1_inf(r, cols, N1, ld, c.h->dsmall, c.red, c.st);
             c.kernels += 4;
             CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
             CK(cudaStreamSynchronize(c.st));
             const double p = c.h->pinned[0] * c.h->pinned[1];
             if (!(p > 0.0) || !std::isfinite(p)) return PINV_ERR_NONFINITE;
-            a = 1.0 / p;
+            a = d->kind == PINV_OUTER_G ? 1.0 / std::sqrt(p) : 1.0 / p;
         }
         if (d->kind == PINV_MOORE_PENROSE) {
             transpose_scale(m, n, c.A, c.lda, a, c.X[0], m, c.st);
             ++c.kernels;
         } else {
-            const bool own_g = d->host_buffers || c.cplx;
-            const double* G = own_g ? c.Gd : d->G;
-            const int ldg = own_g ? m : d->ldg;
             scale_copy(n, m, G, ldg, a, c.X[0], m, c.st);
             ++c.kernels;
         }
@@ -1333,14 +1361,31 @@ int group_begin_impl(Group& G) {
     CK(cudaMemcpyAsync(G.tabG, tg.data(), sizeof(InstanceRef) * G.batch, cudaMemcpyHostToDevice, G.st));
     gather_pad(G.tabA, G.batch, G.M, G.N, c.Ad, slab, G.st);
     if (gk) gather_pad(G.tabG, G.batch, G.N, G.M, c.Gd, slab, G.st);
-    // alpha = 0: the Section 4 recipe per instance (norms on the padded slab are the instance's)
+    // alpha = 0: the recipe of a lone solve per instance (norms on the padded
+    // slab are the instance's: zero padding adds zero rows and columns)
     for (int b = 0; b < G.batch; ++b) {
         if (alpha[b] == 0.0) {
-            norms_1_inf(G.M, G.N, c.Ad + b * slab, G.N, h->dsmall, c.red, G.st);
+            if (gk) {
+                // P = GA or AG, chosen by the instance's own shape as a lone
+                // solve does (padding can make the group's side differ when
+                // the padded shape is square); one unbatched FP64 product into
+                // the instance's s x s square, which fits either choice
+                double* P = c.sq[0] + b * slab;
+                const double* Ab = c.Ad + b * slab;
+                const double* Gb = c.Gd + b * slab;
+                const int keep = c.batch;
+                c.batch = 1;
+                if (G.d[b].m > G.d[b].n) gemm(c, G.N, G.N, G.M, Gb, G.M, false, Ab, G.N, false, epi1(term(P, c.s, 1)));
+                else                     gemm(c, G.M, G.M, G.N, Ab, G.N, false, Gb, G.M, false, epi1(term(P, c.s, 1)));
+                c.batch = keep;
+                norms_1_inf(c.s, c.s, P, c.s, h->dsmall, c.red, G.st);
+            } else {
+                norms_1_inf(G.M, G.N, c.Ad + b * slab, G.N, h->dsmall, c.red, G.st);
+            }
             CK(cudaMemcpyAsync(G.pinned, h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, G.st));
             CK(cudaStreamSynchronize(G.st));
             const double pr = G.pinned[0] * G.pinned[1];
-            alpha[b] = (pr > 0 && std::isfinite(pr)) ? 1.0 / pr : 1.0;
+            alpha[b] = (pr > 0 && std::isfinite(pr)) ? (gk ? 1.0 / std::sqrt(pr) : 1.0 / pr) : 1.0;
         }
         G.info[b].alpha = alpha[b];
         G.info[b].side = G.left ? 1 : 0;
