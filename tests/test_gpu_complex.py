@@ -160,3 +160,30 @@ def test_complex_rejects_the_symmetric_hint(handle):
     G = dev(np.eye(32, dtype=np.complex128))
     with pytest.raises(PinvError):
         handle.solve_complex(dev(s.A), kind="outer_g", G=G, alpha=1.0, symmetric=True)
+
+
+@pytest.mark.parametrize("m,n,prec", [(129, 257, "fp64"), (257, 129, "fp64_tc"), (1, 1, "fp64"), (3, 7, "fp64_tc")])
+def test_complex_ragged_and_both_sides(handle, m, n, prec):
+    """Odd sizes (ragged tiles on the 2m x 2n embedding, half-width products of
+    odd width), the right residual side (m < n) and the 1 x 1 case."""
+    r = min(m, n)
+    w = W.rectangular_complex(m, n, r, 1.0, 1e-2, seed=m + 7 * n)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    ref, oinfo = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+    X, info = handle.solve_complex(dev(w.A), alpha=alpha, tol=1e-12, prec=prec)
+    assert info["status"] == 0
+    assert info["side"] == ("left" if m > n else "right")
+    assert_close(host(X), ref, 1e-12)
+    assert rel(host(X), pinv_closed_form(w)) < 1e-12
+
+
+def test_complex_mixed_precision_full_rank(handle):
+    """BF16 growth loops, FP32-class, then FP64-class on a full-rank complex
+    problem (alpha <= 1/sigma_max^2 as the schedule requires) with the finish."""
+    w = W.rectangular_complex(300, 180, None, 1.0, 1e-3, seed=26)
+    X, info = handle.solve_complex(dev(w.A), alpha=1.0 / w.s[0] ** 2, tol=1e-12, prec="mixed_bf16",
+                                   finish="clean", check=True)
+    assert info["status"] == 0
+    assert 1 in info["precision"] and 3 in info["precision"]
+    assert rel(host(X), pinv_closed_form(w)) < 1e-9
+    assert max(info["penrose"]) < 1e-9
