@@ -187,3 +187,17 @@ def test_complex_mixed_precision_full_rank(handle):
     assert 1 in info["precision"] and 3 in info["precision"]
     assert rel(host(X), pinv_closed_form(w)) < 1e-9
     assert max(info["penrose"]) < 1e-9
+
+
+def test_complex_paper_stop_rule_uses_complex_norms(handle):
+    """Eq. stopreliable measures ||X_{k+1} - X_k||_F / (18^k alpha) with the
+    complex Frobenius norm: each loop's measure equals the oracle's."""
+    w = W.rectangular_complex(48, 36, None, 1.0, 1e-2, seed=27)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    ref, oinfo = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-6, stop=H.STOP_PAPER, alpha=alpha)
+    X, info = handle.solve_complex(dev(w.A), alpha=alpha, tol=1e-6, stop="paper")
+    assert info["iters"] == oinfo.iters
+    for got, want in zip(info["history"], oinfo.history):
+        if want > 1e-9:
+            assert abs(got - want) <= 1e-9 * want
+    assert rel(host(X), ref) < 1e-9

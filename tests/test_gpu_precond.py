@@ -128,3 +128,13 @@ def test_zero_diagonal_is_rejected(handle):
     Z[5, 5] = 0.0
     with pytest.raises(PinvError):
         handle.preconditioner(dev(Z), loops=1)
+
+
+def test_bad_requests_are_rejected_before_any_work(handle):
+    from paper_1604_07893_gb300 import PinvError
+    A = dev(W.grid_operator(6, seed=12, complex_=False))
+    for kw in (dict(loops=0), dict(loops=129), dict(chop=-1.0), dict(alpha=float("nan")), dict(prec="mixed_fp8")):
+        with pytest.raises(PinvError):
+            handle.preconditioner(A, **{"loops": 1, **kw})
+    with pytest.raises(ValueError):
+        handle.preconditioner(dev(np.zeros((4, 5))))
