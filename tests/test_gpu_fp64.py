@@ -403,3 +403,25 @@ def test_device_loop_decisions_match_the_oracle(handle, prec):
     X2, info2 = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, prec=prec, max_iter=2, raise_on_error=False)
     assert oinfo2.status == "maxiter" and info2["status"] == -5 and info2["iters"] == 2
     assert rel(host(X2), ref2) < 1e-12
+
+
+@pytest.mark.parametrize("m,n", [(64, 48), (48, 64), (128, 128), (100, 37), (1, 1)])
+def test_small_device_loop_solves_match_the_oracle(handle, m, n):
+    """Small plain FP64 solves of several shapes (both residual sides, ragged
+    tiles, 1 x 1) run their loop on the device: loop count, per-loop measures
+    and the result agree with the oracle, and a later solve of another matrix of
+    the same shape reuses the cached loop correctly."""
+    w = W.rectangular(m, n, None, 1.0, 1e-2, seed=3 * m + n)
+    alpha = H.alpha_pan_schreiber(w.s[0], w.s[-1])
+    ref, oinfo = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-12, prec="fp64")
+    assert info["status"] == 0 and info["iters"] == oinfo.iters and info["loops_run"] == oinfo.loops_run
+    for got, want in zip(info["history"][:info["loops_run"]], oinfo.history):
+        if want > 1e-9:
+            assert abs(got - want) <= 1e-6 * want
+    assert rel(host(X), ref) < 1e-12
+    w2 = W.rectangular(m, n, None, 1.0, 1e-1, seed=3 * m + n + 1)
+    a2 = H.alpha_pan_schreiber(w2.s[0], w2.s[-1])
+    ref2, _ = H.solve(w2.A, H.x0_moore_penrose(w2.A, a2), tol=1e-12, alpha=a2)
+    X2, _ = handle.solve(dev(w2.A), alpha=a2, tol=1e-12, prec="fp64")
+    assert rel(host(X2), ref2) < 1e-12
