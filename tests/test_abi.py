@@ -49,3 +49,29 @@ int main(void) { printf("%zu %zu %zu %zu\n", sizeof(pinv_config), sizeof(pinv_de
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     assert [int(x) for x in out] == [ctypes.sizeof(_lib.Config), ctypes.sizeof(_lib.Desc),
                                      ctypes.sizeof(_lib.Info), ctypes.sizeof(_lib.PrecondDesc)]
+
+
+def test_every_field_offset_matches_the_header():
+    """offsetof of each field of the public structs, compiled against the header,
+    equals the binding's ctypes layout (a reordered or retyped field that keeps
+    the struct size would otherwise pass the size check)."""
+    import subprocess
+    import tempfile
+    structs = {"pinv_config": _lib.Config, "pinv_desc": _lib.Desc, "pinv_info": _lib.Info,
+               "pinv_precond_desc": _lib.PrecondDesc}
+    lines = []
+    for cname, cls in structs.items():
+        for fname, _ in cls._fields_:
+            lines.append(f'printf("{cname}.{fname} %zu\\n", offsetof({cname}, {fname}));')
+    src = "#include <stdio.h>\n#include <stddef.h>\n#include \"pinv.h\"\nint main(void) {\n" + \
+          "\n".join(lines) + "\nreturn 0; }\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "o.c")
+        exe = os.path.join(d, "o")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split("\n")
+    got = dict(l.split() for l in out if l.strip())
+    for cname, cls in structs.items():
+        for fname, _ in cls._fields_:
+            assert int(got[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
