@@ -142,7 +142,8 @@ typedef struct {
                                 spectrum (weighted Moore-Penrose G = N^{-1}A^T M,
                                 Bott-Duffin G = P_L with A positive definite,
                                 G = I with A positive definite); one extra
-                                product                                           */
+                                product.  A = 0 (or GA = 0) takes alpha = 1:
+                                X0 = 0 whatever alpha, and X = 0 is the answer    */
     double       tol;        /* stop tolerance for `stop`                            */
     pinv_stop    stop;
     int          max_iter;   /* 0 = the paper's 100 (Section 8)                      */

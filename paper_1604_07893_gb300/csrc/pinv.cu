@@ -645,8 +645,8 @@ int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
                 CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
                 CK(cudaStreamSynchronize(c.st));
                 const double pr = c.h->pinned[0] * c.h->pinned[1];
-                if (!(pr > 0.0) || !std::isfinite(pr)) return PINV_ERR_NONFINITE;
-                a = 1.0 / std::sqrt(pr);
+                if (!std::isfinite(pr)) return PINV_ERR_NONFINITE;
+                a = pr > 0.0 ? 1.0 / std::sqrt(pr) : 1.0;   // GA = 0: X0 = 0 for every alpha
             }
             scale_copy(n, n, c.X[1], m, a, c.X[0], m, c.st);
             ++c.kernels;
@@ -689,8 +689,10 @@ int initial_value(Ctx& c, const pinv_desc* d, double* alpha) {
             CK(cudaMemcpyAsync(c.h->pinned, c.h->dsmall, 2 * sizeof(double), cudaMemcpyDeviceToHost, c.st));
             CK(cudaStreamSynchronize(c.st));
             const double p = c.h->pinned[0] * c.h->pinned[1];
-            if (!(p > 0.0) || !std::isfinite(p)) return PINV_ERR_NONFINITE;
-            a = d->kind == PINV_OUTER_G ? 1.0 / std::sqrt(p) : 1.0 / p;
+            if (!std::isfinite(p)) return PINV_ERR_NONFINITE;
+            // A = 0 (or GA = 0): X0 = 0 for every alpha and X = 0 is the answer;
+            // take alpha = 1 as a batched group does
+            a = !(p > 0.0) ? 1.0 : (d->kind == PINV_OUTER_G ? 1.0 / std::sqrt(p) : 1.0 / p);
         }
         if (d->kind == PINV_MOORE_PENROSE) {
             transpose_scale(m, n, c.A, c.lda, a, c.X[0], m, c.st);

@@ -325,6 +325,13 @@ def test_zero_matrix(handle, prec):
     X, info = handle.solve(dev(A), alpha=1.0, tol=1e-12, prec=prec)
     assert info["status"] == 0 and info["iters"] == oinfo.iters == 1
     assert np.array_equal(host(X), ref)
+    # the alpha = 0 recipe is undefined for A = 0; any alpha gives X0 = 0, so the
+    # solve takes alpha = 1 (as a batched group does) and returns X = 0
+    X0, info0 = handle.solve(dev(A), alpha=0.0, tol=1e-12, prec=prec)
+    assert info0["status"] == 0 and info0["alpha"] == 1.0 and not host(X0).any()
+    G = np.zeros((4, 6))
+    Xg, infog = handle.solve(dev(A), kind="outer_g", G=dev(G), alpha=0.0, tol=1e-12, prec=prec)
+    assert infog["status"] == 0 and not host(Xg).any()
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp64_tc"])
