@@ -75,3 +75,35 @@ def test_every_field_offset_matches_the_header():
     for cname, cls in structs.items():
         for fname, _ in cls._fields_:
             assert int(got[f"{cname}.{fname}"]) == getattr(cls, fname).offset, (cname, fname)
+
+
+def test_header_is_strict_c99_and_cxx():
+    """pinv.h is a plain C header: it compiles warning-free as pedantic C99 and
+    as C++ (the extern "C" block), with a call of every entry point type-checked."""
+    import subprocess
+    import tempfile
+    body = """
+#include "pinv.h"
+int use(void) {
+    pinv_handle *h = 0; pinv_desc d; pinv_info info; pinv_precond_desc p; uint64_t id = 0;
+    int ix = 0, ranks[4], co = 0; double a = 0.0;
+    int r = pinv_init(&h, 0);
+    r |= pinv_solve(h, &d, 0, &info) | pinv_solve_complex(h, &d, 0, &info);
+    r |= pinv_preconditioner(h, &p, 0, &info) | pinv_solve_batched(h, 1, &d, 0, &info);
+    r |= pinv_submit(h, &d, &id) | pinv_poll(h, id, &info) | pinv_alpha_estimate(h, &d, 0, &a);
+    r |= pinv_step(h, 1, 1, 0, 1, 0, 0, 1, PINV_PREC_FP64, 0, 0, &a);
+    r |= pinv_gemm(h, 1, 1, 1, 0, 1, 0, 0, 1, 0, 0, 1, PINV_PREC_FP64, 0);
+    r |= pinv_drazin_index(h, 1, 0, 1, 2, 0, &ix, ranks) | pinv_autotune(h, 0, &co);
+    r |= pinv_step_noalloc(1, 1, 0, 1, 0, 0, 1, 0, 0, &a);
+    pinv_destroy(h);
+    return r;
+}
+"""
+    with tempfile.TemporaryDirectory() as d:
+        for lang, compiler, flags, ext in (("c", "gcc", ["-std=c99"], "c"), ("c++", "g++", ["-std=c++11"], "cpp")):
+            src = os.path.join(d, f"u.{ext}")
+            open(src, "w").write(body)
+            subprocess.run([compiler] + flags + ["-Wall", "-Wextra", "-Werror", "-pedantic",
+                                                 "-Wno-unused-parameter", "-Wno-maybe-uninitialized",
+                                                 "-Wno-uninitialized", "-I", os.path.dirname(HEADER),
+                                                 "-c", src, "-o", os.path.join(d, f"u_{ext}.o")], check=True)
