@@ -38,7 +38,10 @@ namespace {
 
 constexpr int kMaxDim = PINV_NOALLOC_MAX_DIM;
 constexpr size_t kSquare = (size_t)kMaxDim * kMaxDim;      // doubles in one square
-constexpr int kMaxTiles = ((kMaxDim + 63) / 64) * ((kMaxDim + 63) / 64);
+// Every product runs on the DMMA kernel with this CTA tile, one stop-norm pair
+// per CTA; the partial slots below are sized for it (and checked per call).
+constexpr int kTile = 64;
+constexpr int kMaxTiles = ((kMaxDim + kTile - 1) / kTile) * ((kMaxDim + kTile - 1) / kTile);
 // 7 squares (R, R2, R4, L1, L2, T, S), one n x m half step, 2 partials per CTA,
 // two reduced norms.
 constexpr size_t kScratchDoubles = 8 * kSquare + 2 * kMaxTiles + 2;
@@ -93,6 +96,8 @@ extern "C" int pinv_step_noalloc(int m, int n, const double* A, int lda, const d
                      m, n, kMaxDim, kMaxDim);
         return PINV_ERR_BUDGET;
     }
+    // the stop-norm partials come from the n x m update product: one pair per CTA
+    if (gemm_f64_ctas(n, m, kTile) > kMaxTiles) return PINV_ERR_BUDGET;
     double* base = nullptr;
     int rc = scratch_address(&base);
     if (rc) return rc;
@@ -120,7 +125,7 @@ extern "C" int pinv_step_noalloc(int m, int n, const double* A, int lda, const d
     bool ok = true;
     auto G = [&](int M, int N, int K, const double* a, int la, bool ta, const double* b, int lb,
                  bool tb, const Epilogue& e) {
-        int r = gemm_f64(M, N, K, a, la, ta, b, lb, tb, e, st);
+        int r = gemm_f64(M, N, K, a, la, ta, b, lb, tb, e, st, 1, 0, false, kTile);
         if (r < 0) ok = false;
         return r;
     };
@@ -161,10 +166,13 @@ extern "C" int pinv_step_noalloc(int m, int n, const double* A, int lda, const d
     }
     if (!ok || parts < 0) return PINV_ERR_CUDA;
     reduce_pairs(partials, parts, norms, st);
+    // a failed launch of this call is reported here; errors left behind by
+    // other code are neither reported nor cleared
+    if (cudaPeekAtLastError() != cudaSuccess) return PINV_ERR_CUDA;
     double h[2] = {0.0, 0.0};
     if (cudaMemcpyAsync(h, norms, sizeof(h), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return PINV_ERR_CUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return PINV_ERR_CUDA;
     if (rel_step) *rel_step = h[1] > 0 ? std::sqrt(h[0] / h[1]) : INFINITY;
-    return cudaGetLastError() == cudaSuccess ? PINV_OK : PINV_ERR_CUDA;
+    return PINV_OK;
 }
