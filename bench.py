@@ -3,12 +3,16 @@
 
 Workload (seeded, synthetic): A = U diag(s) V^T, Haar U (4096 x 2304) and
 V (3072 x 2304), s log-spaced in [1e-4, 1] (rank 2304, kappa 1e4 on the
-range), X0 = alpha A^T with alpha = 2/(s_1^2 + s_r^2) (Section 4), stabilised
-variant (Section 7) with the cleanup-and-one-loop finish.
+range), X0 = alpha A^T with alpha = 1/s_1^2 (Section 4: any 0 < alpha <
+2/s_1^2 converges; this end of the range keeps every residual eigenvalue in
+[0, 1), which low-precision loops need), stabilised variant (Section 7) with
+the cleanup finish.
 
-Settings: stabilised variant switched on after the first loop whose step is
-below 0.5, order-18 stop (step < 1e-2 keeps that loop's result: the next step
-would be below rounding), cleanup finish.
+Settings: mixed precision -- FP32-class products while the iterate grows,
+FP64-class products from the loop after the first step below 1 -- the
+stabilised product in the FP64-class loops after a step below 0.9, order-18
+stop (step < 1e-2 keeps that loop's result: the next step would be below
+rounding), cleanup finish (projection + order-2 step in FP64 class).
 
 One step = one full solve through pinv_solve on device-resident A.  The
 metric counts a solve only if it reaches the 1e-9 Penrose residual; the
@@ -16,11 +20,15 @@ accuracy of the last timed result is checked after the timed region
 (Penrose residuals on the device and sampled rows against the closed form
 V diag(1/s) U^T).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64_tc|fp64|fp32|mixed_bf16]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp32|fp64_tc|fp64|mixed_bf16]
 
-The default path computes every product FP64-accurately on the BF16 tensor
-cores (7 exact BF16 slices per operand, 28 slice products per FP64 product);
-the plain FP64 iteration (native FP64 DMMA products) is timed beside it.
+The default (--prec fp32) is the mixed form: FP32-class slice products (4
+exact BF16 slices per operand, 10 slice products) in the growth loops,
+FP64-class ones (7 slices, 28 slice products) in the last loops and the
+finish, all on the BF16 tensor cores.  Beside it the line carries the same
+solve with every product FP64-class on the tensor cores (fp64_tc) and the
+plain FP64 iteration on native FP64 DMMA products (fp64_gpu), each with its
+own loop count.
   python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores
 
 Multi-GPU: independent replicas (one solve per rank per step, no collective on
@@ -163,21 +171,25 @@ def replica_throughput(world: int, steps: int, max_ms: float) -> float:
 def workload():
     from paper_1604_07893_gb300 import workloads as W
     w = W.rectangular(M, N, RANK, 1.0, S_MIN, seed=SEED)
-    alpha = 2.0 / (w.s[0] ** 2 + w.s[-1] ** 2)
+    alpha = 1.0 / w.s[0] ** 2
     return w, alpha
 
 
+SWITCH_TOL = 0.9
+
+
 def solve_kwargs(prec, alpha):
-    """Stabilised variant, switched on after the first loop whose step is below
-    0.5 (the iterate is then accurate to ~1e-6, so X A X does not collapse
-    anything), stopped by the order-18 rule at step < 1e-2, cleanup finish."""
+    """Stabilised variant in the FP64-class loops after a step below 0.9 (the
+    iterate is then within one order-18 contraction of its limit, so X A X
+    does not collapse anything), stopped by the order-18 rule at step < 1e-2,
+    cleanup finish."""
     return dict(alpha=alpha, tol=1e-2, stop="order18", prec=prec, variant="stabilized",
-                switch_tol=0.5, finish="clean")
+                switch_tol=SWITCH_TOL, finish="clean")
 
 
 # Loops of one solve of the headline workload with the bench's settings, as the
 # oracle itself runs them (order-18 stop at 1e-2, stabilised after a step
-# below 0.5, cleanup finish): 8 loops, one of them stabilised.  The GPU solve
+# below 0.9, cleanup finish): 8 loops, one of them stabilised.  The GPU solve
 # reports the same counts.
 ORACLE_LOOPS, ORACLE_STAB_LOOPS = 8, 1
 
@@ -212,10 +224,17 @@ def cpu_oracle_sample(A, alpha, loops_per_solve=ORACLE_LOOPS, stab_loops=ORACLE_
             "s_per_solve": per_solve}
 
 
+SCHEDULES = {"fp32": "fp32-class products while the step is >= 1, then fp64-class; finish fp64-class",
+             "fp64_tc": "fp64-class products throughout",
+             "fp64": "native fp64 (DMMA) products throughout",
+             "mixed_bf16": "bf16 while the step is > 0.5, fp32-class, then fp64-class"}
+
+
 def bench_config(prec, world):
     """The `config` of the headline line, shared by both arms."""
     return {"workload": WORKLOAD, "m": M, "n": N, "rank": RANK, "s_range": [S_MIN, 1.0],
-            "prec": prec, "variant": "stabilized", "switch_tol": 0.5, "stop": "order18",
+            "alpha": "1/s_1^2", "prec": prec, "schedule": SCHEDULES[prec],
+            "variant": "stabilized", "switch_tol": SWITCH_TOL, "stop": "order18",
             "tol": 1e-2, "finish": "clean",
             "parallelism": f"replicas{world}", "l2": "inputs larger than L2 (A 100 MB, workspace 0.8 GB)"}
 
@@ -310,20 +329,25 @@ def run_ours(args):
         h.solve(A_np, X_np, host=True, **kw)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
 
-    # plain FP64 GPU iteration beside the mixed form
-    fp64 = None
-    if args.prec != "fp64" and not args.no_fp64:
-        kw64 = solve_kwargs("fp64", alpha)
-        h.solve(A, X, **kw64)
+    # the same solve with every product FP64-class on the tensor cores, and the
+    # plain FP64 GPU iteration (native FP64 DMMA products), beside the mixed form
+    def other_arm(prec, reps):
+        kwo = solve_kwargs(prec, alpha)
+        h.solve(A, X, **kwo)
         torch.cuda.synchronize(dev)
         s0 = torch.cuda.Event(enable_timing=True)
         s1 = torch.cuda.Event(enable_timing=True)
         s0.record(stream)
-        _, i64 = h.solve(A, X, **kw64)
+        for _ in range(reps):
+            _, io = h.solve(A, X, **kwo)
         s1.record(stream)
         torch.cuda.synchronize(dev)
-        fp64 = {"value": 1e3 / s0.elapsed_time(s1), "unit": UNIT, "ms_per_solve": s0.elapsed_time(s1),
-                "loops": i64["iters"]}
+        _, co = h.solve(A, X, check=True, **kwo)
+        ms = s0.elapsed_time(s1) / reps
+        return {"value": 1e3 / ms, "unit": UNIT, "ms_per_solve": ms, "loops": io["iters"],
+                "stabilized_loops": io["stabilized_loops"], "penrose_max": max(co["penrose"])}
+    fp64_tc = other_arm("fp64_tc", 3) if args.prec != "fp64_tc" and not args.no_fp64 else None
+    fp64 = other_arm("fp64", 1) if args.prec != "fp64" and not args.no_fp64 else None
 
     if rank != 0:
         h.close()
@@ -358,13 +382,16 @@ def run_ours(args):
         "metric": METRIC, "value": value if ok else 0.0, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": {"fp64": "f64", "fp64_tc": "bf16 slices (fp64-class)", "fp32": "bf16 slices (fp32-class)",
+        "dtype": {"fp64": "f64", "fp64_tc": "bf16 slices (fp64-class)",
+                  "fp32": "bf16 slices (fp32-class, then fp64-class)",
                   "mixed_bf16": "bf16 + bf16 slices"}[args.prec],
         "data": "synthetic",
         "config": bench_config(args.prec, world),
         "latency_ms": {"p50": p50, "p99": p99},
         "accuracy": {"penrose_max": penrose, "sampled_rows_rel_err": row_err, "meets_1e-9": ok,
-                     "loops": infos[-1]["iters"], "stabilized_loops": infos[-1]["stabilized_loops"]},
+                     "loops": infos[-1]["iters"], "stabilized_loops": infos[-1]["stabilized_loops"],
+                     "loop_classes": ["fp64" if p == 0 else {1: "bf16", 3: "fp32-class", 4: "fp64-class"}[p]
+                                      for p in infos[-1]["precision"]]},
         "e2e": {"value": world / e2e_s if ok else 0.0, "unit": UNIT,
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": N * M * 8},
         "gpu_launches": sum(i["kernels"] for i in infos),
@@ -375,6 +402,7 @@ def run_ours(args):
                      "gemm_launches": gemm_launches, "gemm_share_of_step": gemm_ms / total_ms},
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "fp64_tc": fp64_tc,
         "fp64_gpu": fp64,
     }
     print(json.dumps(line), flush=True)
@@ -447,11 +475,31 @@ def run_mp64(args):
     h.close()
 
 
+def _roofline(infos, peaks_prec="bf16"):
+    """The dominant kernel's rate over the given solves (profile=True): BF16
+    slice-product flops (or FP64 flops for the DMMA path) / CUDA-event time of
+    the product kernels, against the measured BF16 sustained peak."""
+    peaks, src = load_peaks()
+    gemm_ms = sum(i["gemm_ms"] for i in infos)
+    if gemm_ms <= 0:
+        return None
+    fp64 = peaks_prec == "fp64"
+    work = sum(i["gemm_flops"] for i in infos) if fp64 else sum(i["tensor_flops"] for i in infos)
+    achieved = work / (gemm_ms * 1e-3) / 1e12
+    peak, note = dominant_peak("fp64" if fp64 else "fp32", peaks)
+    return {"bound": "tensor", "kernel": "gemm_f64_kernel" if fp64 else "tc_gemm_kernel",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "fp64_equivalent_tflops": sum(i["gemm_flops"] for i in infos) / (gemm_ms * 1e-3) / 1e12,
+            "traffic": None, "peak_source": f"{src}: {note}",
+            "gemm_share_of_step": None}
+
+
 def run_drazin(args):
     """Drazin inverse of a 2048 x 2048 index-2 matrix (C 1536 x 1536, 256 2x2
-    Jordan blocks), X0 = A^2 / Tr(A^3), FP64-class products on the tensor cores,
-    order-18 stop (step < 1e-2), finish A^2 X^5 A^2 + one order-2 step; native FP64
-    beside it."""
+    Jordan blocks), X0 = A^2 / Tr(A^3), order-18 stop (step < 1e-2), finish
+    A^2 X^5 A^2 + one order-2 step.  The line's value is the mixed form
+    (FP32-class growth loops, then FP64-class); every product FP64-class on the
+    tensor cores (fp64_tc) and native FP64 (fp64_gpu) are timed beside it."""
     import torch
     from oracle import hyperpower as H
     from paper_1604_07893_gb300 import Handle, workloads as W
@@ -466,22 +514,33 @@ def run_drazin(args):
     h = Handle(0)
     st = torch.cuda.current_stream()
     res = {}
-    for prec in ("fp64_tc", "fp64"):
+    roof = None
+    total_ms = None
+    for prec in ("fp32", "fp64_tc", "fp64"):
         kw = dict(kind="drazin", drazin_index=2, alpha=0.0, tol=1e-2, stop="order18", prec=prec, finish="clean")
-        for _ in range(args.warmup if prec == "fp64_tc" else 1):
+        for _ in range(args.warmup if prec != "fp64" else 1):
             h.solve(A, X, **kw)
-        times = []
-        for _ in range(args.steps if prec == "fp64_tc" else 1):
+        times, infos = [], []
+        for _ in range(args.steps if prec != "fp64" else 1):
             e0, e1 = _events(st)
             e0.record(st)
-            _, info = h.solve(A, X, **kw)
+            _, info = h.solve(A, X, profile=(prec == "fp32"), **kw)
             e1.record(st)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
+            infos.append(info)
         _, cinfo = h.solve(A, X, check=True, **kw)
         err = float(np.linalg.norm(X.cpu().numpy()[rows] - ref_rows) / np.linalg.norm(ref_rows))
         res[prec] = {"value": 1e3 / statistics.mean(times), "ms_per_solve": statistics.mean(times),
-                     "loops": info["iters"], "drazin_residuals": cinfo["drazin"], "sampled_rows_rel_err": err}
+                     "loops": info["iters"], "drazin_residuals": cinfo["drazin"], "sampled_rows_rel_err": err,
+                     "meets_1e-9": bool(err <= 1e-9 and max(cinfo["drazin"]) <= 1e-9),
+                     "loop_classes": ["fp64" if p == 0 else {1: "bf16", 3: "fp32-class", 4: "fp64-class"}[p]
+                                      for p in info["precision"]]}
+        if prec == "fp32":
+            roof = _roofline(infos)
+            total_ms = sum(times)
+            if roof:
+                roof["gemm_share_of_step"] = sum(i["gemm_ms"] for i in infos) / total_ms
     # the literal spectrum (eigenvalues all around the annulus): X0 = A^2/Tr(A^3)
     # cannot converge there; G = A^l (A^{2l+1})^T A^l does
     dl = W.drazin_index2(2048, 512, seed=2, sector=math.pi)
@@ -506,13 +565,15 @@ def run_drazin(args):
     t0 = time.perf_counter()
     H.hyperpower_step(d.A, H.x0_drazin(d.A, 2), side="right")
     t_loop = time.perf_counter() - t0
-    loops = res["fp64_tc"]["loops"] + 2
-    _emit({"metric": "Drazin inverses/s at 1e-9 (2048x2048, index 2)", "value": res["fp64_tc"]["value"],
+    loops = res["fp32"]["loops"] + 2
+    _emit({"metric": "Drazin inverses/s at 1e-9 (2048x2048, index 2)",
+           "value": res["fp32"]["value"] if res["fp32"]["meets_1e-9"] else 0.0,
            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-           "dtype": "bf16 slices (fp64-class)",
+           "dtype": "bf16 slices (fp32-class, then fp64-class)",
            "config": {"workload": "drazin_2048_index2", "n_nilpotent": 512, "spectrum": "sector |arg| <= pi/8",
-                      "stop": "order18", "tol": 1e-2,
+                      "prec": "fp32", "schedule": SCHEDULES["fp32"], "stop": "order18", "tol": 1e-2,
                       "steps": args.steps, "warmup": args.warmup},
+           "mixed": res["fp32"], "roofline": roof,
            "fp64_tc": res["fp64_tc"], "fp64_gpu": res["fp64"], "full_annulus_spectrum": res["annulus_literal"],
            "cpu_baseline": {"value": 1.0 / (t_loop * loops), "unit": "solves/s", "kind": "oracle",
                             "cores": len(os.sched_getaffinity(0)),
@@ -948,7 +1009,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp64_tc", choices=["fp64_tc", "fp64", "fp32", "mixed_bf16"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64_tc", "fp64", "mixed_bf16"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--workload", default="mp4096x3072",

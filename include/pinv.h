@@ -83,14 +83,25 @@ typedef enum {
 typedef enum {
     PINV_PREC_FP64       = 0, /* every product in native FP64 (DMMA)               */
     PINV_PREC_MIXED_BF16 = 1, /* loops in BF16 while the step is > 0.5 (growth phase),
-                                 FP32-class until it is < 1e-4 or stops falling, then
-                                 FP64-class (tensor cores).  For problems without a
-                                 null block (full column rank, nonsingular); needs
-                                 alpha <= 1/sigma_max^2 (e.g. the alpha = 0 recipe) */
+                                 then FP32-class loops, then FP64-class (tensor cores)
+                                 after the first FP32-class loop whose step is < 1.
+                                 For problems without a null block (full column rank,
+                                 nonsingular): on a rank-deficient problem BF16
+                                 rounding lands in the null block, which grows by 18
+                                 per loop (Theorem 6.2).  Needs alpha <= 1/sigma_max^2
+                                 (e.g. the alpha = 0 recipe)                       */
     PINV_PREC_MIXED_FP8  = 2, /* reserved: FP8 early loops (returns PINV_ERR_ARG)  */
     PINV_PREC_FP32       = 3, /* FP32-class loops (4 exact BF16 slices, 10 slice
-                                 products, 31 bits) until the step is < 1e-4 or
-                                 stops falling, then FP64-class                    */
+                                 products, 31 bits) while the iterate grows, then
+                                 FP64-class loops after the first step below 1: the
+                                 order-18 contraction of that loop removes the
+                                 FP32-class rounding of the range.  Also for rank-
+                                 deficient and rectangular problems (with the finish,
+                                 which removes the rounding in the blocks the loop
+                                 does not contract).  Needs alpha <= 1/sigma_max^2:
+                                 with 2/(sigma_1^2 + sigma_r^2) the top residual
+                                 eigenvalue sits at -1 and FP32-class rounding pushes
+                                 it past                                         */
     PINV_PREC_FP64_TC    = 4, /* every product FP64-accurate on the BF16 tensor
                                  cores: 7 exact slices per operand, 28 products    */
     PINV_PREC_BF16_FP32  = 5  /* FP32-finished: BF16 while the step is > 0.5, then
@@ -102,8 +113,9 @@ typedef enum {
 
 typedef enum {
     PINV_VARIANT_PLAIN      = 0, /* Eq. PM, 7 products per loop                    */
-    PINV_VARIANT_STABILIZED = 1  /* Eq. PM-modified once the step < switch_tol:
-                                    7 + 2 products per loop (the paper counts 8)   */
+    PINV_VARIANT_STABILIZED = 1  /* Eq. PM-modified in the final-class loops after
+                                    a step < switch_tol: 7 + 2 products per loop
+                                    (the paper counts 8)                           */
 } pinv_variant;
 
 typedef enum {
@@ -111,11 +123,11 @@ typedef enum {
     PINV_FINISH_CLEAN = 1    /* after the loops: projection X <- (XA)^T X (AX)^T
                                 (Moore-Penrose), A^l X^{2l+1} A^l (Drazin) or
                                 X A X (general G: fixes any outer inverse),
-                                then one FP64-class order-2 step of the same
-                                family, X <- X + (I - XA) X (Eq. hyper, p = 2),
-                                which squares the projection's rounding (after
-                                schedules with low-precision loops: one
-                                FP64-class order-18 loop instead)              */
+                                then one order-2 step of the same family,
+                                X <- X + (I - XA) X (Eq. hyper, p = 2), which
+                                squares the projection's rounding (after BF16
+                                loops: one order-18 loop instead); both in the
+                                schedule's final class                          */
 } pinv_finish;
 
 /* --------------------------------------------------------------- structs */
@@ -351,6 +363,18 @@ int  pinv_drazin_index(pinv_handle *h, int n, const double *A, int lda, int max_
  * tensor-core engine won everywhere.  The choice belongs to the handle. */
 int  pinv_autotune(pinv_handle *h, void *stream, int *crossover);
 
+/* Failure detection: the number of polls a device-side wait in the main loop
+ * of the tensor-core product kernel makes before it gives up, for every later
+ * call on this handle (0 restores the default, about a second of polling).
+ * When a wait gives up the kernel records an error word, stops issuing work,
+ * waits -- always with the default limit -- until the bulk copies and MMAs it
+ * already issued have landed, releases its TMEM and returns; the call then
+ * returns PINV_ERR_TIMEOUT and clears the word, so the next call starts clean.
+ * A short limit makes such a wait run out on purpose (the operand copies take
+ * longer than a few polls), which tests that path without a fault.  No
+ * counterpart in the paper. */
+int  pinv_set_wait_limit(pinv_handle *h, unsigned polls);
+
 /* For callers that cannot allocate device memory (a plugin whose host
  * framework owns the allocator, code under a pool that forbids cudaMalloc,
  * code that must not trigger the implicit synchronisation of cudaMalloc or
@@ -366,7 +390,9 @@ int  pinv_autotune(pinv_handle *h, void *stream, int *crossover);
  *   - The first call on each device looks up the array's device address
  *     (cudaGetSymbolAddress); make that first call before any stream capture.
  *   - All calls on a device share the array and it keeps the last call's
- *     contents: calls that overlap on the GPU race, so serialise them. */
+ *     contents: calls that overlap on the GPU race, so serialise them.
+ *   - The call returns after `stream` has finished the loop: it synchronises
+ *     the stream to read the two stop norms into *rel_step. */
 #define PINV_NOALLOC_MAX_DIM 128
 int  pinv_step_noalloc(int m, int n, const double *A, int lda, const double *X_in,
                        double *X_out, int ldx, int stabilized, void *stream,

@@ -201,12 +201,29 @@ def finish_moore_penrose(A: np.ndarray, X: np.ndarray, mul, side: str, step: str
     return X + mul(X, np.eye(A.shape[0]) - mul(A, X))
 
 
+def finish_drazin(A: np.ndarray, X: np.ndarray, l: int, mul, step: str = "order2") -> np.ndarray:
+    """The Drazin finish: X <- A^l X^{2l+1} A^l, then one order-2 step
+    X + X (I - AX) (or one order-18 loop)."""
+    Al = A
+    for _ in range(l - 1):
+        Al = mul(Al, A)
+    V = X
+    for _ in range(2 * l):
+        V = mul(V, X)
+    X = mul(mul(Al, V), Al)
+    if step == "order18":
+        return pm_loop(A, X, mul, "right")
+    return X + mul(X, np.eye(A.shape[0]) - mul(A, X))
+
+
 def run_schedule(A: np.ndarray, X0: np.ndarray, classes: list, finish: str | None = "order2",
-                 finish_class: str = "fp64_class", stabilise_from: int | None = None):
+                 finish_class: str = "fp64_class", stabilise_from: int | None = None,
+                 drazin_index: int = 0):
     """Loops k = 0 .. len(classes)-1 with the products of class classes[k]
-    (plus X A X in loops >= stabilise_from), then the finish in finish_class.
+    (plus X A X in loops >= stabilise_from), then the finish in finish_class
+    (the Drazin finish when drazin_index > 0, else the Moore-Penrose one).
     Returns (X, relative steps of the loops)."""
-    side = H.choose_side(*A.shape)
+    side = "right" if drazin_index else H.choose_side(*A.shape)
     X = X0
     steps = []
     for k, cls in enumerate(classes):
@@ -220,5 +237,8 @@ def run_schedule(A: np.ndarray, X0: np.ndarray, classes: list, finish: str | Non
         if not np.all(np.isfinite(X)):
             return X, steps
     if finish is not None:
-        X = finish_moore_penrose(A, X, CLASSES[finish_class], side, finish)
+        if drazin_index:
+            X = finish_drazin(A, X, drazin_index, CLASSES[finish_class], finish)
+        else:
+            X = finish_moore_penrose(A, X, CLASSES[finish_class], side, finish)
     return X, steps

@@ -27,7 +27,7 @@ HISTORY = 128
 EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_complex", "pinv_preconditioner",
            "pinv_solve_batched", "pinv_submit",
            "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_autotune", "pinv_drazin_index",
-           "pinv_step_noalloc")
+           "pinv_step_noalloc", "pinv_set_wait_limit")
 NOALLOC_MAX_DIM = 128
 
 
@@ -108,6 +108,7 @@ def load() -> C.CDLL:
                                       P(C.c_int)]
     lib.pinv_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
+    lib.pinv_set_wait_limit.argtypes = [C.c_void_p, C.c_uint]
     for name in EXPORTS:
         if name != "pinv_destroy":
             getattr(lib, name).restype = C.c_int
@@ -322,6 +323,13 @@ class Handle:
         if rc != PINV_OK:
             raise PinvError(rc, "pinv_gemm")
         return C
+
+    def set_wait_limit(self, polls: int):
+        """pinv_set_wait_limit: polls before a tensor-core kernel wait gives up
+        (0 = the default of about a second), for every later call."""
+        rc = self._lib.pinv_set_wait_limit(self._h, C.c_uint(polls))
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_set_wait_limit")
 
     def drazin_index(self, A, *, max_index: int = 16, stream=None):
         """pinv_drazin_index: ind(A) of a square device matrix and the ranks of

@@ -85,6 +85,7 @@ struct pinv_handle {
     double* pinned = nullptr;  // host pinned readback block
     double* dsmall = nullptr;  // device: reduction outputs
     int* derr = nullptr;       // device error word of the tensor-core kernels
+    unsigned wait_limit = 0;   // polls of a tensor-core kernel wait (0: the default)
     int tc_crossover = 0;      // pinv_autotune: FP64-class products below this size use DMMA
     int sms = 1;               // streaming multiprocessors of the device
     std::vector<cudaEvent_t> events;  // profiling pool (pairs), created on demand
@@ -283,7 +284,7 @@ int gemm(Ctx& c, int M, int N, int K, const double* A, int lda, bool tA, const d
         }
         r = tc_gemm(M, N, K, A, lda, tA, B, ldb, tB, e, tc_mode(c.prec_k), c.tcws, c.tcws_bytes,
                     c.h->derr, c.st, &c.kernels, prof_ev(c, slot, 0), prof_ev(c, slot, 1), c.batch,
-                    c.stride, c.yield_sms, sym);
+                    c.stride, c.yield_sms, sym, c.h->wait_limit);
     }
     if (c.cplx && r >= 0) {
         for (int o = 0; o < e.nout; ++o) {
@@ -315,16 +316,31 @@ int read_norms(Ctx& c, int count, double* dx2, double* x2) {
     return PINV_OK;
 }
 
-// One loop of Eq. PM in FP64: Xout = Xin (I + R)(T S + mu R2 + psi R4).
-// Returns the number of pair partials written for ||Xout - Xin||, ||Xin||, or < 0.
+// Precision schedule (monotone): the product class of the next loop from the
+// class of the last loop and its relative step `rel` (||X_{k+1}-X_k||/||X_k||).
+//  * BF16 serves the growth phase while the step is above 0.5 (problems
+//    without a null block only: on a rank-deficient problem BF16 rounding lands
+//    in the null block, which grows by 18 per loop, Theorem 6.2).
+//  * FP32-class loops run while the iterate still grows (step >= 1); after the
+//    first FP32-class loop whose step is below 1 the iterate is within one
+//    order-18 contraction of its limit, and every later loop runs in the final
+//    class: that loop takes the remaining error e to e^18 and removes the
+//    FP32-class rounding of the range block at the same time.  Requires
+//    alpha <= 1/sigma_max^2 (with 2/(sigma_1^2 + sigma_r^2) the top residual
+//    eigenvalue sits at -1 and FP32-class rounding pushes it past).
+int next_level(int level, int last_level, int final_class, double rel) {
+    if (level == TC_BF16) return rel <= 0.5 ? TC_FP32 : level;
+    if (level == TC_FP32 && final_class != TC_FP32 && last_level == TC_FP32 && rel < 1.0) return final_class;
+    return level;
+}
+
 // One order-2 step of the hyperpower family (p = 2): X' = X + R X (left) or
 // X + X R, R = I - XA | I - AX; it squares the residual with two products.
-// The finish uses it after the projection when every loop was FP64-class: the
-// projection's error is then first-order rounding, which one squaring removes.
-// After low-precision loops the projection leaves the second-order remainder
-// of their persistent off-diagonal blocks (up to ~1e-2), and a full order-18
-// loop follows instead.
-bool finish_order2(int prec) { return prec == PINV_PREC_FP64 || prec == PINV_PREC_FP64_TC; }
+// The finish uses it after the projection unless BF16 loops ran: the
+// projection's error is then first-order rounding (of FP64- or FP32-class
+// loops), which one squaring removes.  After BF16 loops the projection leaves
+// the second-order remainder of their persistent off-diagonal blocks (up to
+// ~1e-2), and a full order-18 loop follows instead.
 
 int ns_step_f64(Ctx& c, const double* Xin, double* Xout) {
     const int s = c.s, m = c.m, n = c.n;
@@ -1076,20 +1092,17 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
     double prev = INFINITY;
     bool stabilise = false;
     int status = PINV_ERR_MAXITER, reason = 2;
-    // precision of the final (FP64-class) products: native FP64 or the tensor-core engine
     // the precision of the last loops (and of the stop rule): native FP64, the
     // FP64-class slice engine, or FP32-class for the FP32-finished schedule
     const int fp64_class = d->prec == PINV_PREC_FP64 ? 0 : (d->prec == PINV_PREC_BF16_FP32 ? TC_FP32 : TC_FP64);
-    // Precision schedule: the level only rises.  BF16 serves the growth phase
-    // (step > 0.5: the iterate is still being scaled up and any error is
-    // corrected later -- for problems without a null block); FP32-class
-    // products then run until the step falls below 1e-4 or stops falling
-    // (their noise floor); every later loop, the stop rule and the switch to
-    // the stabilised loop use FP64-class products.
+    // Precision schedule (next_level): the class only rises, BF16 -> FP32-class
+    // -> final class; the stop rule and the stabilising product use final-class
+    // loops only.
     int level = (d->prec == PINV_PREC_MIXED_BF16 || d->prec == PINV_PREC_BF16_FP32)
                     ? TC_BF16 : (d->prec == PINV_PREC_FP32 ? TC_FP32 : fp64_class);
     int prev_prec = -1;
-    double prev2 = INFINITY;
+    double prev_rel = INFINITY;   // relative step of the last loop (schedule input)
+    bool bf16_ran = false;
     // Small plain solves at one precision run the whole loop on the device (a
     // graph WHILE node with the stop rule in a kernel): one launch per solve.
     bool on_device = replay && !h->device_loop_off && d->variant == PINV_VARIANT_PLAIN && level == fp64_class &&
@@ -1107,16 +1120,17 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         }
     }
     for (int k = 0; !on_device && k < max_iter; ++k) {
-        const bool stab_now = stabilise;
         const double* Xk = c.X[cur];
         double* Xn = c.X[cur ^ 1];
         int parts;
-        // product precision of loop k (the step of loop k-1 says how far from
+        // product class of loop k (the step of loop k-1 says how far from
         // convergence the iterate is; low precision only far from it)
-        if (level == TC_BF16 && prev <= 0.5) level = TC_FP32;
-        if (level == TC_FP32 && (prev <= 1e-4 || (prev < 1e-2 && prev >= 0.25 * prev2))) level = fp64_class;
+        level = next_level(level, prev_prec, fp64_class, prev_rel);
         const int prec_k = level;
         c.prec_k = prec_k;
+        if (prec_k == TC_BF16) bf16_ran = true;
+        // the stabilising product runs in final-class loops only
+        const bool stab_now = stabilise && prec_k == fp64_class;
         double dx2, x2;
         if (stab_now) ++info->stabilized_loops;
         if (replay) {
@@ -1149,9 +1163,9 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         // most a factor 18 (|p(r)| <= 18 for |r| <= 1)
         const double rel = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
         if (rel > 1e3 && k > 0) { status = PINV_ERR_DIVERGED; info->iters = k; break; }
-        if (d->variant == PINV_VARIANT_STABILIZED && e < switch_tol && prec_k == fp64_class) stabilise = true;
-        prev2 = prev;
+        if (d->variant == PINV_VARIANT_STABILIZED && e < switch_tol) stabilise = true;
         prev = e;
+        prev_rel = rel;
         prev_prec = prec_k;
         info->rel_step = e;
         cur ^= 1;
@@ -1163,10 +1177,9 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         // projection, then one order-2 step (Theorems 6.2 / 7.1: the blocks the
         // loop does not contract are removed; the step squares the projection's
         // first-order rounding in the range block) -- or one order-18 loop
-        // after low-precision loops
+        // after BF16 loops
         cleanup_f64(c, d, c.X[cur], c.X[cur ^ 1]);
-        int parts = finish_order2(d->prec) ? ns_step_f64(c, c.X[cur ^ 1], c.X[cur])
-                                           : pm_loop_f64(c, c.X[cur ^ 1], c.X[cur]);
+        int parts = !bf16_ran ? ns_step_f64(c, c.X[cur ^ 1], c.X[cur]) : pm_loop_f64(c, c.X[cur ^ 1], c.X[cur]);
         if (parts < 0) return info->status = PINV_ERR_CUDA;
     }
     const double* Xfinal = c.X[cur];
@@ -1196,6 +1209,8 @@ struct Group {
     std::vector<pinv_info> info;
     int batch = 0, M = 0, N = 0, prec = 0, fp64_class = 0, level = 0, prev_prec = -1;
     bool left = false, stabilise = false, finish = false;
+    bool stab_now = false;         // the loop in flight appends the stabilising product
+    bool bf16_ran = false;         // some loop ran BF16 products (finish: order-18 loop)
     int k = 0, cur = 0, max_iter = 100;
     char* mem = nullptr;
     double* pinned = nullptr;      // norms [2 batch] then masks
@@ -1205,7 +1220,7 @@ struct Group {
     double* dalpha = nullptr;
     double* dnorms = nullptr;
     cudaEvent_t ev = nullptr;
-    std::vector<double> prev, prev2;
+    std::vector<double> prev, prev_rel;
     std::vector<char> done;
     int parts = 0;
     int err = PINV_OK;
@@ -1277,7 +1292,7 @@ int group_begin_impl(Group& G) {
     const bool gk = d0.kind == PINV_OUTER_G;
     G.info.assign(G.batch, pinv_info{});
     G.prev.assign(G.batch, INFINITY);
-    G.prev2.assign(G.batch, INFINITY);
+    G.prev_rel.assign(G.batch, INFINITY);
     G.done.assign(G.batch, 0);
     if (G.serving) {
         // smaller problems on higher-priority streams: their CTAs are scheduled
@@ -1406,20 +1421,21 @@ int group_begin_impl(Group& G) {
 // Issue loop k for every instance (asynchronous; norms land in pinned memory).
 int group_issue_impl(Group& G) {
     Ctx& c = G.c;
-    double maxprev = 0.0, maxprev2 = 0.0;
+    double maxrel = 0.0;   // the slowest running instance decides the group's class
     for (int b = 0; b < G.batch; ++b)
-        if (!G.done[b]) { maxprev = std::max(maxprev, G.prev[b]); maxprev2 = std::max(maxprev2, G.prev2[b]); }
-    if (G.level == TC_BF16 && maxprev <= 0.5) G.level = TC_FP32;
-    if (G.level == TC_FP32 && (maxprev <= 1e-4 || (maxprev < 1e-2 && maxprev >= 0.25 * maxprev2))) G.level = G.fp64_class;
+        if (!G.done[b]) maxrel = std::max(maxrel, G.prev_rel[b]);
+    G.level = next_level(G.level, G.prev_prec, G.fp64_class, maxrel);
     c.prec_k = G.level;
+    if (G.level == TC_BF16) G.bf16_ran = true;
+    G.stab_now = G.stabilise && G.level == G.fp64_class;
     if (!G.serving) {
         // one-shot batches issue directly: a group runs ~9 loops, and capturing
         // and instantiating its graphs (~3 ms per group) costs more than the
         // launches it saves (measured 1354 vs 1214 ms for 4096 problems)
         const double* Xk = c.X[G.cur];
         double* Xn = c.X[G.cur ^ 1];
-        int parts = pm_loop_f64(c, Xk, G.stabilise ? c.X[2] : Xn);
-        if (G.stabilise) parts = stabilise_f64(c, c.X[2], Xk, Xn);
+        int parts = pm_loop_f64(c, Xk, G.stab_now ? c.X[2] : Xn);
+        if (G.stab_now) parts = stabilise_f64(c, c.X[2], Xk, Xn);
         if (parts < 0) return G.err = PINV_ERR_CUDA;
         G.parts = parts;
         reduce_pairs(c.partials, parts, G.dnorms, G.st, G.batch);
@@ -1432,7 +1448,7 @@ int group_issue_impl(Group& G) {
     // serving groups live for many loops next to other groups: their loop
     // chain is replayed as a CUDA graph (one per level, stabilised flag and
     // ping-pong side), which frees the host to feed the other groups
-    const int key = (G.level * 2 + (G.stabilise ? 1 : 0)) * 2 + G.cur;
+    const int key = (G.level * 2 + (G.stab_now ? 1 : 0)) * 2 + G.cur;
     auto it = G.graphs.find(key);
     if (it == G.graphs.end()) {
         // capture the loop: seven (or nine) products, the norm reduction and the
@@ -1441,8 +1457,8 @@ int group_issue_impl(Group& G) {
         CK(cudaStreamBeginCapture(G.st, cudaStreamCaptureModeThreadLocal));
         const double* Xk = c.X[G.cur];
         double* Xn = c.X[G.cur ^ 1];
-        int parts = pm_loop_f64(c, Xk, G.stabilise ? c.X[2] : Xn);
-        if (G.stabilise) parts = stabilise_f64(c, c.X[2], Xk, Xn);
+        int parts = pm_loop_f64(c, Xk, G.stab_now ? c.X[2] : Xn);
+        if (G.stab_now) parts = stabilise_f64(c, c.X[2], Xk, Xn);
         if (parts >= 0) {
             reduce_pairs(c.partials, parts, G.dnorms, G.st, G.batch);
             cudaMemcpyAsync(G.pinned, G.dnorms, sizeof(double) * 2 * G.batch, cudaMemcpyDeviceToHost, G.st);
@@ -1510,7 +1526,7 @@ int group_complete_impl(Group& G) {
         const double e = stop_measure(&x, dx2, x2, k, I.alpha);
         I.loops_run = k + 1;
         if (k < PINV_HISTORY) { I.history[k] = e; I.precision[k] = (signed char)prec_k; }
-        if (G.stabilise) ++I.stabilized_loops;
+        if (G.stab_now) ++I.stabilized_loops;
         const int maxit = x.max_iter ? x.max_iter : 100;
         int stop = 0;   // 1: keep X_k (buffer cur); 2: keep X_{k+1} (buffer cur^1)
         if (!std::isfinite(e)) { I.status = PINV_ERR_NONFINITE; stop = 1; }
@@ -1519,7 +1535,7 @@ int group_complete_impl(Group& G) {
         }
         else {
             const double pv = G.prev[b];
-            const bool stalled = G.stabilise ? (e >= pv) : (pv < 1e-3 && e >= pv * pv);
+            const bool stalled = G.stab_now ? (e >= pv) : (pv < 1e-3 && e >= pv * pv);
             const double rel = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
             if (stalled && final_class) { I.status = PINV_OK; I.stop_reason = 1; I.iters = k; I.rel_step = pv; stop = 1; }
             else if (rel > 1e3 && k > 0) { I.status = PINV_ERR_DIVERGED; I.iters = k; stop = 1; }
@@ -1530,14 +1546,14 @@ int group_complete_impl(Group& G) {
             mask[stop == 1 ? b : G.batch + b] = 1;
             any_copy = true;
         } else {
-            G.prev2[b] = G.prev[b];
             G.prev[b] = e;
+            G.prev_rel[b] = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
             I.rel_step = e;
             I.iters = k + 1;
             if (!(e < (x.switch_tol > 0 ? x.switch_tol : 1e-3))) all_below_switch = false;
         }
     }
-    if (G.d[0].variant == PINV_VARIANT_STABILIZED && prec_k == G.fp64_class && all_below_switch) G.stabilise = true;
+    if (G.d[0].variant == PINV_VARIANT_STABILIZED && all_below_switch) G.stabilise = true;
     G.prev_prec = prec_k;
     if (any_copy) {
         // The host rewrites this mask only after the next loop's event, which the
@@ -1572,7 +1588,7 @@ int group_finish_issue_impl(Group& G) {
     c.prec_k = G.fp64_class;   // the finish runs in the schedule's final class
     pinv_desc d0 = G.d[0];
     cleanup_f64(c, &d0, c.X[0], c.X[1]);
-    const int parts = finish_order2(G.prec) ? ns_step_f64(c, c.X[1], c.X[0]) : pm_loop_f64(c, c.X[1], c.X[0]);
+    const int parts = !G.bf16_ran ? ns_step_f64(c, c.X[1], c.X[0]) : pm_loop_f64(c, c.X[1], c.X[0]);
     if (parts < 0) return G.err = PINV_ERR_CUDA;
     scatter_out(G.tabX, G.dmask, G.batch, G.N, G.M, c.X[0], G.M, c.stride, G.st);
     CK(cudaPeekAtLastError());
@@ -2078,7 +2094,7 @@ int pinv_gemm(pinv_handle* h, int M, int N, int K, const double* A, int lda, int
         if (rc) return rc;
         int kernels = 0;
         if (tc_gemm(M, N, K, A, lda, trans_a != 0, B, ldb, trans_b != 0, e, tc_mode(pk), h->ws, h->ws_bytes,
-                    h->derr, st, &kernels) < 0)
+                    h->derr, st, &kernels, nullptr, nullptr, 1, 0, false, false, h->wait_limit) < 0)
             return PINV_ERR_CUDA;
     }
     CK(cudaMemcpyAsync(h->pinned + 2, h->derr, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -2090,6 +2106,12 @@ int pinv_gemm(pinv_handle* h, int M, int N, int K, const double* A, int lda, int
         return PINV_ERR_TIMEOUT;
     }
     CK(cudaGetLastError());
+    return PINV_OK;
+}
+
+int pinv_set_wait_limit(pinv_handle* h, unsigned polls) {
+    if (!h) return PINV_ERR_ARG;
+    h->wait_limit = polls;
     return PINV_OK;
 }
 

@@ -20,8 +20,8 @@
 //   FP32-class: 4 slices (31 bits), s + t <= 3 (10 products)
 //   BF16:       1 slice rounded to nearest (no grid), one product
 //
-// Kernel layout (persistent, one CTA per SM, 10 warps; vertically adjacent
-// tiles run as two-CTA clusters sharing the B tile by TMA multicast):
+// Kernel layout (persistent, one CTA per SM walking the tiles, 10 warps; every
+// CTA issues its own TMA loads):
 //   warp 0      TMA producer: 3-D tensor maps [slice][row][k], 128B swizzle,
 //               ragged edges zero-filled by the TMA unit
 //   warp 1      TMEM allocator + single-thread tcgen05.mma issuer
@@ -34,6 +34,7 @@
 //               Eq. PM (identity, side inputs, up to three outputs) and the
 //               stop-norm partials
 // Every mbarrier wait is bounded; on timeout the kernel records an error code,
+// waits (bounded) until its own bulk copies and MMAs in flight have landed,
 // releases its TMEM and returns.
 
 #include <cuda.h>
@@ -85,6 +86,7 @@ struct TcParams {
     int tiles_m, tiles_n;
     Epilogue epi;
     int* err;             // device error word (0 = ok)
+    unsigned wait_limit;  // polls before a wait of the main loop gives up
     // bit patterns of the row maxima of op(A) and of the column maxima of op(B)
     // (exact modes): the epilogue scales each entry by 2^(e_i + f_j)
     const unsigned long long* rmax;
@@ -134,9 +136,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 // Bounded wait for the phase with parity `parity` to complete.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, unsigned limit = WAIT_LIMIT) {
     const uint32_t addr = smem_u32(bar);
-    for (unsigned i = 0; i < WAIT_LIMIT; ++i) {
+    for (unsigned i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
@@ -177,31 +179,6 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
-}
-// Multicast variant: the tile lands at the same shared-memory offset in every
-// CTA of `mask` and completes bytes on the barrier at the same offset in each.
-__device__ __forceinline__ void tma_load_3d_mc(void* dst, const CUtensorMap* map, uint64_t* bar, int c0,
-                                               int c1, int c2, uint16_t mask) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster"
-        " [%0], [%1, {%3, %4, %5}], [%2], %6;" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit_mc(uint64_t* bar, uint16_t mask) {
-    asm volatile(
-        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
-            smem_u32(bar)),
-        "h"(mask)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\nbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
@@ -274,11 +251,6 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 }
 
 // ------------------------------------------------------------------ the kernel
-// MC = false: one CTA per tile.  MC = true: clusters of two CTAs on vertically
-// adjacent tiles (m-blocks 2i, 2i+1, same n-block): each CTA loads its own A
-// tile and half of the shared B tile, multicast to both, so every CTA reads 24
-// instead of 32 KiB from L2 per stage; a stage is released only when both CTAs'
-// MMAs are done with it (the commit is multicast to both empty barriers).
 // Lean final pass of one epilogue warp for one tile (used when each pair has a
 // single K-chunk: few units per tile, so this pass weighs most): its 32 rows
 // (one per lane) x EPI_COLS columns of the tile sums in TMEM (units 2^-ubase)
@@ -357,7 +329,7 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
     if (rmax) __syncwarp();   // ecol is rewritten for the next tile
 }
 
-template <bool MC, bool LEAN>
+template <bool LEAN>
 __global__ void __launch_bounds__(THREADS, 1)   // 10 warps: 3 share a sub-partition (16K registers): <= 168 each
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                const __grid_constant__ TcParams P) {
@@ -367,31 +339,28 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     uint64_t* empty = full + STAGES;
     uint64_t* accf = empty + STAGES;
     uint64_t* acce = accf + 2;
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(acce + 2);
+    uint64_t* drain = acce + 2;   // completion of every MMA the issuer launched
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // Work items: tiles (MC = false) or vertical tile pairs (MC = true, one per cluster).
-    const int tiles_m2 = (P.tiles_m + 1) / 2;
-    const int tiles_per = MC ? tiles_m2 * P.tiles_n
-                             : (P.sym ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n);
+    const int tiles_per = P.sym ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;
     const int ntiles = tiles_per * P.batch;
-    const uint32_t crank = MC ? cluster_rank() : 0;
-    const int work0 = MC ? (int)(blockIdx.x >> 1) : (int)blockIdx.x;
-    const int wstep = MC ? (int)(gridDim.x >> 1) : (int)gridDim.x;
-    // tile of work item w for this CTA: instance b, blocks (mb, nb)
+    const int work0 = (int)blockIdx.x;
+    const int wstep = (int)gridDim.x;
+    // tile w of the launch: instance b, blocks (mb, nb)
     auto locate = [&](int w, int& b, int& mb, int& nb) {
         b = w / tiles_per;
-        const int tt = w % tiles_per;
-        if (MC) { mb = 2 * (tt % tiles_m2) + (int)crank; nb = tt / tiles_m2; }
-        else tile_coords(tt, P.tiles_m, P.sym, mb, nb);
+        tile_coords(w % tiles_per, P.tiles_m, P.sym, mb, nb);
     };
+    const unsigned wl = P.wait_limit;
     const int kchunks = (P.K + P.chunk - 1) / P.chunk;
     const int units = P.ngroups * kchunks;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], MC ? 2 : 1); }
+        for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 32 * EPI_WARPS); }
+        mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -403,7 +372,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     }
     tc_fence_before();
     __syncthreads();
-    if (MC) cluster_sync();   // the peer's barriers exist before any multicast reaches them
     tc_fence_after();
     const uint32_t tmem = *tmem_holder;
 
@@ -412,6 +380,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
+            // stages with a load issued (bit s), and the parity of its phase (bit s)
+            uint32_t issued = 0, ipar = 0;
             for (int tile = work0; tile < ntiles && !*abort_flag; tile += wstep) {
                 int b, mb, nb;
                 locate(tile, b, mb, nb);
@@ -423,22 +393,28 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     for (int q = 0; q < P.grp_npair[grp] && !*abort_flag; ++q) {
                         const int pr = P.grp_pair0[grp] + q;
                         for (int k = k_begin; k < k_end; k += BK) {
-                            if (!mbar_wait(&empty[stage], phase ^ 1)) {
+                            if (!mbar_wait(&empty[stage], phase ^ 1, wl)) {
                                 record_error(P.err, 1); *abort_flag = 1; break;
                             }
                             uint8_t* sa = smem + stage * STAGE_BYTES;
                             mbar_expect_tx(&full[stage], STAGE_BYTES);
                             tma_load_3d(sa, &mapA, &full[stage], k, m0, b * P.S + P.pair_s[pr]);
-                            if (MC)   // my half of the B tile, to both CTAs (8 KiB = 64 rows)
-                                tma_load_3d_mc(sa + A_TILE_BYTES + crank * (B_TILE_BYTES / 2), &mapB, &full[stage],
-                                               k, n0 + (int)crank * (BN / 2), b * P.S + P.pair_t[pr], (uint16_t)3);
-                            else
-                                tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, b * P.S + P.pair_t[pr]);
+                            tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, b * P.S + P.pair_t[pr]);
+                            issued |= 1u << stage;
+                            ipar = (ipar & ~(1u << stage)) | (phase << stage);
                             if (++stage == STAGES) { stage = 0; phase ^= 1; }
                         }
                     }
                 }
             }
+            // No bulk copy may still be writing into this CTA's shared memory when
+            // it exits: wait (bounded, full limit) for the last load of every
+            // stage.  A stage is reloaded only after its previous load was
+            // consumed, so the last phase issued is the only one that can be
+            // outstanding; on the normal path every wait returns at once.
+            for (int s2 = 0; s2 < STAGES; ++s2)
+                if ((issued >> s2) & 1u)
+                    if (!mbar_wait(&full[s2], (ipar >> s2) & 1u)) record_error(P.err, 5);
         }
     } else if (warp == 1) {
         // ---------------------------------------------------------- MMA issuer
@@ -453,7 +429,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     const int grp = u / kchunks, ch = u % kchunks;
                     const int k_begin = ch * P.chunk;
                     const int k_end = min(P.K, k_begin + P.chunk);
-                    if (!mbar_wait(&acce[buf], accphase[buf] ^ 1)) {
+                    if (!mbar_wait(&acce[buf], accphase[buf] ^ 1, wl)) {
                         record_error(P.err, 2); *abort_flag = 1; break;
                     }
                     tc_fence_after();
@@ -461,7 +437,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     uint32_t acc = 0;   // the group's pairs all add into one accumulator
                     for (int q = 0; q < P.grp_npair[grp] && !*abort_flag; ++q) {
                         for (int k = k_begin; k < k_end; k += BK) {
-                            if (!mbar_wait(&full[stage], phase)) {
+                            if (!mbar_wait(&full[stage], phase, wl)) {
                                 record_error(P.err, 3); *abort_flag = 1; break;
                             }
                             tc_fence_after();
@@ -472,8 +448,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                                 mma_bf16(d, smem_desc(a0 + kk * 32), smem_desc(b0 + kk * 32), idesc, acc);
                                 acc = 1;
                             }
-                            if (MC) mma_commit_mc(&empty[stage], (uint16_t)3);   // release in both CTAs
-                            else mma_commit(&empty[stage]);
+                            mma_commit(&empty[stage]);
                             if (++stage == STAGES) { stage = 0; phase ^= 1; }
                         }
                     }
@@ -482,6 +457,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     buf ^= 1;
                 }
             }
+            // every MMA this thread issued has finished (reading shared memory,
+            // writing TMEM) before the CTA releases either: on the normal path the
+            // epilogue has already drained them all
+            mma_commit(drain);
+            if (!mbar_wait(drain, 0)) record_error(P.err, 6);
         }
     } else {
         // ---------------------------------------------------------- epilogue (warps 2..9)
@@ -508,10 +488,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             int b, mb, nb;
             locate(tile, b, mb, nb);
             const int m0 = mb * BM, n0 = nb * BN;
-            // slot of the tile's partials (instance-major, nb-major then mb); an
-            // MC partner past the last m-block computes zeros and writes none
+            // slot of the tile's partials (instance-major, nb-major then mb)
             const int slot = b * P.tiles_m * P.tiles_n + nb * P.tiles_m + mb;
-            const bool real_tile = mb < P.tiles_m;
             const bool mirror = P.sym && mb != nb;   // also write the transposed tile
             Epilogue E = P.epi;   // instance b's matrices
             const long long off = (long long)b * P.stride;
@@ -533,7 +511,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
                     for (int j = 0; j < EPI_COLS; ++j) iacc[j] = 0;
                 }
-                if (*abort_flag || !mbar_wait(&accf[buf], accphase[buf])) {
+                if (*abort_flag || !mbar_wait(&accf[buf], accphase[buf], wl)) {
                     record_error(P.err, 4); *abort_flag = 1; ok = false; break;
                 }
                 tc_fence_after();
@@ -651,7 +629,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     sd += __shfl_xor_sync(0xffffffffu, sd, off);
                     sx += __shfl_xor_sync(0xffffffffu, sx, off);
                 }
-                if (lane == 0 && real_tile) {
+                if (lane == 0) {
                     E.partials[2 * (EPI_WARPS * slot + ew)] = sd;
                     E.partials[2 * (EPI_WARPS * slot + ew) + 1] = sx;
                 }
@@ -662,7 +640,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     __syncwarp();
     tc_fence_before();
     __syncthreads();
-    if (MC) cluster_sync();   // no CTA leaves while its peer may still write into it
     if (warp == 1) {
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
@@ -875,8 +852,7 @@ bool prepare_kernels() {
     const int dev = current_device();
     std::lock_guard<std::mutex> lk(g_dev_mu);
     if (g_dev[dev].attr) return true;
-    const void* kernels[4] = {(const void*)tc_gemm_kernel<false, false>, (const void*)tc_gemm_kernel<false, true>,
-                              (const void*)tc_gemm_kernel<true, false>, (const void*)tc_gemm_kernel<true, true>};
+    const void* kernels[2] = {(const void*)tc_gemm_kernel<false>, (const void*)tc_gemm_kernel<true>};
     for (const void* k : kernels) {
         cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
         cudaFuncAttributes fa;
@@ -920,7 +896,7 @@ size_t tc_smem_bytes() { return STAGES * STAGE_BYTES + 1024 + 256; }
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb, bool transB,
             const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err, cudaStream_t st,
             int* kernels, cudaEvent_t ev_begin, cudaEvent_t ev_end, int batch, long long stride,
-            bool one_tile_per_cta, bool sym_out) {
+            bool one_tile_per_cta, bool sym_out, unsigned wait_limit) {
     if (sym_out && (M != N || epi.partials)) return -1;
     const int Kp = ((K + 7) / 8) * 8;
     if (batch < 1 || tc_workspace_bytes(M, N, K, mode, batch) > ws_bytes) return -1;
@@ -952,15 +928,8 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
                                          mode.S, mode.exact, sb, stride);
         *kernels += 2;
     }
-    // clusters of two when there are at least two m-blocks to pair (not in symmetric mode)
-    const int tiles_m_ = (M + BM - 1) / BM;
-    // (not for launches that release their SMs after every tile: those share the
-    // GPU with other streams by priority, and a CTA pair needs two SMs of one
-    // GPC free at once, which lower-priority single CTAs keep taking)
-    const bool mc = !sym_out && tiles_m_ >= 2 && !one_tile_per_cta;
     CUtensorMap ma, mb;
-    if (!make_map(&ma, sa, batch * mode.S, M, Kp, BM) ||
-        !make_map(&mb, sb, batch * mode.S, N, Kp, mc ? BN / 2 : BN))
+    if (!make_map(&ma, sa, batch * mode.S, M, Kp, BM) || !make_map(&mb, sb, batch * mode.S, N, Kp, BN))
         return -1;
 
     TcParams P;
@@ -1008,6 +977,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.tiles_n = (N + BN - 1) / BN;
     P.epi = epi;
     P.err = err;
+    P.wait_limit = wait_limit ? wait_limit : WAIT_LIMIT;
     P.rmax = mode.exact ? ea : nullptr;
     P.cmax = mode.exact ? eb : nullptr;
     const int tiles = sym_out ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;   // per instance
@@ -1016,35 +986,13 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     const bool lean = (K + P.chunk - 1) / P.chunk == 1;
     if (!prepare_kernels()) return -1;
     if (ev_begin) cudaEventRecord(ev_begin, st);
-    if (mc) {
-        // one work item per cluster: a vertical pair of tiles
-        const int items = ((P.tiles_m + 1) / 2) * P.tiles_n * batch;
-        const int clusters = (one_tile_per_cta || items < num_sms() / 2) ? items : num_sms() / 2;
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(2 * clusters);
-        cfg.blockDim = dim3(THREADS);
-        cfg.dynamicSmemBytes = tc_smem_bytes();
-        cfg.stream = st;
-        cudaLaunchAttribute at[1];
-        at[0].id = cudaLaunchAttributeClusterDimension;
-        at[0].val.clusterDim.x = 2;
-        at[0].val.clusterDim.y = 1;
-        at[0].val.clusterDim.z = 1;
-        cfg.attrs = at;
-        cfg.numAttrs = 1;
-        if (cudaError_t e = lean ? cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true, true>, ma, mb, P)
-                                 : cudaLaunchKernelEx(&cfg, tc_gemm_kernel<true, false>, ma, mb, P);
-            e != cudaSuccess) {
-            std::fprintf(stderr, "tc_gemm: cluster launch failed: %s\n", cudaGetErrorString(e));
-            return -1;
-        }
-    } else {
+    {
         const int all_tiles = tiles * batch;
         // persistent (one CTA per SM walking the tiles) unless the caller wants
         // the SMs released after every tile (so higher-priority streams get in)
         const int grid = (one_tile_per_cta || all_tiles < num_sms()) ? all_tiles : num_sms();
-        if (lean) tc_gemm_kernel<false, true><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
-        else tc_gemm_kernel<false, false><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+        if (lean) tc_gemm_kernel<true><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+        else tc_gemm_kernel<false><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
     }
     if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;

@@ -30,10 +30,12 @@ size_t tc_smem_bytes();
 // instances one after another) or -1.  sym_out (M == N, no partials): the
 // caller guarantees op(A) op(B) is symmetric; only the upper-triangle tiles are
 // computed and each off-diagonal tile is also written transposed.
+// wait_limit: polls before a wait of the kernel's main loop gives up (0: the
+// default, about a second); the drain before exit always uses the default.
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb,
             bool transB, const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err,
             cudaStream_t st, int* kernels, cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr,
             int batch = 1, long long stride = 0, bool one_tile_per_cta = false,
-            bool sym_out = false);
+            bool sym_out = false, unsigned wait_limit = 0);
 
 }  // namespace pinv

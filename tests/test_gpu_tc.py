@@ -116,6 +116,27 @@ def test_mixed_solve_full_rank(handle, prec):
     assert rel(X.cpu().numpy(), pinv_closed_form(w)) <= 1e-9
 
 
+@pytest.mark.parametrize("m,n,r", [(512, 384, 288), (300, 420, 250)])
+def test_fp32_class_schedule_on_a_rank_deficient_problem(handle, m, n, r):
+    """FP32-class loops while the iterate grows, then FP64-class loops, then the
+    finish, with alpha = 1/s_1^2 (kappa 1e4 on the range): the same answer as
+    the FP64 oracle to 1e-9, on both residual sides; the precision record shows
+    the growth loops in FP32 class and the last loops in FP64 class."""
+    w = W.rectangular(m, n, r, 1.0, 1e-4, seed=12)
+    alpha = 1.0 / w.s[0] ** 2
+    ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-2, stop=H.STOP_ORDER18, alpha=alpha,
+                     finish="moore_penrose")
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp32", variant="stabilized",
+                           switch_tol=0.9, finish="clean", check=True)
+    assert info["status"] == 0
+    prec = info["precision"]
+    assert prec[0] == 3 and prec[-1] == 4 and sorted(prec) == prec
+    assert info["stabilized_loops"] >= 1
+    assert rel(X.cpu().numpy(), ref) <= 1e-9
+    assert rel(X.cpu().numpy(), pinv_closed_form(w)) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9
+
+
 def test_mixed_solve_spd(handle):
     s = W.spd(512, 1e-3, 1.0, seed=5)
     alpha = 1.0 / s.lam.max()          # BF16 loops need alpha <= 1/lambda_max
@@ -248,6 +269,24 @@ def test_drazin_order18_finish_parity(handle):
                            finish="clean", prec="fp64_tc", check=True)
     assert info["status"] == 0
     assert info["iters"] == oinfo.iters
+    assert rel(X.cpu().numpy(), ref) <= 1e-9
+    assert rel(X.cpu().numpy(), drazin_closed_form(d)) <= 1e-9
+    assert max(info["drazin"]) <= 1e-9
+
+
+@pytest.mark.parametrize("n,nil", [(256, 64), (600, 150)])
+def test_drazin_fp32_class_schedule_parity(handle, n, nil):
+    """The Drazin family in the mixed schedule (FP32-class growth loops, then
+    FP64-class loops and the finish in FP64 class): within 1e-9 of the FP64
+    oracle and of the closed form, Drazin residuals below 1e-9."""
+    d = W.drazin_index2(n, nil, seed=2)
+    alpha = 1.0 / np.trace(np.linalg.matrix_power(d.A, 3))
+    ref, _ = H.solve(d.A, H.x0_drazin(d.A, 2, alpha), tol=1e-2, stop=H.STOP_ORDER18, alpha=alpha,
+                     finish="drazin", drazin_index=2)
+    X, info = handle.solve(dev(d.A), kind="drazin", drazin_index=2, alpha=0.0, tol=1e-2, stop="order18",
+                           finish="clean", prec="fp32", check=True)
+    assert info["status"] == 0
+    assert info["precision"][0] == 3 and info["precision"][-1] == 4
     assert rel(X.cpu().numpy(), ref) <= 1e-9
     assert rel(X.cpu().numpy(), drazin_closed_form(d)) <= 1e-9
     assert max(info["drazin"]) <= 1e-9

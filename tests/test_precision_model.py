@@ -17,6 +17,10 @@ iteration tolerates in its early loops:
   lands in the null block, which grows by 18 per loop (Theorem 6.2) faster
   than the finish can remove it.
 * On a full-rank problem (no null block) BF16 growth loops are harmless.
+* On the Drazin family (index 2: a nilpotent block, on which I - AX keeps the
+  eigenvalue 1), FP32-class growth loops then FP64 class meet the FP64
+  accuracy, while one FP8 (per-tensor scaled E4M3) or BF16 first loop already
+  makes the iteration fail.
 """
 
 from fractions import Fraction
@@ -27,7 +31,7 @@ import pytest
 from oracle import hyperpower as H
 from oracle import precision as PM
 from paper_1604_07893_gb300 import workloads as W
-from tests.helpers import pinv_closed_form, rel
+from tests.helpers import drazin_closed_form, pinv_closed_form, rel
 
 
 # ----------------------------------------------------------------- formats
@@ -181,3 +185,33 @@ def test_bf16_growth_loops_are_harmless_without_a_null_block():
     classes = ["bf16"] * 4 + ["fp32_class"] + ["fp64_class"] * 2
     X, steps = PM.run_schedule(w.A, H.x0_moore_penrose(w.A, alpha), classes, finish="order18")
     assert rel(X, pinv_closed_form(w)) <= 1e-12
+
+
+@pytest.fixture(scope="module")
+def drazin_family():
+    return W.drazin_index2(128, 32, seed=2)
+
+
+def _drazin_schedule(d, classes):
+    X, steps = PM.run_schedule(d.A, H.x0_drazin(d.A, 2), classes, drazin_index=2)
+    if not np.all(np.isfinite(X)):
+        return np.inf, steps
+    return rel(X, drazin_closed_form(d)), steps
+
+
+def test_drazin_fp32_class_growth_loops_then_fp64_class(drazin_family):
+    err, steps = _drazin_schedule(drazin_family, ["fp32_class"] * 3 + ["fp64_class"] * 2)
+    ref, _ = _drazin_schedule(drazin_family, ["fp64_class"] * 5)
+    assert ref <= 1e-13
+    assert err <= 1e-13
+    assert steps[-1] < 1e-2   # the order-18 stop fires on the second FP64-class loop
+
+
+@pytest.mark.parametrize("first", ["fp8", "bf16"])
+def test_drazin_low_precision_first_loop_fails(drazin_family, first):
+    """After the loop that should have converged, the step grows again (the
+    first loop's rounding in the nilpotent block, amplified 18 per loop) and the
+    result misses the 1e-9 bar (FP8: it diverges)."""
+    err, steps = _drazin_schedule(drazin_family, [first] + ["fp32_class"] * 2 + ["fp64_class"] * 3)
+    assert steps[-1] > 1.0
+    assert not err <= 1e-9
