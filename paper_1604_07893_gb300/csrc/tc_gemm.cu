@@ -66,6 +66,8 @@ constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
 constexpr int TMEM_COLS = 4 * BN;
 constexpr unsigned WAIT_LIMIT = 1u << 22;   // polls before a wait gives up (about a second)
 
+enum { OUT_STORE = 1, OUT_NEG = 2, OUT_MUL = 4, OUT_S1 = 8, OUT_S2 = 16, OUT_ID = 32 };
+
 struct TcParams {
     int M, N, K;          // K = logical length (the tensor maps are zero-padded beyond it)
     int npairs;
@@ -77,7 +79,8 @@ struct TcParams {
     int grp_pair0[64], grp_npair[64];
     int chunk;            // K elements per exact accumulation
     int dint;             // diagonals 0..dint are summed exactly in int64 (Horner), -1: none
-    int ubase;            // the tile sums in TMEM are in units of 2^-ubase (row-normalised)
+    int ubase;            // the Horner sums are in units of 2^-ubase (row-normalised)
+    int hshift;           // the final fixed-point tile sums are in units of 2^-(ubase + hshift)
     int exact;            // 1: slices on power-of-two grids (integer-valued products)
     int S;                // slices per operand (tensor-map slice index = instance * S + s)
     int batch;            // instances; instance b uses every FP64 matrix at +b*stride
@@ -85,6 +88,11 @@ struct TcParams {
     int sym;              // output symmetric (M == N): only tiles with nb >= mb, mirrored
     int tiles_m, tiles_n;
     Epilogue epi;
+    // per output: which terms of out = a_acc acc + a_s1 s1 + a_s2 s2 + a_id I
+    // are present, as integer flags (OUT_*), so that the final pass tests no
+    // FP64 value: on GB300 every FP64 instruction -- a compare included -- holds
+    // a sub-partition's FP64 unit for about 64 clocks per warp
+    int okind[3];
     int* err;             // device error word (0 = ok)
     unsigned wait_limit;  // polls before a wait of the main loop gives up
     // bit patterns of the row maxima of op(A) and of the column maxima of op(B)
@@ -107,10 +115,9 @@ __device__ __forceinline__ void tile_coords(int t, int tm, int sym, int& mb, int
 __device__ __forceinline__ int exponent_of(unsigned long long bits) {
     const int bexp = (int)((bits >> 52) & 0x7FF);
     if (bexp) return bexp - 1022;
-    int e = 0;   // zero or subnormal
-    const double v = __longlong_as_double((long long)bits);
-    if (v > 0.0) frexp(v, &e);
-    return e;
+    // zero or subnormal (m 2^-1074, 1 <= m < 2^52): 2^(p-1074) <= x < 2^(p-1073)
+    const unsigned long long m = bits & 0xFFFFFFFFFFFFFull;
+    return m ? (63 - __clzll((long long)m)) - 1073 : 0;
 }
 __device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i) { return exponent_of(mx[i]); }
 
@@ -119,6 +126,56 @@ __device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i
 __device__ __forceinline__ double scale_pow2(double a, int e) {
     if (e >= -1022 && e <= 1023) return a * __longlong_as_double((long long)(e + 1023) << 52);
     return ldexp(a, e);
+}
+
+// V 2^E for a 64-bit signed fixed-point value, rounded to nearest (ties to
+// even), assembled from integer operations: GB300 issues about two FP64
+// instructions per clock per SM, and the final pass of every tile would
+// otherwise spend most of its time on the conversion and the scaling.  A
+// result outside the normal range (subnormal, overflow; e.g. a NaN or infinity
+// in a row maximum, whose exponent is huge) takes ldexp on the FP64 pipe.
+// Out of line, so that the compiler cannot evaluate the FP64 conversion on
+// every call and discard it (predication).
+__device__ __noinline__ double fixed_to_double_slow(long long V, int E) { return ldexp((double)V, E); }
+__device__ __noinline__ double float_to_double_slow(uint32_t f) { return (double)__uint_as_float(f); }
+
+__device__ __forceinline__ double fixed_to_double(long long V, int E) {
+    if (V == 0) return 0.0;
+    const unsigned long long sign = (unsigned long long)V & 0x8000000000000000ull;
+    const unsigned long long u = V < 0 ? 0ull - (unsigned long long)V : (unsigned long long)V;
+    const int p = 63 - __clzll((long long)u);            // 2^p <= u < 2^(p+1)
+    unsigned long long m;                                 // 53-bit significand (may round up to 2^53)
+    if (p > 52) {
+        const int sh = p - 52;
+        m = u >> sh;
+        const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+        if (rem > half || (rem == half && (m & 1ull))) ++m;
+    } else {
+        m = u << (52 - p);
+    }
+    const int be = p + E + 1023;                          // biased exponent
+    if (be < 1 || be > 2045) return fixed_to_double_slow(V, E);
+    // m = 2^53 after rounding carries into the exponent field: still exact
+    return __longlong_as_double((long long)(sign | (((unsigned long long)be << 52) + (m - (1ull << 52)))));
+}
+
+// The double of an FP32 bit pattern (exact), by integer operations for normal
+// values.
+__device__ __forceinline__ double float_bits_to_double(uint32_t f) {
+    const uint32_t ex = (f >> 23) & 0xFFu;
+    if (ex == 0 || ex == 0xFFu) return float_to_double_slow(f);   // zero, subnormal, inf, NaN
+    const unsigned long long bits = ((unsigned long long)(f & 0x80000000u) << 32) |
+                                    ((unsigned long long)(ex - 127 + 1023) << 52) |
+                                    ((unsigned long long)(f & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)bits);
+}
+
+// a_acc * a, the coefficient given by its flags: +1 and -1 (the only ones the
+// chain uses) without an FP64 instruction.
+__device__ __forceinline__ double times_coef(int kind, double c, double a) {
+    if (kind & OUT_NEG) return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ull);
+    if (kind & OUT_MUL) return c * a;
+    return a;
 }
 
 // ------------------------------------------------------------------ PTX helpers
@@ -274,7 +331,7 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
         __syncwarp();
     }
     const bool rowok = row < P.M;
-    const int erow = ((rmax && rowok) ? grid_exponent(rmax, row) : 0) - P.ubase;
+    const int erow = ((rmax && rowok) ? grid_exponent(rmax, row) : 0) - P.ubase - P.hshift;
     const double* s1 = (E.s1 && rowok) ? E.s1 + (size_t)row * E.ld1 : nullptr;
     const double* s2 = (E.s2 && rowok) ? E.s2 + (size_t)row * E.ld2 : nullptr;
     const bool norms = E.partials != nullptr;
@@ -289,12 +346,10 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
         double a[8], v1[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            a[j] = __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]);
-            if (rmax) {
-                const int e = erow + ecol[c + j];
-                a[j] = (e >= -1022 && e <= 1023) ? a[j] * __longlong_as_double((long long)(e + 1023) << 52)
-                                                 : ldexp(a[j], e);
-            }
+            // the tile sum: fixed point (exact modes) or FP32 bits (BF16)
+            a[j] = P.exact ? fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
+                                             erow + (rmax ? ecol[c + j] : 0))
+                           : float_bits_to_double(r[2 * j]);
             v1[j] = (s1 && j < ncol) ? s1[cb + j] : 0.0;
         }
         const bool diag = cb < row0w + 32 && cb + 8 > row0w;   // the diagonal crosses this group
@@ -303,15 +358,16 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
         for (int o = 0; o < 3; ++o) {
             if (o < E.nout) {
                 const EpiTerm& t = E.o[o];
-                double* out = t.out ? t.out + (size_t)row * t.ld + cb : nullptr;
-                const bool use_s1 = t.a_s1 != 0.0, use_s2 = t.a_s2 != 0.0 && s2 != nullptr;
+                const int kind = P.okind[o];
+                double* out = (kind & OUT_STORE) ? t.out + (size_t)row * t.ld + cb : nullptr;
+                const bool use_s2 = (kind & OUT_S2) && s2 != nullptr;
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
                     if (j < ncol) {
-                        double v = t.a_acc == 1.0 ? a[j] : t.a_acc * a[j];
-                        if (use_s1) v = fma(t.a_s1, v1[j], v);
+                        double v = times_coef(kind, t.a_acc, a[j]);
+                        if (kind & OUT_S1) v = fma(t.a_s1, v1[j], v);
                         if (use_s2) v = fma(t.a_s2, s2[cb + j], v);
-                        if (diag && j == dg) v += t.a_id;
+                        if ((kind & OUT_ID) && diag && j == dg) v += t.a_id;
                         if (out) {
                             out[j] = v;
                             if (mirror) t.out[(size_t)(cb + j) * t.ld + row] = v;   // warp-coalesced
@@ -340,7 +396,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     uint64_t* accf = empty + STAGES;
     uint64_t* acce = accf + 2;
     uint64_t* drain = acce + 2;   // completion of every MMA the issuer launched
-    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(drain + 1);
+    uint64_t* tdone = drain + 1;  // every epilogue warp has finished with TMEM
+    uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tdone + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -361,6 +418,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 32 * EPI_WARPS); }
         mbar_init(drain, 1);
+        mbar_init(tdone, EPI_WARPS);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -472,10 +530,15 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         // sums are added to the running sums of the tile in TMEM columns
         // [2BN, 4BN) (once per diagonal, or every 127 drains).  Diagonals 0..dint go into
         // an exact int64 by Horner's rule (C <- 256 C + I_d on the integer
-        // pipe; the host picks dint so that |C| < 2^62); at the end of diagonal
-        // dint C becomes one FP64 value, and later (tiny) diagonals are added in
-        // FP64.  This keeps FP64 instructions -- about 2 per clock per SM on
-        // GB300 -- out of all but the last flushes.
+        // pipe; the host picks dint so that |C| < 2^62).  The later diagonals
+        // (2^-8(d-dint) of the unit and smaller) are summed in FP32 registers,
+        // whose rounding lies far below the truncation of the slice pairs, and
+        // after the last unit the tile sum becomes one fixed-point integer
+        // V = C 2^h + round(F 2^h) (units 2^-(ubase+h), |V| < 2^62).  The final
+        // pass turns V into a double with integer operations; FP64
+        // instructions -- about 2 per clock per SM on GB300 -- are left to the
+        // fused combination only.  BF16 products (one unit) keep the FP32
+        // accumulator bits.
         const int lg = warp & 3;                 // TMEM lane group of this warp
         const int half = (warp - 2) >> 2;        // which BN/2 columns of the tile
         const int ew = warp - 2;                 // epilogue warp index
@@ -517,7 +580,10 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 tc_fence_after();
                 const uint32_t taddr = lane_base + buf * BN + half * EPI_COLS;
                 const int uexp = 14 + 8 * d;   // slice products q q' 2^-(14+8d): accumulator / unit
-                const float unit = P.exact ? ldexpf(1.0f, uexp) : 1.0f;
+                const bool horner = P.exact && d <= P.dint;
+                // exact diagonals: the accumulator in integer units; later ones:
+                // FP32 in units of 2^-ubase
+                const float unit = ldexpf(1.0f, horner ? uexp : P.ubase);
                 {
                     // the whole drain in one load; the accumulator goes back to the
                     // MMA issuer before the conversion work
@@ -527,53 +593,65 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     mbar_arrive(&acce[buf]);
 #pragma unroll
                     for (int j = 0; j < EPI_COLS; ++j) {
-                        if (P.exact) iacc[j] += __float2int_rn(__uint_as_float(r[j]) * unit);
+                        if (horner) iacc[j] += __float2int_rn(__uint_as_float(r[j]) * unit);
+                        else if (P.exact) iacc[j] = __float_as_int(fmaf(__uint_as_float(r[j]), unit, __int_as_float(iacc[j])));
                         else iacc[j] = (int)r[j];   // one drain only: keep the FP32 bits
                     }
                 }
                 accphase[buf] ^= 1;
                 buf ^= 1;
+                const bool last = u + 1 == units;
                 const bool diag_done =
-                    (u + 1 == units) || (P.pair_s[P.grp_pair0[(u + 1) / kchunks]] +
-                                         P.pair_t[P.grp_pair0[(u + 1) / kchunks]] != d);
-                if (diag_done || ++ndrain == 127) {   // add the int32 sums to the tile sums in TMEM
-                    ndrain = 0;
-                    const bool horner = P.exact && d <= P.dint;
-                    const bool shift = horner && have64 && d != hdiag;       // first flush of diagonal d > 0
-                    const bool to_fp64 = horner && diag_done && d == P.dint;  // C is complete: one FP64 value
-                    // FP64 flush of a diagonal past dint: I_d 2^-(14+8d) in units of 2^-ubase
-                    const double sc = scale_pow2(1.0, P.ubase - uexp);
+                    last || (P.pair_s[P.grp_pair0[(u + 1) / kchunks]] + P.pair_t[P.grp_pair0[(u + 1) / kchunks]] != d);
+                const long long hmul = 1LL << P.hshift;
+                if (horner) {
+                    if (diag_done || ++ndrain == 127) {   // add the int32 sums to the Horner sums in TMEM
+                        ndrain = 0;
+                        const bool shift = have64 && d != hdiag;   // first flush of diagonal d > 0
 #pragma unroll
-                    for (int c = 0; c < EPI_COLS; c += 16) {
-                        uint32_t r[32];
-                        if (have64) tmem_ld32_raw(acc64 + 2 * c, r);
+                        for (int c = 0; c < EPI_COLS; c += 16) {
+                            uint32_t r[32];
+                            if (have64) tmem_ld32_raw(acc64 + 2 * c, r);
 #pragma unroll
-                        for (int j = 0; j < 16; ++j) {
-                            if (horner) {
+                            for (int j = 0; j < 16; ++j) {
                                 long long C = have64 ? (long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j])
                                                      : 0LL;
                                 if (shift) C *= 256;
                                 C += iacc[c + j];
-                                if (to_fp64) {
-                                    const double v = (double)C;   // units 2^-(14+8 dint) = 2^-ubase
-                                    r[2 * j] = (uint32_t)__double2loint(v);
-                                    r[2 * j + 1] = (uint32_t)__double2hiint(v);
-                                } else {
-                                    r[2 * j] = (uint32_t)(unsigned long long)C;
-                                    r[2 * j + 1] = (uint32_t)((unsigned long long)C >> 32);
-                                }
-                            } else {
-                                const double o = have64 ? __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]) : 0.0;
-                                const double nw = P.exact ? fma((double)iacc[c + j], sc, o)
-                                                          : o + (double)__int_as_float(iacc[c + j]);
-                                r[2 * j] = (uint32_t)__double2loint(nw);
-                                r[2 * j + 1] = (uint32_t)__double2hiint(nw);
+                                if (last) C *= hmul;   // every diagonal was exact: the final fixed point
+                                r[2 * j] = (uint32_t)(unsigned long long)C;
+                                r[2 * j + 1] = (uint32_t)((unsigned long long)C >> 32);
                             }
+                            tmem_st32_raw(acc64 + 2 * c, r);
                         }
-                        tmem_st32_raw(acc64 + 2 * c, r);
+                        have64 = true;
+                        hdiag = d;
                     }
-                    have64 = true;
-                    hdiag = d;
+                } else {
+                    ndrain = 1;   // FP32 sums run on to the last unit without a flush
+                    if (last) {   // V = C 2^h + round(F 2^h), or the FP32 bits of a BF16 product
+                        const float fh = ldexpf(1.0f, P.hshift);
+#pragma unroll
+                        for (int c = 0; c < EPI_COLS; c += 16) {
+                            uint32_t r[32];
+                            if (have64) tmem_ld32_raw(acc64 + 2 * c, r);
+#pragma unroll
+                            for (int j = 0; j < 16; ++j) {
+                                if (P.exact) {
+                                    long long V = have64 ? (long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j])
+                                                         : 0LL;
+                                    V = V * hmul + __float2ll_rn(__int_as_float(iacc[c + j]) * fh);
+                                    r[2 * j] = (uint32_t)(unsigned long long)V;
+                                    r[2 * j + 1] = (uint32_t)((unsigned long long)V >> 32);
+                                } else {
+                                    r[2 * j] = (uint32_t)iacc[c + j];
+                                    r[2 * j + 1] = 0u;
+                                }
+                            }
+                            tmem_st32_raw(acc64 + 2 * c, r);
+                        }
+                        have64 = true;
+                    }
                 }
             }
             if (!ok) break;
@@ -584,7 +662,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             } else {
                 // fused FP64 epilogue for this row of the tile, 16 columns at a time
                 const int row = m0 + row_in_tile;
-                const int ei = (rmax && row < P.M) ? grid_exponent(rmax, row) : 0;
+                const int ei = ((rmax && row < P.M) ? grid_exponent(rmax, row) : 0) - P.ubase - P.hshift;
                 const double* s1 = (E.s1 && row < P.M) ? E.s1 + (size_t)row * E.ld1 : nullptr;
                 const double* s2 = (E.s2 && row < P.M) ? E.s2 + (size_t)row * E.ld2 : nullptr;
                 // FP64 instructions are scarce: terms with a zero coefficient are
@@ -600,19 +678,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     for (int j = 0; j < 16; ++j) {
                         const int col = n0 + half * EPI_COLS + c + j;
                         if (col < P.N) {
-                            double a = __hiloint2double((int)r[2 * j + 1], (int)r[2 * j]);
-                            if (rmax) a = scale_pow2(a, ei + grid_exponent(cmax, col) - P.ubase);
+                            const double a =
+                                P.exact ? fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
+                                                          ei + (rmax ? grid_exponent(cmax, col) : 0))
+                                        : float_bits_to_double(r[2 * j]);
                             const double v1 = s1 ? s1[col] : 0.0;
                             const double v2 = s2 ? s2[col] : 0.0;
     #pragma unroll
                             for (int o = 0; o < 3; ++o) {
                                 if (o < E.nout) {
                                     const EpiTerm& t = E.o[o];
-                                    double v = t.a_acc * a;
-                                    if (t.a_s1 != 0.0) v = fma(t.a_s1, v1, v);
-                                    if (t.a_s2 != 0.0) v = fma(t.a_s2, v2, v);
-                                    if (row == col) v += t.a_id;
-                                    if (t.out) {
+                                    const int kind = P.okind[o];
+                                    double v = times_coef(kind, t.a_acc, a);
+                                    if (kind & OUT_S1) v = fma(t.a_s1, v1, v);
+                                    if (kind & OUT_S2) v = fma(t.a_s2, v2, v);
+                                    if ((kind & OUT_ID) && row == col) v += t.a_id;
+                                    if (kind & OUT_STORE) {
                                         t.out[(size_t)row * t.ld + col] = v;
                                         if (mirror) t.out[(size_t)col * t.ld + row] = v;   // warp-coalesced
                                     }
@@ -635,12 +716,22 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 }
             }
         }
+        // this warp is done with TMEM (normal end or abort): tell the deallocator
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tdone);
     }
 
     __syncwarp();
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
+        // The CTA barrier above is not relied on to order the epilogue warps'
+        // last TMEM loads before the release (measured: the producer and MMA
+        // warps can leave it while the epilogue warps are still in their final
+        // pass); the release waits for every epilogue warp's arrival instead.
+        if (lane == 0 && !mbar_wait(tdone, 0)) record_error(P.err, 7);
+        __syncwarp();
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS));
     }
@@ -967,15 +1058,35 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
             p0 = p1;
         }
     }
-    // Horner in int64 up to the last diagonal d with |C| <= 1.01 K 2^(14+8d) < 2^62
+    // Horner in int64 up to the last diagonal d with |C| <= 1.05 K 2^(14+8d) < 2^62
+    // (the sum over the diagonals is below 1.01 K 2^(14+8d); the margin also
+    // covers the FP32 sums of the later diagonals, < 0.03 K 2^(14+8 dint));
+    // then the largest shift h that keeps V = C 2^h + F 2^h below 2^62
     P.dint = -1;
     if (mode.exact)
         for (int d = 0; d <= mode.L; ++d)
-            if (1.01 * (double)K * std::ldexp(1.0, 14 + 8 * d) < std::ldexp(1.0, 62)) P.dint = d;
+            if (1.05 * (double)K * std::ldexp(1.0, 14 + 8 * d) < std::ldexp(1.0, 62)) P.dint = d;
     P.ubase = mode.exact ? 14 + 8 * std::max(P.dint, 0) : 0;
+    P.hshift = 0;
+    if (mode.exact)
+        while (P.hshift < 40 && 1.05 * (double)K * std::ldexp(1.0, P.ubase + P.hshift + 1) < std::ldexp(1.0, 62))
+            ++P.hshift;
     P.tiles_m = (M + BM - 1) / BM;
     P.tiles_n = (N + BN - 1) / BN;
     P.epi = epi;
+    for (int o = 0; o < 3; ++o) {
+        const EpiTerm& t = epi.o[o];
+        int k = 0;
+        if (o < epi.nout) {
+            if (t.out) k |= OUT_STORE;
+            if (t.a_acc == -1.0) k |= OUT_NEG;
+            else if (t.a_acc != 1.0) k |= OUT_MUL;
+            if (t.a_s1 != 0.0) k |= OUT_S1;
+            if (t.a_s2 != 0.0 && epi.s2) k |= OUT_S2;
+            if (t.a_id != 0.0) k |= OUT_ID;
+        }
+        P.okind[o] = k;
+    }
     P.err = err;
     P.wait_limit = wait_limit ? wait_limit : WAIT_LIMIT;
     P.rmax = mode.exact ? ea : nullptr;
