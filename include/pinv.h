@@ -54,6 +54,8 @@ extern "C" {
 #define PINV_ERR_TIMEOUT    -6   /* a bounded device-side wait gave up            */
 #define PINV_ERR_CUDA       -7   /* a CUDA runtime call failed                    */
 #define PINV_ERR_UNKNOWN_ID -8   /* pinv_poll: no such request                     */
+#define PINV_ERR_BUSY       -9   /* pinv_submit: the admission queue is full (the
+                                    request is rejected; nothing was queued)       */
 
 /* ------------------------------------------------------------------ enums */
 typedef enum {
@@ -134,8 +136,25 @@ typedef enum {
 typedef struct {
     size_t hbm_budget_bytes; /* cap on the handle's workspace; 0 = no cap           */
     int    device;           /* CUDA device ordinal                                 */
-    int    reserved[6];
+    int    max_queued;       /* serving: requests waiting for admission at most;
+                                pinv_submit rejects further ones with
+                                PINV_ERR_BUSY until admission drains the queue.
+                                0 = no cap (the queue grows with the backlog)      */
+    int    reserved[5];
 } pinv_config;
+
+/* Counters of the serving loop (pinv_serving_stats). */
+typedef struct {
+    uint64_t submitted;      /* pinv_submit calls that queued a request            */
+    uint64_t rejected;       /* pinv_submit calls refused with PINV_ERR_BUSY      */
+    uint64_t admitted;       /* requests moved from the queue into running groups  */
+    uint64_t completed;      /* requests whose final status is known               */
+    int      queued;         /* waiting for admission now (the backlog)            */
+    int      running;        /* admitted and not yet completed                     */
+    int      groups;         /* running groups (one stream each)                   */
+    int      reserved;
+    size_t   device_bytes;   /* device memory held by the running groups           */
+} pinv_serving_counters;
 
 typedef struct {
     int m, n;                /* A is m x n; X and G are n x m                       */
@@ -296,7 +315,9 @@ int  pinv_solve_batched(pinv_handle *h, int count, const pinv_desc *descs, void 
  * id.  The descriptor is copied; A, G and X must stay valid until pinv_poll
  * reports a final status.  Moore-Penrose and general-G problems with device
  * buffers (PINV_ERR_ARG otherwise); PINV_ERR_BUDGET if the problem's device
- * memory alone exceeds the handle's HBM budget.  Thread-safe with pinv_poll.
+ * memory alone exceeds the handle's HBM budget; PINV_ERR_BUSY (rejected, not
+ * queued) when cfg->max_queued requests are already waiting for admission.
+ * Thread-safe with pinv_poll.
  * Each group of requests runs on its own stream (by priority: smaller problems
  * first).  With the CUDA default of eight hardware queues, streams beyond
  * eight share queues and a small group's kernels can wait behind a large
@@ -314,6 +335,13 @@ int  pinv_submit(pinv_handle *h, const pinv_desc *desc, uint64_t *request_id);
  * the request is then forgotten.  Results equal a lone pinv_solve of the same
  * request up to the rounding of the padded shape. */
 int  pinv_poll(pinv_handle *h, uint64_t request_id, pinv_info *info);
+
+/* Counters of the handle's serving loop: submitted, rejected (PINV_ERR_BUSY),
+ * admitted and completed requests since pinv_init, and the current backlog
+ * (queued), admitted requests still computing, their groups and the device
+ * memory those hold.  Thread-safe with pinv_submit / pinv_poll.  No
+ * counterpart in the paper (serving is this library's). */
+int  pinv_serving_stats(pinv_handle *h, pinv_serving_counters *stats);
 
 /* Section 4's scaling for rectangular A: *alpha = 1/(||A||_1 ||A||_inf),
  * computed on the device; desc->A (device) and shape are read. */

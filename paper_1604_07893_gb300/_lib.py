@@ -16,7 +16,8 @@ LIB_PATH = os.path.join(HERE, "libpinv.so")
 
 PINV_OK, PINV_PENDING = 0, 1
 ERRORS = {-1: "PINV_ERR_ARG", -2: "PINV_ERR_BUDGET", -3: "PINV_ERR_NONFINITE", -4: "PINV_ERR_DIVERGED",
-          -5: "PINV_ERR_MAXITER", -6: "PINV_ERR_TIMEOUT", -7: "PINV_ERR_CUDA", -8: "PINV_ERR_UNKNOWN_ID"}
+          -5: "PINV_ERR_MAXITER", -6: "PINV_ERR_TIMEOUT", -7: "PINV_ERR_CUDA", -8: "PINV_ERR_UNKNOWN_ID",
+          -9: "PINV_ERR_BUSY"}
 KIND = {"moore_penrose": 0, "drazin": 1, "outer_g": 2, "drazin_normal": 3}
 STOP = {"rel_fro": 0, "paper": 1, "order18": 2}
 PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3, "fp64_tc": 4, "bf16_fp32": 5}
@@ -27,12 +28,19 @@ HISTORY = 128
 EXPORTS = ("pinv_init", "pinv_destroy", "pinv_solve", "pinv_solve_complex", "pinv_preconditioner",
            "pinv_solve_batched", "pinv_submit",
            "pinv_poll", "pinv_alpha_estimate", "pinv_step", "pinv_gemm", "pinv_autotune", "pinv_drazin_index",
-           "pinv_step_noalloc", "pinv_set_wait_limit")
+           "pinv_step_noalloc", "pinv_set_wait_limit", "pinv_serving_stats")
 NOALLOC_MAX_DIM = 128
 
 
 class Config(C.Structure):
-    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("device", C.c_int), ("reserved", C.c_int * 6)]
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("device", C.c_int), ("max_queued", C.c_int),
+                ("reserved", C.c_int * 5)]
+
+
+class ServingStats(C.Structure):
+    _fields_ = [("submitted", C.c_uint64), ("rejected", C.c_uint64), ("admitted", C.c_uint64),
+                ("completed", C.c_uint64), ("queued", C.c_int), ("running", C.c_int), ("groups", C.c_int),
+                ("reserved", C.c_int), ("device_bytes", C.c_size_t)]
 
 
 class Desc(C.Structure):
@@ -109,6 +117,7 @@ def load() -> C.CDLL:
     lib.pinv_step_noalloc.argtypes = [C.c_int, C.c_int, C.c_void_p, C.c_int, C.c_void_p,
                                       C.c_void_p, C.c_int, C.c_int, C.c_void_p, P(C.c_double)]
     lib.pinv_set_wait_limit.argtypes = [C.c_void_p, C.c_uint]
+    lib.pinv_serving_stats.argtypes = [C.c_void_p, P(ServingStats)]
     for name in EXPORTS:
         if name != "pinv_destroy":
             getattr(lib, name).restype = C.c_int
@@ -142,11 +151,11 @@ def _dev_ptr(t, cplx: bool = False) -> int:
 class Handle:
     """pinv_init / pinv_destroy."""
 
-    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, max_queued: int = 0):
         lib = load()
         self._lib = lib
         self._h = C.c_void_p()
-        cfg = Config(hbm_budget_bytes=hbm_budget_bytes, device=device)
+        cfg = Config(hbm_budget_bytes=hbm_budget_bytes, device=device, max_queued=max_queued)
         rc = lib.pinv_init(C.byref(self._h), C.byref(cfg))
         if rc != PINV_OK:
             raise PinvError(rc, "pinv_init")
@@ -287,6 +296,14 @@ class Handle:
         if rc != PINV_OK:
             raise PinvError(rc, "pinv_submit")
         return rid.value
+
+    def serving_stats(self) -> dict:
+        """pinv_serving_stats: counters of the serving loop and its backlog."""
+        st = ServingStats()
+        rc = self._lib.pinv_serving_stats(self._h, C.byref(st))
+        if rc != PINV_OK:
+            raise PinvError(rc, "pinv_serving_stats")
+        return {k: getattr(st, k) for k, _ in ServingStats._fields_ if k != "reserved"}
 
     def poll(self, rid: int):
         """Returns None while pending, else (status, info dict)."""

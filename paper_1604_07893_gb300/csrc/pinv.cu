@@ -116,6 +116,9 @@ struct pinv_handle {
         std::chrono::steady_clock::time_point t_submit;
     };
     std::deque<uint64_t> queue;                 // submitted, not yet admitted
+    int max_queued = 0;                         // admission-queue cap (0: none)
+    uint64_t n_submitted = 0, n_rejected = 0, n_admitted = 0, n_completed = 0;
+    int n_running = 0;                          // admitted requests not yet completed
     std::map<uint64_t, Request> requests;
     struct Running;                             // a group of admitted requests on the device
     std::vector<std::unique_ptr<Running>> running;
@@ -1636,7 +1639,12 @@ int run_groups(std::vector<std::unique_ptr<Group>>& groups) {
         if (int r = group_finish_issue(*g)) { if (!g->err) g->err = r; rc = r; }
     for (auto& g : groups) {
         if (!g->err && g->finish && cudaStreamSynchronize(g->st) != cudaSuccess) rc = g->err = PINV_ERR_CUDA;
-        for (auto& I : g->info) if (g->err && I.status == PINV_OK) I.status = g->err;
+        for (auto& I : g->info) {
+            if (g->err && I.status == PINV_OK) I.status = g->err;
+            I.gemms = g->c.gemms;   // each instance's share of the group's executed work
+            I.gemm_flops = g->c.gemm_flops / g->batch;
+            I.tensor_flops = g->c.tensor_flops / g->batch;
+        }
         g->release();
     }
     return rc;
@@ -1703,10 +1711,13 @@ int serve_round(pinv_handle* h) {
             }
             r->bytes = bytes;
             const int rc = group_begin(*r->g);
+            h->n_admitted += r->ids.size();
             if (rc) {
                 for (uint64_t id : r->ids) { h->requests[id].status = rc; h->requests[id].info.status = rc; }
+                h->n_completed += r->ids.size();
                 r->g->release();
             } else {
+                h->n_running += (int)r->ids.size();
                 h->serving_bytes += bytes;
                 h->running.push_back(std::move(r));
             }
@@ -1741,10 +1752,17 @@ int serve_round(pinv_handle* h) {
             if (G.err && q.info.status == PINV_OK) q.info.status = G.err;
             if (!G.done[j] && q.info.status == PINV_OK) q.info.status = PINV_ERR_MAXITER;
             q.info.ms = std::chrono::duration<float, std::milli>(now - q.t_submit).count();
+            // the group's products ran for all its requests in lockstep: each
+            // request's share of the executed work
+            q.info.gemms = G.c.gemms;
+            q.info.gemm_flops = G.c.gemm_flops / G.batch;
+            q.info.tensor_flops = G.c.tensor_flops / G.batch;
             q.status = q.info.status;
         }
         G.release();
         h->serving_bytes -= r->bytes;
+        h->n_completed += r->ids.size();
+        h->n_running -= (int)r->ids.size();
         h->running.erase(h->running.begin() + i);
     }
     return PINV_OK;
@@ -1760,6 +1778,7 @@ int pinv_init(pinv_handle** out, const pinv_config* cfg) {
     pinv_handle* h = new pinv_handle();
     h->device = cfg ? cfg->device : 0;
     h->budget = cfg ? cfg->hbm_budget_bytes : 0;
+    h->max_queued = cfg && cfg->max_queued > 0 ? cfg->max_queued : 0;
     cudaError_t e = cudaSetDevice(h->device);
     if (e == cudaSuccess) e = cudaMallocHost(&h->pinned, 64 * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&h->dsmall, 64 * sizeof(double));
@@ -1884,6 +1903,11 @@ int pinv_submit(pinv_handle* h, const pinv_desc* desc, uint64_t* id) {
                                     desc->finish == PINV_FINISH_CLEAN, desc->kind == PINV_OUTER_G);
     if (h->budget && need > h->budget) return PINV_ERR_BUDGET;
     std::lock_guard<std::mutex> lk(h->mu);
+    if (h->max_queued && (int)h->queue.size() >= h->max_queued) {
+        ++h->n_rejected;
+        return PINV_ERR_BUSY;
+    }
+    ++h->n_submitted;
     *id = h->next_id++;
     pinv_handle::Request r;
     r.desc = *desc;
@@ -1907,6 +1931,21 @@ int pinv_poll(pinv_handle* h, uint64_t id, pinv_info* info) {
     if (info) *info = it->second.info;
     h->requests.erase(it);
     return st;
+}
+
+int pinv_serving_stats(pinv_handle* h, pinv_serving_counters* out) {
+    if (!h || !out) return PINV_ERR_ARG;
+    std::lock_guard<std::mutex> lk(h->mu);
+    std::memset(out, 0, sizeof(*out));
+    out->submitted = h->n_submitted;
+    out->rejected = h->n_rejected;
+    out->admitted = h->n_admitted;
+    out->completed = h->n_completed;
+    out->queued = (int)h->queue.size();
+    out->running = h->n_running;
+    out->groups = (int)h->running.size();
+    out->device_bytes = h->serving_bytes;
+    return PINV_OK;
 }
 
 int pinv_alpha_estimate(pinv_handle* h, const pinv_desc* d, void* stream, double* alpha) {

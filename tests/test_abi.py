@@ -38,8 +38,8 @@ def test_struct_sizes_match_the_header():
     src = r'''
 #include <stdio.h>
 #include "pinv.h"
-int main(void) { printf("%zu %zu %zu %zu\n", sizeof(pinv_config), sizeof(pinv_desc), sizeof(pinv_info),
-                        sizeof(pinv_precond_desc)); return 0; }
+int main(void) { printf("%zu %zu %zu %zu %zu\n", sizeof(pinv_config), sizeof(pinv_desc), sizeof(pinv_info),
+                        sizeof(pinv_precond_desc), sizeof(pinv_serving_counters)); return 0; }
 '''
     with tempfile.TemporaryDirectory() as d:
         c = os.path.join(d, "s.c")
@@ -48,7 +48,8 @@ int main(void) { printf("%zu %zu %zu %zu\n", sizeof(pinv_config), sizeof(pinv_de
         subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     assert [int(x) for x in out] == [ctypes.sizeof(_lib.Config), ctypes.sizeof(_lib.Desc),
-                                     ctypes.sizeof(_lib.Info), ctypes.sizeof(_lib.PrecondDesc)]
+                                     ctypes.sizeof(_lib.Info), ctypes.sizeof(_lib.PrecondDesc),
+                                     ctypes.sizeof(_lib.ServingStats)]
 
 
 def test_every_field_offset_matches_the_header():
@@ -58,7 +59,7 @@ def test_every_field_offset_matches_the_header():
     import subprocess
     import tempfile
     structs = {"pinv_config": _lib.Config, "pinv_desc": _lib.Desc, "pinv_info": _lib.Info,
-               "pinv_precond_desc": _lib.PrecondDesc}
+               "pinv_precond_desc": _lib.PrecondDesc, "pinv_serving_counters": _lib.ServingStats}
     lines = []
     for cname, cls in structs.items():
         for fname, _ in cls._fields_:
@@ -95,6 +96,7 @@ int use(void) {
     r |= pinv_gemm(h, 1, 1, 1, 0, 1, 0, 0, 1, 0, 0, 1, PINV_PREC_FP64, 0);
     r |= pinv_drazin_index(h, 1, 0, 1, 2, 0, &ix, ranks) | pinv_autotune(h, 0, &co);
     r |= pinv_step_noalloc(1, 1, 0, 1, 0, 0, 1, 0, 0, &a);
+    { pinv_serving_counters st; r |= pinv_serving_stats(h, &st) | pinv_set_wait_limit(h, 0u); }
     pinv_destroy(h);
     return r;
 }

@@ -107,3 +107,32 @@ def test_budget_admission_and_rejection(cuda):
         assert done[i][0] == 0
         assert rel(X.cpu().numpy(), spd_inverse(s)) <= 1e-9
     h.close()
+
+
+def test_admission_queue_cap_rejects_and_counts(cuda):
+    """max_queued bounds the backlog: submissions beyond it are rejected with
+    PINV_ERR_BUSY and counted; admitted requests still complete correctly and
+    the counters add up (submitted = completed at the end, none queued)."""
+    from paper_1604_07893_gb300 import Handle, PinvError
+    h = Handle(0, max_queued=3)
+    reqs = [make_request(128, seed=40 + i) for i in range(8)]
+    ids, rejected = [], 0
+    for s, A, G, X in reqs:
+        try:
+            ids.append((h.submit(A, X, G=G, kind="outer_g", alpha=1.0 / s.lam.max(), tol=1e-12,
+                                 prec="fp64_tc"), s, X))
+        except PinvError as e:
+            assert e.code == -9
+            rejected += 1
+    assert len(ids) == 3 and rejected == 5          # nothing polled yet: the queue holds 3
+    st = h.serving_stats()
+    assert st["queued"] == 3 and st["rejected"] == 5 and st["submitted"] == 3
+    done = drain(h, [i for i, _, _ in ids])
+    assert len(done) == 3
+    for i, s, X in ids:
+        assert done[i][0] == 0
+        assert rel(X.cpu().numpy(), spd_inverse(s)) <= 1e-9
+        assert done[i][1]["tensor_flops"] > 0
+    st = h.serving_stats()
+    assert st["queued"] == 0 and st["running"] == 0 and st["completed"] == 3 and st["admitted"] == 3
+    h.close()
