@@ -64,6 +64,13 @@ constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
 // TMEM columns: two FP32 MMA accumulators [0, 2BN) and the FP64 running sums of
 // the tile (two 32-bit columns per double) [2BN, 4BN).
 constexpr int TMEM_COLS = 4 * BN;
+// shared memory of the final pass: per epilogue warp a 32-row x 8-column
+// staging block of doubles (row stride 9: the row-layout writes and the
+// column-layout reads fall in different banks) and the tile's column exponents
+constexpr int STG_COLS = 8;
+constexpr int STG_LD = STG_COLS + 1;
+constexpr int STG_BYTES = EPI_WARPS * 32 * STG_LD * 8;
+constexpr int ECOL_BYTES = EPI_WARPS * EPI_COLS * 4;
 constexpr unsigned WAIT_LIMIT = 1u << 22;   // polls before a wait gives up (about a second)
 
 enum { OUT_STORE = 1, OUT_NEG = 2, OUT_MUL = 4, OUT_S1 = 8, OUT_S2 = 16, OUT_ID = 32 };
@@ -120,13 +127,6 @@ __device__ __forceinline__ int exponent_of(unsigned long long bits) {
     return m ? (63 - __clzll((long long)m)) - 1073 : 0;
 }
 __device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i) { return exponent_of(mx[i]); }
-
-// a * 2^e: one multiplication by a constructed power of two when 2^e is a
-// normal double (then it rounds exactly like ldexp), ldexp otherwise.
-__device__ __forceinline__ double scale_pow2(double a, int e) {
-    if (e >= -1022 && e <= 1023) return a * __longlong_as_double((long long)(e + 1023) << 52);
-    return ldexp(a, e);
-}
 
 // V 2^E for a 64-bit signed fixed-point value, rounded to nearest (ties to
 // even), assembled from integer operations: GB300 issues about two FP64
@@ -309,15 +309,17 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 
 // ------------------------------------------------------------------ the kernel
 // Lean final pass of one epilogue warp for one tile (used when each pair has a
-// single K-chunk: few units per tile, so this pass weighs most): its 32 rows
-// (one per lane) x EPI_COLS columns of the tile sums in TMEM (units 2^-ubase)
-// become out = a_acc acc 2^(e_i + f_j) + a_s1 s1 + a_s2 s2 + a_id I for up to
-// three outputs, plus the stop-norm partials of output 0 against s1.  It is
-// bound by instruction issue, so per element it does little: the column
-// exponents of the tile are computed once per warp (shared memory), the scale
-// is one product with the power of two 2^(e_i + f_j) formed from them, terms
-// are chosen per output, and the identity is tested only where the diagonal
-// crosses.
+// single K-chunk: few units per tile, so this pass is most of the tile's
+// latency): its 32 rows (one per lane) x EPI_COLS columns of the tile sums in
+// TMEM become out = a_acc acc 2^(e_i + f_j) + a_s1 s1 + a_s2 s2 + a_id I for up
+// to three outputs, plus the stop-norm partials of output 0 against s1,
+// directly in the TMEM row layout.  It is bound by instruction issue, so per
+// element it does little: the column exponents of the tile are computed once
+// per warp (static shared memory of the lean kernel), the doubles are
+// assembled with integer operations, terms are chosen per output, and the
+// identity is tested only where the diagonal crosses.  (On these short
+// products the shared-memory staging of the other pass costs more
+// instructions than its coalesced accesses save: measured 5-9 % slower.)
 __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogue& E, uint32_t acc64, int row,
                                                 int col0, int row0w, const unsigned long long* rmax,
                                                 const unsigned long long* cmax, int ew, bool mirror, int lane,
@@ -385,6 +387,75 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
     if (rmax) __syncwarp();   // ecol is rewritten for the next tile
 }
 
+// Final pass of one epilogue warp for one tile of a product with several
+// K-chunks: its 32 rows (one per lane) x EPI_COLS columns of the tile sums in
+// TMEM become
+//   out = a_acc acc 2^(e_i + f_j) + a_s1 s1 + a_s2 s2 + a_id I
+// for up to three outputs, plus the stop-norm partials of output 0 against s1.
+// Each group of 8 columns is converted in the TMEM row layout (lane = row;
+// the doubles are assembled with integer operations and the scale goes into
+// the exponent) and staged in shared memory; the combination then runs in a
+// column layout (a warp instruction covers 4 rows x 8 consecutive columns),
+// so that the side-input loads and the output stores are coalesced: with one
+// row per lane every access touched 32 cache lines, which dominated the pass.
+__device__ __forceinline__ void final_pass(const TcParams& P, const Epilogue& E, uint32_t acc64, int row0, int col0,
+                                           const unsigned long long* rmax, const unsigned long long* cmax,
+                                           bool mirror, int lane, double* stg, int* ecol, double& sd, double& sx) {
+    if (P.exact) {
+        for (int cc = lane; cc < EPI_COLS; cc += 32) ecol[cc] = (col0 + cc < P.N) ? grid_exponent(cmax, col0 + cc) : 0;
+        __syncwarp();
+    }
+    const int erow = (P.exact && row0 + lane < P.M) ? grid_exponent(rmax, row0 + lane) - P.ubase - P.hshift : 0;
+    const bool norms = E.partials != nullptr;
+    const int cl = lane & 7, rq = lane >> 3;   // column of the group, row quarter (column layout)
+#pragma unroll 1
+    for (int c = 0; c < EPI_COLS; c += STG_COLS) {
+        {
+            uint32_t r[16];
+            tmem_ld16_raw(acc64 + 2 * c, r);
+#pragma unroll
+            for (int j = 0; j < STG_COLS; ++j)
+                stg[lane * STG_LD + j] =
+                    P.exact ? fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
+                                              erow + ecol[c + j])
+                            : float_bits_to_double(r[2 * j]);
+        }
+        __syncwarp();
+        const int col = col0 + c + cl;
+        if (col < P.N) {
+#pragma unroll 2
+            for (int rr = rq; rr < 32; rr += 4) {
+                const int row = row0 + rr;
+                if (row >= P.M) break;
+                const double a = stg[rr * STG_LD + cl];
+                const double v1 = E.s1 ? E.s1[(size_t)row * E.ld1 + col] : 0.0;
+                const double v2 = E.s2 ? E.s2[(size_t)row * E.ld2 + col] : 0.0;
+#pragma unroll
+                for (int o = 0; o < 3; ++o) {
+                    if (o < E.nout) {
+                        const EpiTerm& t = E.o[o];
+                        const int kind = P.okind[o];
+                        double v = times_coef(kind, t.a_acc, a);
+                        if (kind & OUT_S1) v = fma(t.a_s1, v1, v);
+                        if (kind & OUT_S2) v = fma(t.a_s2, v2, v);
+                        if ((kind & OUT_ID) && row == col) v += t.a_id;
+                        if (kind & OUT_STORE) {
+                            t.out[(size_t)row * t.ld + col] = v;
+                            if (mirror) t.out[(size_t)col * t.ld + row] = v;
+                        }
+                        if (o == 0 && norms) {
+                            const double dd = v - v1;
+                            sd = fma(dd, dd, sd);
+                            sx = fma(v1, v1, sx);
+                        }
+                    }
+                }
+            }
+        }
+        __syncwarp();   // the staging block is rewritten for the next group
+    }
+}
+
 template <bool LEAN>
 __global__ void __launch_bounds__(THREADS, 1)   // 10 warps: 3 share a sub-partition (16K registers): <= 168 each
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
@@ -399,6 +470,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     uint64_t* tdone = drain + 1;  // every epilogue warp has finished with TMEM
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tdone + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
+    double* stg_all = reinterpret_cast<double*>(smem + STAGES * STAGE_BYTES + 256);
+    int* ecol_all = reinterpret_cast<int*>(smem + STAGES * STAGE_BYTES + 256 + STG_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_per = P.sym ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;
@@ -542,7 +615,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         const int lg = warp & 3;                 // TMEM lane group of this warp
         const int half = (warp - 2) >> 2;        // which BN/2 columns of the tile
         const int ew = warp - 2;                 // epilogue warp index
-        const int row_in_tile = lg * 32 + lane;
         const uint32_t lane_base = tmem + ((uint32_t)(lg * 32) << 16);
         const uint32_t acc64 = lane_base + 2 * BN + 2 * half * EPI_COLS;
         int buf = 0;
@@ -656,54 +728,12 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             if (!ok) break;
             double sd = 0.0, sx = 0.0;
-            if constexpr (LEAN) {
-                lean_final_pass(P, E, acc64, m0 + row_in_tile, n0 + half * EPI_COLS, m0 + lg * 32, rmax, cmax,
+            if constexpr (LEAN)
+                lean_final_pass(P, E, acc64, m0 + lg * 32 + lane, n0 + half * EPI_COLS, m0 + lg * 32, rmax, cmax,
                                 ew, mirror, lane, sd, sx);
-            } else {
-                // fused FP64 epilogue for this row of the tile, 16 columns at a time
-                const int row = m0 + row_in_tile;
-                const int ei = ((rmax && row < P.M) ? grid_exponent(rmax, row) : 0) - P.ubase - P.hshift;
-                const double* s1 = (E.s1 && row < P.M) ? E.s1 + (size_t)row * E.ld1 : nullptr;
-                const double* s2 = (E.s2 && row < P.M) ? E.s2 + (size_t)row * E.ld2 : nullptr;
-                // FP64 instructions are scarce: terms with a zero coefficient are
-                // skipped (warp-uniform branches), the identity is added on the
-                // diagonal only, the norms only when asked for
-                const bool norms = E.partials != nullptr;
-    #pragma unroll 1
-                for (int c = 0; c < EPI_COLS; c += 16) {
-                    uint32_t r[32];
-                    tmem_ld32_raw(acc64 + 2 * c, r);
-                    if (row >= P.M) continue;
-    #pragma unroll
-                    for (int j = 0; j < 16; ++j) {
-                        const int col = n0 + half * EPI_COLS + c + j;
-                        if (col < P.N) {
-                            const double a =
-                                P.exact ? fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
-                                                          ei + (rmax ? grid_exponent(cmax, col) : 0))
-                                        : float_bits_to_double(r[2 * j]);
-                            const double v1 = s1 ? s1[col] : 0.0;
-                            const double v2 = s2 ? s2[col] : 0.0;
-    #pragma unroll
-                            for (int o = 0; o < 3; ++o) {
-                                if (o < E.nout) {
-                                    const EpiTerm& t = E.o[o];
-                                    const int kind = P.okind[o];
-                                    double v = times_coef(kind, t.a_acc, a);
-                                    if (kind & OUT_S1) v = fma(t.a_s1, v1, v);
-                                    if (kind & OUT_S2) v = fma(t.a_s2, v2, v);
-                                    if ((kind & OUT_ID) && row == col) v += t.a_id;
-                                    if (kind & OUT_STORE) {
-                                        t.out[(size_t)row * t.ld + col] = v;
-                                        if (mirror) t.out[(size_t)col * t.ld + row] = v;   // warp-coalesced
-                                    }
-                                    if (o == 0 && norms) { const double dd = v - v1; sd = fma(dd, dd, sd); sx = fma(v1, v1, sx); }
-                                }
-                            }
-                        }
-                    }
-                }
-            }
+            else
+                final_pass(P, E, acc64, m0 + lg * 32, n0 + half * EPI_COLS, rmax, cmax, mirror, lane,
+                           stg_all + ew * 32 * STG_LD, ecol_all + ew * EPI_COLS, sd, sx);
             if (E.partials) {  // one pair per (tile, epilogue warp): no barrier between warps
 #pragma unroll
                 for (int off = 16; off; off >>= 1) {
@@ -937,6 +967,14 @@ int num_sms() {
     return g_dev[dev].sms;
 }
 
+// Dynamic shared memory of a kernel: the stages, the barriers, and (for the
+// staged final pass of multi-chunk products) the staging blocks and column
+// exponents; the lean kernel keeps its column exponents in static shared
+// memory and gives the rest to L1.
+size_t smem_bytes(bool lean) {
+    return STAGES * STAGE_BYTES + 1024 + 256 + (lean ? 0 : STG_BYTES + ECOL_BYTES);
+}
+
 // Set the kernels' shared-memory attribute once per device; false if the
 // kernel cannot launch with its block size there.
 bool prepare_kernels() {
@@ -944,8 +982,9 @@ bool prepare_kernels() {
     std::lock_guard<std::mutex> lk(g_dev_mu);
     if (g_dev[dev].attr) return true;
     const void* kernels[2] = {(const void*)tc_gemm_kernel<false>, (const void*)tc_gemm_kernel<true>};
-    for (const void* k : kernels) {
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
+    for (int i = 0; i < 2; ++i) {
+        const void* k = kernels[i];
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(i == 1));
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.maxThreadsPerBlock < THREADS) {
             std::fprintf(stderr, "tc_gemm: kernel uses %d registers; at most %d threads per block fit\n",
@@ -982,7 +1021,7 @@ size_t tc_workspace_bytes(int M, int N, int K, const TcMode& m, int batch) {
            al(8 * (size_t)batch * (M + N)) + 1024;
 }
 
-size_t tc_smem_bytes() { return STAGES * STAGE_BYTES + 1024 + 256; }
+size_t tc_smem_bytes() { return smem_bytes(false); }
 
 int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const double* B, int ldb, bool transB,
             const Epilogue& epi, const TcMode& mode, void* ws, size_t ws_bytes, int* err, cudaStream_t st,
@@ -1093,7 +1132,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.cmax = mode.exact ? eb : nullptr;
     const int tiles = sym_out ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;   // per instance
     // one K-chunk per pair (short products, or BF16 with its single pair): few
-    // units per tile, so the final epilogue pass weighs most -- the lean one
+    // units per tile, so the final pass is most of a tile's latency -- the lean one
     const bool lean = (K + P.chunk - 1) / P.chunk == 1;
     if (!prepare_kernels()) return -1;
     if (ev_begin) cudaEventRecord(ev_begin, st);
@@ -1102,8 +1141,8 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
         // persistent (one CTA per SM walking the tiles) unless the caller wants
         // the SMs released after every tile (so higher-priority streams get in)
         const int grid = (one_tile_per_cta || all_tiles < num_sms()) ? all_tiles : num_sms();
-        if (lean) tc_gemm_kernel<true><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
-        else tc_gemm_kernel<false><<<grid, THREADS, tc_smem_bytes(), st>>>(ma, mb, P);
+        if (lean) tc_gemm_kernel<true><<<grid, THREADS, smem_bytes(true), st>>>(ma, mb, P);
+        else tc_gemm_kernel<false><<<grid, THREADS, smem_bytes(false), st>>>(ma, mb, P);
     }
     if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;
