@@ -64,15 +64,30 @@ M, N, RANK, S_MIN, SEED = 4096, 3072, 2304, 1e-4, 1
 METRIC = "pseudoinverses/s at 1e-9 Penrose residual"
 UNIT = "solves/s"
 WORKLOAD = "moore_penrose_rank_deficient_4096x3072_r2304"
-# dram__bytes_read.sum + dram__bytes_write.sum per launch of the dominant
-# kernel from the committed ncu summary under profiles/ (None until captured
-# for the current kernel).
-TRAFFIC_BYTES = {"fp64": None, "fp32": None, "mixed_bf16": None,
-                 # profiles/tc_gemm_kernel_fp64class_3072x3072x4096.md gives the bytes of
-                 # a 3072x3072x4096 launch, scaled to this workload's mean launch by the
-                 # FP64-equivalent flops it processes
-                 "fp64_tc": 3.332e9 + 79.2e6}
-TRAFFIC_REF_FLOPS = 2.0 * 3072 * 3072 * 4096   # the captured launch's 2MNK
+# dram__bytes_read.sum + dram__bytes_write.sum of one 3072x3072x4096 launch of
+# the dominant kernel in each product class, from the committed ncu summaries
+# (profiles/tc_gemm_kernel_fp32class_3072x3072x4096.md and ..._fp64class_...),
+# per FP64-equivalent flop of that launch; a solve's mean launch weights them by
+# the FP64-equivalent work each class processed (this workload's products are
+# n x n x m and n x n x n with n = 3072, m = 4096: the captured shapes).
+TRAFFIC_REF_FLOPS = 2.0 * 3072 * 3072 * 4096   # the captured launches' 2MNK
+TRAFFIC_PER_FLOP = {"fp32": (970.9e6 + 70.6e6) / TRAFFIC_REF_FLOPS,
+                    "fp64_tc": (3.284e9 + 72.4e6) / TRAFFIC_REF_FLOPS}
+
+
+def mean_launch_traffic(prec, gemm_flops, tensor_flops, launches):
+    """DRAM bytes of the mean tensor-core launch of a solve, from the per-class
+    figures: the FP64-class and FP32-class work (28 and 10 slice products per
+    FP64-equivalent flop) are separated from the totals.  None where the solve
+    ran classes without a captured figure (BF16, native FP64)."""
+    if not launches or prec not in ("fp32", "fp64_tc"):
+        return None
+    if prec == "fp64_tc":
+        f64, f32 = gemm_flops, 0.0
+    else:
+        f64 = max(0.0, (tensor_flops - 10.0 * gemm_flops) / 18.0)
+        f32 = max(0.0, gemm_flops - f64)
+    return (f32 * TRAFFIC_PER_FLOP["fp32"] + f64 * TRAFFIC_PER_FLOP["fp64_tc"]) / launches
 
 
 def env_rank():
@@ -366,9 +381,7 @@ def run_ours(args):
     work = gemm_flops if args.prec == "fp64" else sum(i["tensor_flops"] for i in infos)
     achieved = work / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
     fp64_equiv = gemm_flops / (gemm_ms * 1e-3) / 1e12 if gemm_ms > 0 else None
-    traffic = TRAFFIC_BYTES.get(args.prec)
-    if traffic is not None and gemm_launches:
-        traffic = traffic * (gemm_flops / gemm_launches) / TRAFFIC_REF_FLOPS   # per mean launch
+    traffic = mean_launch_traffic(args.prec, gemm_flops, sum(i["tensor_flops"] for i in infos), gemm_launches)
     value = replica_throughput(world, args.steps, total_ms)
     sorted_ms = sorted(per_step)
     p50 = statistics.median(per_step)
