@@ -476,10 +476,24 @@ def run_mp64(args):
         out[key] = {"value": 1e3 / statistics.mean(lat), "p50_ms": statistics.median(lat),
                      "p99_ms": _pct(lat, 0.99), "rel_err_vs_closed_form": err, "loops": info["iters"],
                      "kernels_per_solve": info["kernels"]}
+    # roofline of the autotuned solve's products (they run on the FP64 DMMA
+    # kernel below the measured crossover): CUDA-event time of the product
+    # launches in one profiled (host-driven) solve
+    _, pinfo = h.solve(A, X, alpha=alpha, tol=1e-12, prec="fp64_tc", profile=True)
+    peaks, src = load_peaks()
+    peak64, note64 = dominant_peak("fp64", peaks)
+    gemm_s = pinfo["gemm_ms"] * 1e-3
+    roof = {"bound": "fp64 (DMMA)", "kernel": "gemm_f64_kernel", "unit": "TFLOP/s",
+            "achieved": pinfo["gemm_flops"] / gemm_s / 1e12 if gemm_s > 0 else None, "peak": peak64,
+            "frac": pinfo["gemm_flops"] / gemm_s / 1e12 / peak64 if gemm_s > 0 else None,
+            "gemm_share_of_solve": pinfo["gemm_ms"] / out["autotuned"]["p50_ms"], "traffic": None,
+            "peak_source": f"{src}: {note64}",
+            "note": "latency-bound: 48 x 48 x 64 products of a few CTAs each"}
     t0 = time.perf_counter()
     ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-12, alpha=alpha)
     t_cpu = time.perf_counter() - t0
     _emit({"metric": "pseudoinverses/s (64x48, latency-bound)", "value": out["autotuned"]["value"],
+           "roofline": roof,
            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
            "config": {"workload": "moore_penrose_64x48", "alpha": alpha, "tol": 1e-12},
            "fp64_tc": out["fp64_tc"], "autotuned": out["autotuned"], "crossover": out["crossover"],
@@ -644,6 +658,19 @@ def run_batched(args):
         H.solve(w.A, H.x0_moore_penrose(w.A, 1.0 / w.s[0] ** 2), tol=1e-12, alpha=1.0 / w.s[0] ** 2)
     t_cpu = (time.perf_counter() - t0) / 8
     t = statistics.median(times)
+    # roofline of the batch: the tensor-core work every instance's products
+    # executed (its share of its padded group's launches) over the batch time
+    peaks, src = load_peaks()
+    tensor = sum(infos[i].tensor_flops for i in range(count))
+    fp64eq = sum(infos[i].gemm_flops for i in range(count))
+    roof = {"bound": "tensor", "kernel": "tc_gemm_kernel (every product of the batch, padded groups)",
+            "achieved": tensor / t / 1e12, "peak": peaks["bf16_tflops_sustained"], "unit": "TFLOP/s",
+            "frac": tensor / t / 1e12 / peaks["bf16_tflops_sustained"],
+            "fp64_equivalent_tflops": fp64eq / t / 1e12,
+            "algorithmic_fp64_equivalent_tflops": sum(
+                (4.0 * min(w.A.shape) ** 2 * max(w.A.shape) + 10.0 * min(w.A.shape) ** 3) * infos[i].iters
+                for i, w in enumerate(ws)) / t / 1e12,
+            "traffic": None, "peak_source": f"{src}: bf16 sustained"}
     _emit({"metric": "pseudoinverses/s, 4096 uneven problems", "value": count / t, "unit": "solves/s",
            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "bf16 + bf16 slices",
            "config": {"workload": f"uneven_batch_{count}", "m": [32, 512], "n": [16, "m"],
@@ -652,6 +679,7 @@ def run_batched(args):
                       "finish": "clean",
                       "steps": args.steps},
            "ms_per_batch": t * 1e3, "status_ok": sum(1 for i in range(count) if infos[i].status == 0),
+           "roofline": roof,
            "loops": {"min": min(loops), "max": max(loops)},
            "accuracy": {"sampled": 64, "max_rel_err_vs_closed_form": max(errs), "meets_1e-4": max(errs) <= 1e-4},
            "fp64_gpu_batched": {"value": count / t64, "s_per_batch": t64, "status": rc64},
