@@ -54,7 +54,12 @@ namespace {
 constexpr int BM = 128;
 constexpr int BN = 128;
 constexpr int BK = 64;          // 64 bf16 = one 128-byte swizzle row
-constexpr int STAGES = 6;
+constexpr int STAGES = 6;        // pipeline stages of products with several K-chunks
+// Single-chunk products (short K: every tile is few units and the epilogue's
+// fixed cost dominates) keep four stages: the shared memory given back becomes
+// L1, which holds the epilogue's register spills and side inputs (4096-problem
+// batch: 540 ms with six stages, 498 with four, 496 with three, 506 with five)
+constexpr int LEAN_STAGES = 4;
 constexpr int EPI_WARPS = 8;    // two per TMEM lane quarter, each owning BN/2 columns
 constexpr int EPI_COLS = BN / 2;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
@@ -462,16 +467,17 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                const __grid_constant__ TcParams P) {
     extern __shared__ __align__(1024) uint8_t smem_raw[];
     uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    uint64_t* full = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
-    uint64_t* empty = full + STAGES;
-    uint64_t* accf = empty + STAGES;
+    constexpr int NST = LEAN ? LEAN_STAGES : STAGES;
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + NST * STAGE_BYTES);
+    uint64_t* empty = full + NST;
+    uint64_t* accf = empty + NST;
     uint64_t* acce = accf + 2;
     uint64_t* drain = acce + 2;   // completion of every MMA the issuer launched
     uint64_t* tdone = drain + 1;  // every epilogue warp has finished with TMEM
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tdone + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
-    double* stg_all = reinterpret_cast<double*>(smem + STAGES * STAGE_BYTES + 256);
-    int* ecol_all = reinterpret_cast<int*>(smem + STAGES * STAGE_BYTES + 256 + STG_BYTES);
+    double* stg_all = reinterpret_cast<double*>(smem + NST * STAGE_BYTES + 256);
+    int* ecol_all = reinterpret_cast<int*>(smem + NST * STAGE_BYTES + 256 + STG_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_per = P.sym ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;
@@ -488,7 +494,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     const int units = P.ngroups * kchunks;
 
     if (threadIdx.x == 0) {
-        for (int i = 0; i < STAGES; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
+        for (int i = 0; i < NST; ++i) { mbar_init(&full[i], 1); mbar_init(&empty[i], 1); }
         for (int i = 0; i < 2; ++i) { mbar_init(&accf[i], 1); mbar_init(&acce[i], 32 * EPI_WARPS); }
         mbar_init(drain, 1);
         mbar_init(tdone, EPI_WARPS);
@@ -533,7 +539,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                             tma_load_3d(sa + A_TILE_BYTES, &mapB, &full[stage], k, n0, b * P.S + P.pair_t[pr]);
                             issued |= 1u << stage;
                             ipar = (ipar & ~(1u << stage)) | (phase << stage);
-                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                            if (++stage == NST) { stage = 0; phase ^= 1; }
                         }
                     }
                 }
@@ -543,7 +549,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             // stage.  A stage is reloaded only after its previous load was
             // consumed, so the last phase issued is the only one that can be
             // outstanding; on the normal path every wait returns at once.
-            for (int s2 = 0; s2 < STAGES; ++s2)
+            for (int s2 = 0; s2 < NST; ++s2)
                 if ((issued >> s2) & 1u)
                     if (!mbar_wait(&full[s2], (ipar >> s2) & 1u)) record_error(P.err, 5);
         }
@@ -580,7 +586,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                                 acc = 1;
                             }
                             mma_commit(&empty[stage]);
-                            if (++stage == STAGES) { stage = 0; phase ^= 1; }
+                            if (++stage == NST) { stage = 0; phase ^= 1; }
                         }
                     }
                     mma_commit(&accf[buf]);
@@ -972,7 +978,7 @@ int num_sms() {
 // exponents; the lean kernel keeps its column exponents in static shared
 // memory and gives the rest to L1.
 size_t smem_bytes(bool lean) {
-    return STAGES * STAGE_BYTES + 1024 + 256 + (lean ? 0 : STG_BYTES + ECOL_BYTES);
+    return (lean ? LEAN_STAGES : STAGES) * STAGE_BYTES + 1024 + 256 + (lean ? 0 : STG_BYTES + ECOL_BYTES);
 }
 
 // Set the kernels' shared-memory attribute once per device; false if the
