@@ -662,18 +662,23 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 // exact diagonals: the accumulator in integer units; later ones:
                 // FP32 in units of 2^-ubase
                 const float unit = ldexpf(1.0f, horner ? uexp : P.ubase);
-                {
-                    // the whole drain in one load; the accumulator goes back to the
-                    // MMA issuer before the conversion work
-                    uint32_t r[EPI_COLS];
-                    tmem_ld64_raw(taddr, r);
-                    tc_fence_before();
-                    mbar_arrive(&acce[buf]);
 #pragma unroll
-                    for (int j = 0; j < EPI_COLS; ++j) {
-                        if (horner) iacc[j] += __float2int_rn(__uint_as_float(r[j]) * unit);
-                        else if (P.exact) iacc[j] = __float_as_int(fmaf(__uint_as_float(r[j]), unit, __int_as_float(iacc[j])));
-                        else iacc[j] = (int)r[j];   // one drain only: keep the FP32 bits
+                for (int hh = 0; hh < EPI_COLS; hh += 32) {
+                    // the drain in two 32-column loads, each converted at once (32
+                    // registers in flight next to the 64 of the sums, not 64); the
+                    // accumulator goes back to the MMA issuer after the second load
+                    uint32_t r[32];
+                    tmem_ld32_raw(taddr + hh, r);
+                    if (hh + 32 == EPI_COLS) {
+                        tc_fence_before();
+                        mbar_arrive(&acce[buf]);
+                    }
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        if (horner) iacc[hh + j] += __float2int_rn(__uint_as_float(r[j]) * unit);
+                        else if (P.exact)
+                            iacc[hh + j] = __float_as_int(fmaf(__uint_as_float(r[j]), unit, __int_as_float(iacc[hh + j])));
+                        else iacc[hh + j] = (int)r[j];   // one drain only: keep the FP32 bits
                     }
                 }
                 accphase[buf] ^= 1;
