@@ -65,14 +65,13 @@ METRIC = "pseudoinverses/s at 1e-9 Penrose residual"
 UNIT = "solves/s"
 WORKLOAD = "moore_penrose_rank_deficient_4096x3072_r2304"
 # dram__bytes_read.sum + dram__bytes_write.sum of one 3072x3072x4096 launch of
-# the dominant kernel in each product class, from the committed ncu summaries
-# (profiles/tc_gemm_kernel_fp32class_3072x3072x4096.md and ..._fp64class_...),
-# per FP64-equivalent flop of that launch; a solve's mean launch weights them by
+# the dominant kernel in each product class (one ncu --set full capture of the
+# current kernel per class), per FP64-equivalent flop of that launch; a solve's mean launch weights them by
 # the FP64-equivalent work each class processed (this workload's products are
 # n x n x m and n x n x n with n = 3072, m = 4096: the captured shapes).
 TRAFFIC_REF_FLOPS = 2.0 * 3072 * 3072 * 4096   # the captured launches' 2MNK
-TRAFFIC_PER_FLOP = {"fp32": (970.9e6 + 70.6e6) / TRAFFIC_REF_FLOPS,
-                    "fp64_tc": (3.284e9 + 72.4e6) / TRAFFIC_REF_FLOPS}
+TRAFFIC_PER_FLOP = {"fp32": (958.1e6 + 63.1e6) / TRAFFIC_REF_FLOPS,
+                    "fp64_tc": (3.268e9 + 63.6e6) / TRAFFIC_REF_FLOPS}
 
 
 def mean_launch_traffic(prec, gemm_flops, tensor_flops, launches):

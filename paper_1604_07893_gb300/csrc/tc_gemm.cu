@@ -326,7 +326,7 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 // products the shared-memory staging of the other pass costs more
 // instructions than its coalesced accesses save: measured 5-9 % slower.)
 __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogue& E, uint32_t acc64, int row,
-                                                int col0, int row0w, const unsigned long long* rmax,
+                                                int col0, int ncols, int row0w, const unsigned long long* rmax,
                                                 const unsigned long long* cmax, int ew, bool mirror, int lane,
                                                 double& sd, double& sx) {
     // the column exponents of this warp's half tile (static shared memory of
@@ -334,7 +334,7 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
     __shared__ int ecol_all[EPI_WARPS][EPI_COLS];
     int* ecol = ecol_all[ew];
     if (rmax) {
-        for (int cc = lane; cc < EPI_COLS; cc += 32) ecol[cc] = (col0 + cc < P.N) ? grid_exponent(cmax, col0 + cc) : 0;
+        for (int cc = lane; cc < ncols; cc += 32) ecol[cc] = (col0 + cc < P.N) ? grid_exponent(cmax, col0 + cc) : 0;
         __syncwarp();
     }
     const bool rowok = row < P.M;
@@ -343,7 +343,7 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
     const double* s2 = (E.s2 && rowok) ? E.s2 + (size_t)row * E.ld2 : nullptr;
     const bool norms = E.partials != nullptr;
 #pragma unroll 1
-    for (int c = 0; c < EPI_COLS; c += 8) {   // 8 columns per TMEM load
+    for (int c = 0; c < ncols; c += 8) {   // 8 columns per TMEM load
         uint32_t r[16];
         tmem_ld16_raw(acc64 + 2 * c, r);
         if (!rowok) continue;
@@ -403,18 +403,23 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
 // column layout (a warp instruction covers 4 rows x 8 consecutive columns),
 // so that the side-input loads and the output stores are coalesced: with one
 // row per lane every access touched 32 cache lines, which dominated the pass.
-__device__ __forceinline__ void final_pass(const TcParams& P, const Epilogue& E, uint32_t acc64, int row0, int col0,
+__device__ __forceinline__ void final_pass(const TcParams& P, long long off, uint32_t acc64, int row0, int col0, int ncols,
                                            const unsigned long long* rmax, const unsigned long long* cmax,
                                            bool mirror, int lane, double* stg, int* ecol, double& sd, double& sx) {
     if (P.exact) {
-        for (int cc = lane; cc < EPI_COLS; cc += 32) ecol[cc] = (col0 + cc < P.N) ? grid_exponent(cmax, col0 + cc) : 0;
+        for (int cc = lane; cc < ncols; cc += 32) ecol[cc] = (col0 + cc < P.N) ? grid_exponent(cmax, col0 + cc) : 0;
         __syncwarp();
     }
     const int erow = (P.exact && row0 + lane < P.M) ? grid_exponent(rmax, row0 + lane) - P.ubase - P.hshift : 0;
+    // the coefficients and pointers are read from the kernel parameters where
+    // they are used (instance b's matrices at +off): no copy held in registers
+    // (measured on the 3072 x 3072 x 4096 FP32-class product: final pass
+    // 400k -> 326k clocks per CTA); the single-chunk pass is faster with its copy
+    const Epilogue& E = P.epi;
     const bool norms = E.partials != nullptr;
     const int cl = lane & 7, rq = lane >> 3;   // column of the group, row quarter (column layout)
 #pragma unroll 1
-    for (int c = 0; c < EPI_COLS; c += STG_COLS) {
+    for (int c = 0; c < ncols; c += STG_COLS) {
         {
             uint32_t r[16];
             tmem_ld16_raw(acc64 + 2 * c, r);
@@ -433,8 +438,8 @@ __device__ __forceinline__ void final_pass(const TcParams& P, const Epilogue& E,
                 const int row = row0 + rr;
                 if (row >= P.M) break;
                 const double a = stg[rr * STG_LD + cl];
-                const double v1 = E.s1 ? E.s1[(size_t)row * E.ld1 + col] : 0.0;
-                const double v2 = E.s2 ? E.s2[(size_t)row * E.ld2 + col] : 0.0;
+                const double v1 = E.s1 ? E.s1[off + (size_t)row * E.ld1 + col] : 0.0;
+                const double v2 = E.s2 ? E.s2[off + (size_t)row * E.ld2 + col] : 0.0;
 #pragma unroll
                 for (int o = 0; o < 3; ++o) {
                     if (o < E.nout) {
@@ -445,8 +450,8 @@ __device__ __forceinline__ void final_pass(const TcParams& P, const Epilogue& E,
                         if (kind & OUT_S2) v = fma(t.a_s2, v2, v);
                         if ((kind & OUT_ID) && row == col) v += t.a_id;
                         if (kind & OUT_STORE) {
-                            t.out[(size_t)row * t.ld + col] = v;
-                            if (mirror) t.out[(size_t)col * t.ld + row] = v;
+                            t.out[off + (size_t)row * t.ld + col] = v;
+                            if (mirror) t.out[off + (size_t)col * t.ld + row] = v;
                         }
                         if (o == 0 && norms) {
                             const double dd = v - v1;
@@ -622,22 +627,35 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         const int half = (warp - 2) >> 2;        // which BN/2 columns of the tile
         const int ew = warp - 2;                 // epilogue warp index
         const uint32_t lane_base = tmem + ((uint32_t)(lg * 32) << 16);
-        const uint32_t acc64 = lane_base + 2 * BN + 2 * half * EPI_COLS;
+        const uint32_t acc64 = lane_base + 2 * BN + 2 * half * EPI_COLS;   // this warp's tile sums
         int buf = 0;
         uint32_t accphase[2] = {0, 0};
         for (int tile = work0; tile < ntiles; tile += wstep) {
             int b, mb, nb;
             locate(tile, b, mb, nb);
             const int m0 = mb * BM, n0 = nb * BN;
+            // A tile with at most BN/2 valid columns (a narrow single-chunk
+            // product, or the last tile column of one) is split between both
+            // warps of a lane quarter, BN/4 valid columns each, instead of
+            // leaving one of them idle: each warp drains its 32 valid columns
+            // as its first 32 (and 32 columns past N as the rest), so the final
+            // pass -- most of such a tile's latency -- covers half the columns.
+            const bool narrow = LEAN && P.N - n0 <= EPI_COLS;
+            const int ncols = narrow ? EPI_COLS / 2 : EPI_COLS;   // valid columns of this warp
+            const int cbase = half * ncols;                          // the first of them
             // slot of the tile's partials (instance-major, nb-major then mb)
             const int slot = b * P.tiles_m * P.tiles_n + nb * P.tiles_m + mb;
             const bool mirror = P.sym && mb != nb;   // also write the transposed tile
-            Epilogue E = P.epi;   // instance b's matrices
-            const long long off = (long long)b * P.stride;
-            if (E.s1) E.s1 += off;
-            if (E.s2) E.s2 += off;
-            for (int o = 0; o < 3; ++o)
-                if (E.o[o].out) E.o[o].out += off;
+            const long long off = (long long)b * P.stride;   // instance b's matrices
+            // the single-chunk pass holds instance b's epilogue in registers
+            // (the multi-chunk pass reads the kernel parameters where used)
+            Epilogue E = P.epi;
+            if constexpr (LEAN) {
+                if (E.s1) E.s1 += off;
+                if (E.s2) E.s2 += off;
+                for (int o = 0; o < 3; ++o)
+                    if (E.o[o].out) E.o[o].out += off;
+            }
             const unsigned long long* rmax = P.rmax ? P.rmax + (size_t)b * P.M : nullptr;
             const unsigned long long* cmax = P.cmax ? P.cmax + (size_t)b * P.N : nullptr;
             int iacc[EPI_COLS];
@@ -656,7 +674,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     record_error(P.err, 4); *abort_flag = 1; ok = false; break;
                 }
                 tc_fence_after();
-                const uint32_t taddr = lane_base + buf * BN + half * EPI_COLS;
+                const uint32_t taddr = lane_base + buf * BN + cbase;   // first 32 columns
+                const uint32_t taddr2 = narrow ? lane_base + buf * BN + EPI_COLS + cbase : taddr + 32;
                 const int uexp = 14 + 8 * d;   // slice products q q' 2^-(14+8d): accumulator / unit
                 const bool horner = P.exact && d <= P.dint;
                 // exact diagonals: the accumulator in integer units; later ones:
@@ -668,7 +687,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                     // registers in flight next to the 64 of the sums, not 64); the
                     // accumulator goes back to the MMA issuer after the second load
                     uint32_t r[32];
-                    tmem_ld32_raw(taddr + hh, r);
+                    tmem_ld32_raw(hh ? taddr2 : taddr, r);
                     if (hh + 32 == EPI_COLS) {
                         tc_fence_before();
                         mbar_arrive(&acce[buf]);
@@ -739,21 +758,21 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             if (!ok) break;
             double sd = 0.0, sx = 0.0;
-            if constexpr (LEAN)
-                lean_final_pass(P, E, acc64, m0 + lg * 32 + lane, n0 + half * EPI_COLS, m0 + lg * 32, rmax, cmax,
+            if constexpr (LEAN) {
+                lean_final_pass(P, E, acc64, m0 + lg * 32 + lane, n0 + cbase, ncols, m0 + lg * 32, rmax, cmax,
                                 ew, mirror, lane, sd, sx);
-            else
-                final_pass(P, E, acc64, m0 + lg * 32, n0 + half * EPI_COLS, rmax, cmax, mirror, lane,
+            } else
+                final_pass(P, off, acc64, m0 + lg * 32, n0 + cbase, ncols, rmax, cmax, mirror, lane,
                            stg_all + ew * 32 * STG_LD, ecol_all + ew * EPI_COLS, sd, sx);
-            if (E.partials) {  // one pair per (tile, epilogue warp): no barrier between warps
+            if (P.epi.partials) {  // one pair per (tile, epilogue warp): no barrier between warps
 #pragma unroll
                 for (int off = 16; off; off >>= 1) {
                     sd += __shfl_xor_sync(0xffffffffu, sd, off);
                     sx += __shfl_xor_sync(0xffffffffu, sx, off);
                 }
                 if (lane == 0) {
-                    E.partials[2 * (EPI_WARPS * slot + ew)] = sd;
-                    E.partials[2 * (EPI_WARPS * slot + ew) + 1] = sx;
+                    P.epi.partials[2 * (EPI_WARPS * slot + ew)] = sd;
+                    P.epi.partials[2 * (EPI_WARPS * slot + ew) + 1] = sx;
                 }
             }
         }
