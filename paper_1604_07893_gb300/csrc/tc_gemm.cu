@@ -175,6 +175,28 @@ __device__ __forceinline__ double float_bits_to_double(uint32_t f) {
     return __longlong_as_double((long long)bits);
 }
 
+// FP64 arithmetic that the compiler may not evaluate ahead of its condition
+// (volatile inline assembly): see the final passes.
+__device__ __forceinline__ double dfma_keep(double a, double b, double c) {
+    double d;
+    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(d) : "d"(a), "d"(b), "d"(c));
+    return d;
+}
+__device__ __forceinline__ double dmul_keep(double a, double b) {
+    double d;
+    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
+    return d;
+}
+__device__ __forceinline__ double dadd_keep(double a, double b) {
+    double d;
+    asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
+    return d;
+}
+// -x by flipping the sign bit (integer pipe)
+__device__ __forceinline__ double neg(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+
 // a_acc * a, the coefficient given by its flags: +1 and -1 (the only ones the
 // chain uses) without an FP64 instruction.
 __device__ __forceinline__ double times_coef(int kind, double c, double a) {
@@ -368,21 +390,46 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
                 const int kind = P.okind[o];
                 double* out = (kind & OUT_STORE) ? t.out + (size_t)row * t.ld + cb : nullptr;
                 const bool use_s2 = (kind & OUT_S2) && s2 != nullptr;
+                // Each term of the combination is applied to the group's 8
+                // values under one uniform test, its FP64 instructions inline
+                // assembly: a term that is absent costs no FP64 instruction
+                // (tested per element, the compiler evaluated every term and
+                // selected -- about 4 FP64 instructions per element at ~64
+                // clocks per warp each on GB300's FP64 pipe)
+                double v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = (kind & OUT_NEG) ? neg(a[j]) : a[j];
+                if (kind & OUT_MUL) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = dmul_keep(t.a_acc, v[j]);
+                }
+                if (kind & OUT_S1) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = dfma_keep(t.a_s1, v1[j], v[j]);
+                }
+                if (use_s2) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = dfma_keep(t.a_s2, j < ncol ? s2[cb + j] : 0.0, v[j]);
+                }
+                if ((kind & OUT_ID) && diag && dg >= 0 && dg < 8) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j == dg) v[j] = dadd_keep(v[j], t.a_id);
+                }
 #pragma unroll
                 for (int j = 0; j < 8; ++j) {
-                    if (j < ncol) {
-                        double v = times_coef(kind, t.a_acc, a[j]);
-                        if (kind & OUT_S1) v = fma(t.a_s1, v1[j], v);
-                        if (use_s2) v = fma(t.a_s2, s2[cb + j], v);
-                        if ((kind & OUT_ID) && diag && j == dg) v += t.a_id;
-                        if (out) {
-                            out[j] = v;
-                            if (mirror) t.out[(size_t)(cb + j) * t.ld + row] = v;   // warp-coalesced
-                        }
-                        if (o == 0 && norms) {
-                            const double dd = v - v1[j];
-                            sd = fma(dd, dd, sd);
-                            sx = fma(v1[j], v1[j], sx);
+                    if (j < ncol && out) {
+                        out[j] = v[j];
+                        if (mirror) t.out[(size_t)(cb + j) * t.ld + row] = v[j];   // warp-coalesced
+                    }
+                }
+                if (o == 0 && norms) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (j < ncol) {
+                            const double dd = dadd_keep(v[j], neg(v1[j]));
+                            sd = dfma_keep(dd, dd, sd);
+                            sx = dfma_keep(v1[j], v1[j], sx);
                         }
                     }
                 }
