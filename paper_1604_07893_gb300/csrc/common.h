@@ -29,6 +29,50 @@ struct Epilogue {
     double* partials;
 };
 
+// The terms an epilogue output has, as integer flags computed on the host, so
+// that the kernels test no FP64 value (on GB300 every FP64 instruction -- a
+// compare included -- holds a sub-partition's FP64 unit for about 64 clocks
+// per warp): OUT_NEG / OUT_MUL for a_acc = -1 / other than +-1.
+enum { OUT_STORE = 1, OUT_NEG = 2, OUT_MUL = 4, OUT_S1 = 8, OUT_S2 = 16, OUT_ID = 32 };
+inline int out_kind(const Epilogue& e, int o) {
+    if (o >= e.nout) return 0;
+    const EpiTerm& t = e.o[o];
+    int k = 0;
+    if (t.out) k |= OUT_STORE;
+    if (t.a_acc == -1.0) k |= OUT_NEG;
+    else if (t.a_acc != 1.0) k |= OUT_MUL;
+    if (t.a_s1 != 0.0 && e.s1) k |= OUT_S1;
+    if (t.a_s2 != 0.0 && e.s2) k |= OUT_S2;
+    if (t.a_id != 0.0) k |= OUT_ID;
+    return k;
+}
+
+#ifdef __CUDACC__
+// FP64 arithmetic for the epilogues' terms, as volatile inline assembly so that
+// the compiler does not evaluate it ahead of the uniform test of the term's
+// flag (evaluating every term of every element and selecting had cost about
+// four FP64 instructions per element at ~64 clocks per warp each).
+__device__ __forceinline__ double dfma_keep(double a, double b, double c) {
+    double d;
+    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(d) : "d"(a), "d"(b), "d"(c));
+    return d;
+}
+__device__ __forceinline__ double dmul_keep(double a, double b) {
+    double d;
+    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
+    return d;
+}
+__device__ __forceinline__ double dadd_keep(double a, double b) {
+    double d;
+    asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
+    return d;
+}
+// -x by flipping the sign bit (integer pipe)
+__device__ __forceinline__ double neg(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
+}
+#endif
+
 inline Epilogue epi_none() {
     Epilogue e{};
     e.nout = 0;

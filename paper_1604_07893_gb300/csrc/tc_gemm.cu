@@ -78,8 +78,6 @@ constexpr int STG_BYTES = EPI_WARPS * 32 * STG_LD * 8;
 constexpr int ECOL_BYTES = EPI_WARPS * EPI_COLS * 4;
 constexpr unsigned WAIT_LIMIT = 1u << 22;   // polls before a wait gives up (about a second)
 
-enum { OUT_STORE = 1, OUT_NEG = 2, OUT_MUL = 4, OUT_S1 = 8, OUT_S2 = 16, OUT_ID = 32 };
-
 struct TcParams {
     int M, N, K;          // K = logical length (the tensor maps are zero-padded beyond it)
     int npairs;
@@ -175,32 +173,10 @@ __device__ __forceinline__ double float_bits_to_double(uint32_t f) {
     return __longlong_as_double((long long)bits);
 }
 
-// FP64 arithmetic that the compiler may not evaluate ahead of its condition
-// (volatile inline assembly): see the final passes.
-__device__ __forceinline__ double dfma_keep(double a, double b, double c) {
-    double d;
-    asm volatile("fma.rn.f64 %0, %1, %2, %3;" : "=d"(d) : "d"(a), "d"(b), "d"(c));
-    return d;
-}
-__device__ __forceinline__ double dmul_keep(double a, double b) {
-    double d;
-    asm volatile("mul.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
-    return d;
-}
-__device__ __forceinline__ double dadd_keep(double a, double b) {
-    double d;
-    asm volatile("add.rn.f64 %0, %1, %2;" : "=d"(d) : "d"(a), "d"(b));
-    return d;
-}
-// -x by flipping the sign bit (integer pipe)
-__device__ __forceinline__ double neg(double x) {
-    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ull);
-}
-
 // a_acc * a, the coefficient given by its flags: +1 and -1 (the only ones the
 // chain uses) without an FP64 instruction.
 __device__ __forceinline__ double times_coef(int kind, double c, double a) {
-    if (kind & OUT_NEG) return __longlong_as_double(__double_as_longlong(a) ^ (long long)0x8000000000000000ull);
+    if (kind & OUT_NEG) return neg(a);
     if (kind & OUT_MUL) return c * a;
     return a;
 }
@@ -299,25 +275,6 @@ __device__ __forceinline__ void tmem_ld16_raw(uint32_t taddr, uint32_t* r) {
         : "memory");
 }
 // 64 columns in one load (the whole drain of an epilogue warp), then the wait.
-__device__ __forceinline__ void tmem_ld64_raw(uint32_t taddr, uint32_t* r) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x64.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31,"
-        "%32,%33,%34,%35,%36,%37,%38,%39,%40,%41,%42,%43,%44,%45,%46,%47,"
-        "%48,%49,%50,%51,%52,%53,%54,%55,%56,%57,%58,%59,%60,%61,%62,%63}, [%64];\n\t"
-        "tcgen05.wait::ld.sync.aligned;"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
-          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
-          "=r"(r[29]), "=r"(r[30]), "=r"(r[31]), "=r"(r[32]), "=r"(r[33]), "=r"(r[34]), "=r"(r[35]),
-          "=r"(r[36]), "=r"(r[37]), "=r"(r[38]), "=r"(r[39]), "=r"(r[40]), "=r"(r[41]), "=r"(r[42]),
-          "=r"(r[43]), "=r"(r[44]), "=r"(r[45]), "=r"(r[46]), "=r"(r[47]), "=r"(r[48]), "=r"(r[49]),
-          "=r"(r[50]), "=r"(r[51]), "=r"(r[52]), "=r"(r[53]), "=r"(r[54]), "=r"(r[55]), "=r"(r[56]),
-          "=r"(r[57]), "=r"(r[58]), "=r"(r[59]), "=r"(r[60]), "=r"(r[61]), "=r"(r[62]), "=r"(r[63])
-        : "r"(taddr)
-        : "memory");
-}
 __device__ __forceinline__ void tmem_st32_raw(uint32_t taddr, const uint32_t* r) {
     asm volatile(
         "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
@@ -492,6 +449,8 @@ __device__ __forceinline__ void final_pass(const TcParams& P, long long off, uin
                     if (o < E.nout) {
                         const EpiTerm& t = E.o[o];
                         const int kind = P.okind[o];
+                        // (plain arithmetic here: the volatile form of the
+                        // single-chunk pass measured 2 % slower on this pass)
                         double v = times_coef(kind, t.a_acc, a);
                         if (kind & OUT_S1) v = fma(t.a_s1, v1, v);
                         if (kind & OUT_S2) v = fma(t.a_s2, v2, v);
@@ -1190,19 +1149,7 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     P.tiles_m = (M + BM - 1) / BM;
     P.tiles_n = (N + BN - 1) / BN;
     P.epi = epi;
-    for (int o = 0; o < 3; ++o) {
-        const EpiTerm& t = epi.o[o];
-        int k = 0;
-        if (o < epi.nout) {
-            if (t.out) k |= OUT_STORE;
-            if (t.a_acc == -1.0) k |= OUT_NEG;
-            else if (t.a_acc != 1.0) k |= OUT_MUL;
-            if (t.a_s1 != 0.0) k |= OUT_S1;
-            if (t.a_s2 != 0.0 && epi.s2) k |= OUT_S2;
-            if (t.a_id != 0.0) k |= OUT_ID;
-        }
-        P.okind[o] = k;
-    }
+    for (int o = 0; o < 3; ++o) P.okind[o] = out_kind(epi, o);
     P.err = err;
     P.wait_limit = wait_limit ? wait_limit : WAIT_LIMIT;
     P.rmax = mode.exact ? ea : nullptr;
