@@ -59,6 +59,27 @@ def test_gemm_against_extended_precision(handle, prec, M, N, K):
     assert check_gemm(handle, A, B, False, False, prec) <= BOUND[prec]
 
 
+@pytest.mark.parametrize("prec", ["fp64_tc", "fp32"])
+@pytest.mark.parametrize("M,N,K", [(2048, 2560, 1100), (2176, 1152, 3000)])
+def test_gemm_more_tiles_than_sms_against_extended_precision(handle, prec, M, N, K):
+    """Multi-chunk products with more 128 x 128 tiles than SMs, in a number
+    that does not divide among them (320 and 153 tiles on 152 SMs): a CTA
+    walks several tiles, and the last wave is partial; every sampled row is
+    checked against the extended-precision product."""
+    rng = np.random.default_rng(M + N + K)
+    A = rng.standard_normal((M, K)) * np.exp(rng.uniform(-3, 3, (M, 1)))
+    B = rng.standard_normal((K, N)) * np.exp(rng.uniform(-3, 3, (1, N)))
+    C = handle.gemm(dev(A), dev(B), prec=prec).cpu().numpy()
+    rows = np.unique(np.concatenate([np.arange(0, M, 16), [M - 1]]))
+    ref = A[rows].astype(np.longdouble) @ B.astype(np.longdouble)
+    scale = np.abs(A[rows]) @ np.abs(B)
+    err = (np.abs(C[rows] - ref) / np.maximum(scale, 1e-300)).astype(np.float64)
+    assert float(err.max()) <= BOUND[prec]
+    # and the deterministic engine: the same product twice is identical
+    C2 = handle.gemm(dev(A), dev(B), prec=prec).cpu().numpy()
+    assert np.array_equal(C, C2)
+
+
 @pytest.mark.parametrize("ta,tb", [(True, False), (False, True), (True, True)])
 def test_gemm_transposes(handle, ta, tb):
     rng = np.random.default_rng(5)
