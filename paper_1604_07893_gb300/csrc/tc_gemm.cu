@@ -162,6 +162,23 @@ __device__ __forceinline__ double fixed_to_double(long long V, int E) {
     return __longlong_as_double((long long)(sign | (((unsigned long long)be << 52) + (m - (1ull << 52)))));
 }
 
+// The same value by one path for every magnitude (normalise, keep 53 bits,
+// round the 11 below them to nearest, ties to even): no divergence between
+// the lanes of a warp, for the single-chunk pass.
+__device__ __forceinline__ double fixed_to_double_uniform(long long V, int E) {
+    const unsigned long long sign = (unsigned long long)V & 0x8000000000000000ull;
+    const unsigned long long u = V < 0 ? 0ull - (unsigned long long)V : (unsigned long long)V;
+    if (u == 0) return 0.0;
+    const int lz = __clzll((long long)u);
+    const unsigned long long n = u << lz;
+    unsigned long long m = n >> 11;                       // 53-bit significand (may round up to 2^53)
+    const unsigned rem = (unsigned)n & 0x7FFu;
+    m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+    const int be = (63 - lz) + E + 1023;                  // biased exponent
+    if (be < 1 || be > 2045) return fixed_to_double_slow(V, E);
+    return __longlong_as_double((long long)(sign | (((unsigned long long)be << 52) + (m - (1ull << 52)))));
+}
+
 // The double of an FP32 bit pattern (exact), by integer operations for normal
 // values.
 __device__ __forceinline__ double float_bits_to_double(uint32_t f) {
@@ -333,8 +350,8 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             // the tile sum: fixed point (exact modes) or FP32 bits (BF16)
-            a[j] = P.exact ? fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
-                                             erow + (rmax ? ecol[c + j] : 0))
+            a[j] = P.exact ? fixed_to_double_uniform((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
+                                                     erow + (rmax ? ecol[c + j] : 0))
                            : float_bits_to_double(r[2 * j]);
             v1[j] = (s1 && j < ncol) ? s1[cb + j] : 0.0;
         }
