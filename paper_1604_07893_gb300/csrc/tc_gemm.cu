@@ -390,11 +390,21 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
                     for (int j = 0; j < 8; ++j)
                         if (j == dg) v[j] = dadd_keep(v[j], t.a_id);
                 }
+                if (out) {
+                    // a whole, 16-byte aligned row segment leaves in four 16-byte stores
+                    if (ncol == 8 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
 #pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    if (j < ncol && out) {
-                        out[j] = v[j];
-                        if (mirror) t.out[(size_t)(cb + j) * t.ld + row] = v[j];   // warp-coalesced
+                        for (int j = 0; j < 8; j += 2)
+                            *reinterpret_cast<double2*>(out + j) = make_double2(v[j], v[j + 1]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (j < ncol) out[j] = v[j];
+                    }
+                    if (mirror) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (j < ncol) t.out[(size_t)(cb + j) * t.ld + row] = v[j];   // warp-coalesced
                     }
                 }
                 if (o == 0 && norms) {
