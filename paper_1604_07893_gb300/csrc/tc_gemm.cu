@@ -198,6 +198,18 @@ __device__ __forceinline__ double times_coef(int kind, double c, double a) {
     return a;
 }
 
+// 32-byte global accesses of four doubles (sm_100 and later); the address is
+// 32-byte aligned
+__device__ __forceinline__ void st_global_v4(double* p, double a, double b, double c, double d) {
+    asm volatile("st.global.v4.f64 [%0], {%1, %2, %3, %4};" ::"l"(p), "d"(a), "d"(b), "d"(c), "d"(d) : "memory");
+}
+__device__ __forceinline__ void ld_global_v4(const double* p, double* v) {
+    asm volatile("ld.global.v4.f64 {%0, %1, %2, %3}, [%4];"
+                 : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
+                 : "l"(p)
+                 : "memory");
+}
+
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -347,13 +359,19 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
         const int ncol = min(8, P.N - cb);         // its valid columns
         if (ncol <= 0) continue;
         double a[8], v1[8];
+        // the first side input's 8 values: two 32-byte loads when aligned and whole
+        const bool v1wide = s1 && ncol == 8 && ((unsigned)reinterpret_cast<uintptr_t>(s1 + cb) & 31u) == 0;
+        if (v1wide) {
+            ld_global_v4(s1 + cb, v1);
+            ld_global_v4(s1 + cb + 4, v1 + 4);
+        }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             // the tile sum: fixed point (exact modes) or FP32 bits (BF16)
             a[j] = P.exact ? fixed_to_double_uniform((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
                                                      erow + (rmax ? ecol[c + j] : 0))
                            : float_bits_to_double(r[2 * j]);
-            v1[j] = (s1 && j < ncol) ? s1[cb + j] : 0.0;
+            if (!v1wide) v1[j] = (s1 && j < ncol) ? s1[cb + j] : 0.0;
         }
         const bool diag = cb < row0w + 32 && cb + 8 > row0w;   // the diagonal crosses this group
         const int dg = row - cb;
@@ -391,8 +409,13 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
                         if (j == dg) v[j] = dadd_keep(v[j], t.a_id);
                 }
                 if (out) {
-                    // a whole, 16-byte aligned row segment leaves in four 16-byte stores
-                    if (ncol == 8 && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
+                    // a whole row segment leaves in two 32-byte stores when it is
+                    // 32-byte aligned, else in four 16-byte ones when 16-byte aligned
+                    const unsigned mis = (unsigned)reinterpret_cast<uintptr_t>(out) & 31u;
+                    if (ncol == 8 && mis == 0) {
+                        st_global_v4(out, v[0], v[1], v[2], v[3]);
+                        st_global_v4(out + 4, v[4], v[5], v[6], v[7]);
+                    } else if (ncol == 8 && (mis & 15u) == 0) {
 #pragma unroll
                         for (int j = 0; j < 8; j += 2)
                             *reinterpret_cast<double2*>(out + j) = make_double2(v[j], v[j + 1]);
