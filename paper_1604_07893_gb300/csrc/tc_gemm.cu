@@ -210,6 +210,27 @@ __device__ __forceinline__ void ld_global_v4(const double* p, double* v) {
                  : "memory");
 }
 
+// Four consecutive doubles from p (nv of them valid, 0 beyond; none when p
+// is null): one 32-byte load when whole and 32-byte aligned
+__device__ __forceinline__ void load4(const double* p, int nv, double* v) {
+    if (p && nv == 4 && ((unsigned)reinterpret_cast<uintptr_t>(p) & 31u) == 0) {
+        ld_global_v4(p, v);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) v[k] = (p && k < nv) ? p[k] : 0.0;
+}
+// The first nv of four doubles to p: one 32-byte store when whole and 32-byte aligned
+__device__ __forceinline__ void store4(double* p, int nv, const double* v) {
+    if (nv == 4 && ((unsigned)reinterpret_cast<uintptr_t>(p) & 31u) == 0) {
+        st_global_v4(p, v[0], v[1], v[2], v[3]);
+        return;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+        if (k < nv) p[k] = v[k];
+}
+
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -471,7 +492,9 @@ __device__ __forceinline__ void final_pass(const TcParams& P, long long off, uin
     // 400k -> 326k clocks per CTA); the single-chunk pass is faster with its copy
     const Epilogue& E = P.epi;
     const bool norms = E.partials != nullptr;
-    const int cl = lane & 7, rq = lane >> 3;   // column of the group, row quarter (column layout)
+    // wide layout: a lane owns 4 consecutive columns of a group row, two lanes
+    // a row, 16 rows per pass, so side inputs and outputs move 32 bytes a lane
+    const int cq = (lane & 1) * 4, rh = lane >> 1;
 #pragma unroll 1
     for (int c = 0; c < ncols; c += STG_COLS) {
         {
@@ -485,34 +508,50 @@ __device__ __forceinline__ void final_pass(const TcParams& P, long long off, uin
                             : float_bits_to_double(r[2 * j]);
         }
         __syncwarp();
-        const int col = col0 + c + cl;
-        if (col < P.N) {
-#pragma unroll 2
-            for (int rr = rq; rr < 32; rr += 4) {
+        const int col = col0 + c + cq;            // this lane's first column
+        const int nv = min(4, P.N - col);         // its valid columns
+        if (nv > 0) {
+#pragma unroll 1
+            for (int rr = rh; rr < 32; rr += 16) {
                 const int row = row0 + rr;
                 if (row >= P.M) break;
-                const double a = stg[rr * STG_LD + cl];
-                const double v1 = E.s1 ? E.s1[off + (size_t)row * E.ld1 + col] : 0.0;
-                const double v2 = E.s2 ? E.s2[off + (size_t)row * E.ld2 + col] : 0.0;
+                double a[4], v1[4], v2[4];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) a[k] = stg[rr * STG_LD + cq + k];
+                load4(E.s1 ? E.s1 + off + (size_t)row * E.ld1 + col : nullptr, nv, v1);
+                load4(E.s2 ? E.s2 + off + (size_t)row * E.ld2 + col : nullptr, nv, v2);
 #pragma unroll
                 for (int o = 0; o < 3; ++o) {
                     if (o < E.nout) {
                         const EpiTerm& t = E.o[o];
                         const int kind = P.okind[o];
-                        // (plain arithmetic here: the volatile form of the
-                        // single-chunk pass measured 2 % slower on this pass)
-                        double v = times_coef(kind, t.a_acc, a);
-                        if (kind & OUT_S1) v = fma(t.a_s1, v1, v);
-                        if (kind & OUT_S2) v = fma(t.a_s2, v2, v);
-                        if ((kind & OUT_ID) && row == col) v += t.a_id;
+                        double v[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            // (plain arithmetic here: the volatile form of the
+                            // single-chunk pass measured 2 % slower on this pass)
+                            v[k] = times_coef(kind, t.a_acc, a[k]);
+                            if (kind & OUT_S1) v[k] = fma(t.a_s1, v1[k], v[k]);
+                            if (kind & OUT_S2) v[k] = fma(t.a_s2, v2[k], v[k]);
+                            if ((kind & OUT_ID) && row == col + k) v[k] += t.a_id;
+                        }
                         if (kind & OUT_STORE) {
-                            t.out[off + (size_t)row * t.ld + col] = v;
-                            if (mirror) t.out[off + (size_t)col * t.ld + row] = v;
+                            store4(t.out + off + (size_t)row * t.ld + col, nv, v);
+                            if (mirror) {
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+                                    if (k < nv) t.out[off + (size_t)(col + k) * t.ld + row] = v[k];
+                            }
                         }
                         if (o == 0 && norms) {
-                            const double dd = v - v1;
-                            sd = fma(dd, dd, sd);
-                            sx = fma(v1, v1, sx);
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                if (k < nv) {
+                                    const double dd = v[k] - v1[k];
+                                    sd = fma(dd, dd, sd);
+                                    sx = fma(v1[k], v1[k], sx);
+                                }
+                            }
                         }
                     }
                 }
