@@ -69,13 +69,6 @@ constexpr int STAGE_BYTES = A_TILE_BYTES + B_TILE_BYTES;
 // TMEM columns: two FP32 MMA accumulators [0, 2BN) and the FP64 running sums of
 // the tile (two 32-bit columns per double) [2BN, 4BN).
 constexpr int TMEM_COLS = 4 * BN;
-// shared memory of the final pass: per epilogue warp a 32-row x 8-column
-// staging block of doubles (row stride 9: the row-layout writes and the
-// column-layout reads fall in different banks) and the tile's column exponents
-constexpr int STG_COLS = 8;
-constexpr int STG_LD = STG_COLS + 1;
-constexpr int STG_BYTES = EPI_WARPS * 32 * STG_LD * 8;
-constexpr int ECOL_BYTES = EPI_WARPS * EPI_COLS * 4;
 constexpr unsigned WAIT_LIMIT = 1u << 22;   // polls before a wait gives up (about a second)
 
 struct TcParams {
@@ -142,30 +135,10 @@ __device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i
 __device__ __noinline__ double fixed_to_double_slow(long long V, int E) { return ldexp((double)V, E); }
 __device__ __noinline__ double float_to_double_slow(uint32_t f) { return (double)__uint_as_float(f); }
 
-__device__ __forceinline__ double fixed_to_double(long long V, int E) {
-    if (V == 0) return 0.0;
-    const unsigned long long sign = (unsigned long long)V & 0x8000000000000000ull;
-    const unsigned long long u = V < 0 ? 0ull - (unsigned long long)V : (unsigned long long)V;
-    const int p = 63 - __clzll((long long)u);            // 2^p <= u < 2^(p+1)
-    unsigned long long m;                                 // 53-bit significand (may round up to 2^53)
-    if (p > 52) {
-        const int sh = p - 52;
-        m = u >> sh;
-        const unsigned long long rem = u & ((1ull << sh) - 1), half = 1ull << (sh - 1);
-        if (rem > half || (rem == half && (m & 1ull))) ++m;
-    } else {
-        m = u << (52 - p);
-    }
-    const int be = p + E + 1023;                          // biased exponent
-    if (be < 1 || be > 2045) return fixed_to_double_slow(V, E);
-    // m = 2^53 after rounding carries into the exponent field: still exact
-    return __longlong_as_double((long long)(sign | (((unsigned long long)be << 52) + (m - (1ull << 52)))));
-}
 
-// The same value by one path for every magnitude (normalise, keep 53 bits,
-// round the 11 below them to nearest, ties to even): no divergence between
-// the lanes of a warp, for the single-chunk pass.
-__device__ __forceinline__ double fixed_to_double_uniform(long long V, int E) {
+// One path for every magnitude (normalise, keep 53 bits, round the 11 below
+// them to nearest, ties to even): no divergence between the lanes of a warp.
+__device__ __forceinline__ double fixed_to_double(long long V, int E) {
     const unsigned long long sign = (unsigned long long)V & 0x8000000000000000ull;
     const unsigned long long u = V < 0 ? 0ull - (unsigned long long)V : (unsigned long long)V;
     if (u == 0) return 0.0;
@@ -190,13 +163,6 @@ __device__ __forceinline__ double float_bits_to_double(uint32_t f) {
     return __longlong_as_double((long long)bits);
 }
 
-// a_acc * a, the coefficient given by its flags: +1 and -1 (the only ones the
-// chain uses) without an FP64 instruction.
-__device__ __forceinline__ double times_coef(int kind, double c, double a) {
-    if (kind & OUT_NEG) return neg(a);
-    if (kind & OUT_MUL) return c * a;
-    return a;
-}
 
 // 32-byte global accesses of four doubles (sm_100 and later); the address is
 // 32-byte aligned
@@ -208,27 +174,6 @@ __device__ __forceinline__ void ld_global_v4(const double* p, double* v) {
                  : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3])
                  : "l"(p)
                  : "memory");
-}
-
-// Four consecutive doubles from p (nv of them valid, 0 beyond; none when p
-// is null): one 32-byte load when whole and 32-byte aligned
-__device__ __forceinline__ void load4(const double* p, int nv, double* v) {
-    if (p && nv == 4 && ((unsigned)reinterpret_cast<uintptr_t>(p) & 31u) == 0) {
-        ld_global_v4(p, v);
-        return;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k) v[k] = (p && k < nv) ? p[k] : 0.0;
-}
-// The first nv of four doubles to p: one 32-byte store when whole and 32-byte aligned
-__device__ __forceinline__ void store4(double* p, int nv, const double* v) {
-    if (nv == 4 && ((unsigned)reinterpret_cast<uintptr_t>(p) & 31u) == 0) {
-        st_global_v4(p, v[0], v[1], v[2], v[3]);
-        return;
-    }
-#pragma unroll
-    for (int k = 0; k < 4; ++k)
-        if (k < nv) p[k] = v[k];
 }
 
 // ------------------------------------------------------------------ PTX helpers
@@ -342,24 +287,24 @@ __device__ __forceinline__ void record_error(int* err, int code) {
 }
 
 // ------------------------------------------------------------------ the kernel
-// Lean final pass of one epilogue warp for one tile (used when each pair has a
-// single K-chunk: few units per tile, so this pass is most of the tile's
-// latency): its 32 rows (one per lane) x EPI_COLS columns of the tile sums in
-// TMEM become out = a_acc acc 2^(e_i + f_j) + a_s1 s1 + a_s2 s2 + a_id I for up
-// to three outputs, plus the stop-norm partials of output 0 against s1,
-// directly in the TMEM row layout.  It is bound by instruction issue, so per
-// element it does little: the column exponents of the tile are computed once
-// per warp (static shared memory of the lean kernel), the doubles are
-// assembled with integer operations, terms are chosen per output, and the
-// identity is tested only where the diagonal crosses.  (On these short
-// products the shared-memory staging of the other pass costs more
-// instructions than its coalesced accesses save: measured 5-9 % slower.)
-__device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogue& E, uint32_t acc64, int row,
+// Final pass of one epilogue warp for one tile: its 32 rows (one per lane) x
+// ncols columns of the tile sums in TMEM become
+//   out = a_acc acc 2^(e_i + f_j) + a_s1 s1 + a_s2 s2 + a_id I
+// for up to three outputs, plus the stop-norm partials of output 0 against s1,
+// directly in the TMEM row layout.  On products with few units per tile this
+// pass is most of the tile's latency, and on long products the next tile's
+// MMAs wait on it; per element it does little: the column exponents of the
+// tile are computed once per warp, the doubles are assembled with integer
+// operations, each term is applied to a group's 8 values under one uniform
+// test, the identity is tested only where the diagonal crosses, and each
+// lane's row segment moves in 32-byte loads and stores.  (A variant staged
+// through shared memory and stored in a column layout measured 0.5 % slower on
+// the headline solve.)
+__device__ __forceinline__ void final_pass(const TcParams& P, const Epilogue& E, uint32_t acc64, int row,
                                                 int col0, int ncols, int row0w, const unsigned long long* rmax,
                                                 const unsigned long long* cmax, int ew, bool mirror, int lane,
                                                 double& sd, double& sx) {
-    // the column exponents of this warp's half tile (static shared memory of
-    // the lean kernels only, so the other kernels keep their footprint)
+    // the column exponents of this warp's half tile (static shared memory)
     __shared__ int ecol_all[EPI_WARPS][EPI_COLS];
     int* ecol = ecol_all[ew];
     if (rmax) {
@@ -389,7 +334,7 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
             // the tile sum: fixed point (exact modes) or FP32 bits (BF16)
-            a[j] = P.exact ? fixed_to_double_uniform((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
+            a[j] = P.exact ? fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
                                                      erow + (rmax ? ecol[c + j] : 0))
                            : float_bits_to_double(r[2 * j]);
             if (!v1wide) v1[j] = (s1 && j < ncol) ? s1[cb + j] : 0.0;
@@ -467,99 +412,6 @@ __device__ __forceinline__ void lean_final_pass(const TcParams& P, const Epilogu
     if (rmax) __syncwarp();   // ecol is rewritten for the next tile
 }
 
-// Final pass of one epilogue warp for one tile of a product with several
-// K-chunks: its 32 rows (one per lane) x EPI_COLS columns of the tile sums in
-// TMEM become
-//   out = a_acc acc 2^(e_i + f_j) + a_s1 s1 + a_s2 s2 + a_id I
-// for up to three outputs, plus the stop-norm partials of output 0 against s1.
-// Each group of 8 columns is converted in the TMEM row layout (lane = row;
-// the doubles are assembled with integer operations and the scale goes into
-// the exponent) and staged in shared memory; the combination then runs in a
-// column layout (a warp instruction covers 4 rows x 8 consecutive columns),
-// so that the side-input loads and the output stores are coalesced: with one
-// row per lane every access touched 32 cache lines, which dominated the pass.
-__device__ __forceinline__ void final_pass(const TcParams& P, long long off, uint32_t acc64, int row0, int col0, int ncols,
-                                           const unsigned long long* rmax, const unsigned long long* cmax,
-                                           bool mirror, int lane, double* stg, int* ecol, double& sd, double& sx) {
-    if (P.exact) {
-        for (int cc = lane; cc < ncols; cc += 32) ecol[cc] = (col0 + cc < P.N) ? grid_exponent(cmax, col0 + cc) : 0;
-        __syncwarp();
-    }
-    const int erow = (P.exact && row0 + lane < P.M) ? grid_exponent(rmax, row0 + lane) - P.ubase - P.hshift : 0;
-    // the coefficients and pointers are read from the kernel parameters where
-    // they are used (instance b's matrices at +off): no copy held in registers
-    // (measured on the 3072 x 3072 x 4096 FP32-class product: final pass
-    // 400k -> 326k clocks per CTA); the single-chunk pass is faster with its copy
-    const Epilogue& E = P.epi;
-    const bool norms = E.partials != nullptr;
-    // wide layout: a lane owns 4 consecutive columns of a group row, two lanes
-    // a row, 16 rows per pass, so side inputs and outputs move 32 bytes a lane
-    const int cq = (lane & 1) * 4, rh = lane >> 1;
-#pragma unroll 1
-    for (int c = 0; c < ncols; c += STG_COLS) {
-        {
-            uint32_t r[16];
-            tmem_ld16_raw(acc64 + 2 * c, r);
-#pragma unroll
-            for (int j = 0; j < STG_COLS; ++j)
-                stg[lane * STG_LD + j] =
-                    P.exact ? fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
-                                              erow + ecol[c + j])
-                            : float_bits_to_double(r[2 * j]);
-        }
-        __syncwarp();
-        const int col = col0 + c + cq;            // this lane's first column
-        const int nv = min(4, P.N - col);         // its valid columns
-        if (nv > 0) {
-#pragma unroll 1
-            for (int rr = rh; rr < 32; rr += 16) {
-                const int row = row0 + rr;
-                if (row >= P.M) break;
-                double a[4], v1[4], v2[4];
-#pragma unroll
-                for (int k = 0; k < 4; ++k) a[k] = stg[rr * STG_LD + cq + k];
-                load4(E.s1 ? E.s1 + off + (size_t)row * E.ld1 + col : nullptr, nv, v1);
-                load4(E.s2 ? E.s2 + off + (size_t)row * E.ld2 + col : nullptr, nv, v2);
-#pragma unroll
-                for (int o = 0; o < 3; ++o) {
-                    if (o < E.nout) {
-                        const EpiTerm& t = E.o[o];
-                        const int kind = P.okind[o];
-                        double v[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            // (plain arithmetic here: the volatile form of the
-                            // single-chunk pass measured 2 % slower on this pass)
-                            v[k] = times_coef(kind, t.a_acc, a[k]);
-                            if (kind & OUT_S1) v[k] = fma(t.a_s1, v1[k], v[k]);
-                            if (kind & OUT_S2) v[k] = fma(t.a_s2, v2[k], v[k]);
-                            if ((kind & OUT_ID) && row == col + k) v[k] += t.a_id;
-                        }
-                        if (kind & OUT_STORE) {
-                            store4(t.out + off + (size_t)row * t.ld + col, nv, v);
-                            if (mirror) {
-#pragma unroll
-                                for (int k = 0; k < 4; ++k)
-                                    if (k < nv) t.out[off + (size_t)(col + k) * t.ld + row] = v[k];
-                            }
-                        }
-                        if (o == 0 && norms) {
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                if (k < nv) {
-                                    const double dd = v[k] - v1[k];
-                                    sd = fma(dd, dd, sd);
-                                    sx = fma(v1[k], v1[k], sx);
-                                }
-                            }
-                        }
-                    }
-                }
-            }
-        }
-        __syncwarp();   // the staging block is rewritten for the next group
-    }
-}
 
 template <bool LEAN>
 __global__ void __launch_bounds__(THREADS, 1)   // 10 warps: 3 share a sub-partition (16K registers): <= 168 each
@@ -576,8 +428,6 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
     uint64_t* tdone = drain + 1;  // every epilogue warp has finished with TMEM
     uint32_t* tmem_holder = reinterpret_cast<uint32_t*>(tdone + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_holder + 1);
-    double* stg_all = reinterpret_cast<double*>(smem + NST * STAGE_BYTES + 256);
-    int* ecol_all = reinterpret_cast<int*>(smem + NST * STAGE_BYTES + 256 + STG_BYTES);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int tiles_per = P.sym ? P.tiles_m * (P.tiles_m + 1) / 2 : P.tiles_m * P.tiles_n;
@@ -742,15 +592,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             const int slot = b * P.tiles_m * P.tiles_n + nb * P.tiles_m + mb;
             const bool mirror = P.sym && mb != nb;   // also write the transposed tile
             const long long off = (long long)b * P.stride;   // instance b's matrices
-            // the single-chunk pass holds instance b's epilogue in registers
-            // (the multi-chunk pass reads the kernel parameters where used)
-            Epilogue E = P.epi;
-            if constexpr (LEAN) {
-                if (E.s1) E.s1 += off;
-                if (E.s2) E.s2 += off;
-                for (int o = 0; o < 3; ++o)
-                    if (E.o[o].out) E.o[o].out += off;
-            }
+            Epilogue E = P.epi;   // instance b's matrices, held in registers
+            if (E.s1) E.s1 += off;
+            if (E.s2) E.s2 += off;
+            for (int o = 0; o < 3; ++o)
+                if (E.o[o].out) E.o[o].out += off;
             const unsigned long long* rmax = P.rmax ? P.rmax + (size_t)b * P.M : nullptr;
             const unsigned long long* cmax = P.cmax ? P.cmax + (size_t)b * P.N : nullptr;
             int iacc[EPI_COLS];
@@ -853,12 +699,8 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             if (!ok) break;
             double sd = 0.0, sx = 0.0;
-            if constexpr (LEAN) {
-                lean_final_pass(P, E, acc64, m0 + lg * 32 + lane, n0 + cbase, ncols, m0 + lg * 32, rmax, cmax,
-                                ew, mirror, lane, sd, sx);
-            } else
-                final_pass(P, off, acc64, m0 + lg * 32, n0 + cbase, ncols, rmax, cmax, mirror, lane,
-                           stg_all + ew * 32 * STG_LD, ecol_all + ew * EPI_COLS, sd, sx);
+            final_pass(P, E, acc64, m0 + lg * 32 + lane, n0 + cbase, ncols, m0 + lg * 32, rmax, cmax, ew,
+                            mirror, lane, sd, sx);
             if (P.epi.partials) {  // one pair per (tile, epilogue warp): no barrier between warps
 #pragma unroll
                 for (int off = 16; off; off >>= 1) {
@@ -1092,12 +934,10 @@ int num_sms() {
     return g_dev[dev].sms;
 }
 
-// Dynamic shared memory of a kernel: the stages, the barriers, and (for the
-// staged final pass of multi-chunk products) the staging blocks and column
-// exponents; the lean kernel keeps its column exponents in static shared
-// memory and gives the rest to L1.
+// Dynamic shared memory of a kernel: the stages and the barriers (the final
+// pass keeps its column exponents in static shared memory); the rest is L1.
 size_t smem_bytes(bool lean) {
-    return (lean ? LEAN_STAGES : STAGES) * STAGE_BYTES + 1024 + 256 + (lean ? 0 : STG_BYTES + ECOL_BYTES);
+    return (lean ? LEAN_STAGES : STAGES) * STAGE_BYTES + 1024 + 256;
 }
 
 // Set the kernels' shared-memory attribute once per device; false if the
