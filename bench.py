@@ -70,8 +70,8 @@ WORKLOAD = "moore_penrose_rank_deficient_4096x3072_r2304"
 # the FP64-equivalent work each class processed (this workload's products are
 # n x n x m and n x n x n with n = 3072, m = 4096: the captured shapes).
 TRAFFIC_REF_FLOPS = 2.0 * 3072 * 3072 * 4096   # the captured launches' 2MNK
-TRAFFIC_PER_FLOP = {"fp32": (958.1e6 + 63.1e6) / TRAFFIC_REF_FLOPS,
-                    "fp64_tc": (3.268e9 + 63.6e6) / TRAFFIC_REF_FLOPS}
+TRAFFIC_PER_FLOP = {"fp32": (960.9e6 + 75.0e6) / TRAFFIC_REF_FLOPS,
+                    "fp64_tc": (3.269e9 + 75.0e6) / TRAFFIC_REF_FLOPS}
 
 
 def mean_launch_traffic(prec, gemm_flops, tensor_flops, launches):
