@@ -17,6 +17,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1626,17 +1627,37 @@ int run_groups(std::vector<std::unique_ptr<Group>>& groups) {
         int r = group_begin(*g);
         if (r) { g->err = r; rc = r; }
     }
+    // Every group advances on its own: a group whose loop has finished on the
+    // device is completed and issued its next loop (or, once its instances have
+    // stopped, its finish) while the others are still computing, so small
+    // groups do not wait for the largest group's loop at every step.
+    std::vector<char> fin(groups.size(), 0);
+    auto advance = [&](size_t i) {
+        Group& g = *groups[i];
+        if (!g.err && g.active() && g.k < g.max_iter) {
+            if (group_issue(g)) rc = g.err;
+        } else if (!fin[i]) {
+            fin[i] = 1;
+            if (int r = group_finish_issue(g)) { if (!g.err) g.err = r; rc = r; }
+        }
+    };
+    for (size_t i = 0; i < groups.size(); ++i) advance(i);
     for (;;) {
-        bool any = false;
-        for (auto& g : groups)
-            if (g->active() && g->k < g->max_iter) { if (group_issue(*g)) rc = g->err; any = true; }
-        if (!any) break;
-        for (auto& g : groups)
-            if (!g->err && g->active() && g->k < g->max_iter) { if (group_complete(*g)) rc = g->err; }
+        bool pending = false, progressed = false;
+        for (size_t i = 0; i < groups.size(); ++i) {
+            Group& g = *groups[i];
+            if (g.err || !g.in_flight) continue;
+            pending = true;
+            if (cudaEventQuery(g.ev) == cudaErrorNotReady) continue;
+            progressed = true;
+            if (group_complete(g)) { rc = g.err; continue; }
+            advance(i);
+        }
+        if (!pending) break;
+        if (!progressed) std::this_thread::sleep_for(std::chrono::microseconds(20));
     }
-    // the finishes of all groups overlap on their streams, then each is waited for
-    for (auto& g : groups)
-        if (int r = group_finish_issue(*g)) { if (!g->err) g->err = r; rc = r; }
+    for (size_t i = 0; i < groups.size(); ++i)
+        if (!fin[i]) { fin[i] = 1; if (int r = group_finish_issue(*groups[i])) { if (!groups[i]->err) groups[i]->err = r; rc = r; } }
     for (auto& g : groups) {
         if (!g->err && g->finish && cudaStreamSynchronize(g->st) != cudaSuccess) rc = g->err = PINV_ERR_CUDA;
         for (auto& I : g->info) {
