@@ -832,14 +832,18 @@ slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans, const 
     const int T = 8 * S - 1;
     // Integer digit extraction (GB300's FP64 pipe is narrow): x = m 2^E with a
     // 53-bit integer m; U = round(|x| / 2^(ei - T)) <= 2^T is a fixed-point
-    // integer; its bytes (most significant first) become balanced digits from
-    // the least significant up (byte + carry >= 128: digit byte + carry - 256,
-    // carry 1); the top digit takes the last carry and stays <= 128 because
-    // U <= 2^T.  Then q_s = +-digit, |q_s| <= 128.  A NaN or infinity poisons
-    // every slice so that the product reports it.
+    // integer; its balanced base-256 digits (the lower ones in [-128, 127], the
+    // top one <= 128 because U <= 2^T) are read off W = U + 128 (1 + 256 + ...
+    // + 256^(S-2)): digit b (from the bottom) = byte b of W - 128, the top one
+    // W >> 8(S-1) -- the carries of the digit-by-digit rule (byte + carry >=
+    // 128: digit - 256, carry 1) happen in the one addition.  Then q_s =
+    // +-digit, |q_s| <= 128.  A NaN or infinity poisons every slice so that
+    // the product reports it.
     uint32_t lo[8], hi[8];
-    int sgn[8], carry[8];
+    int sgn[8];
     bool bad[8];
+    unsigned long long bias = 0;
+    for (int b = 0; b < S - 1; ++b) bias |= 0x80ull << (8 * b);
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
         const long long bits = __double_as_longlong(v[j]);
@@ -852,10 +856,10 @@ slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans, const 
         if (shift >= 0) U = (unsigned long long)mant << shift;   // <= 2^T <= 2^55 since |x| < 2^ei
         else if (shift > -62) U = (unsigned long long)((mant + (1LL << (-shift - 1))) >> (-shift));
         else U = 0;
+        U += bias;
         lo[j] = (uint32_t)U;
         hi[j] = (uint32_t)(U >> 32);
         sgn[j] = bits < 0 ? -1 : 1;
-        carry[j] = 0;
     }
     for (int s = S - 1; s >= 0; --s) {
         const int b = S - 1 - s;                                     // byte index from the bottom
@@ -863,8 +867,8 @@ slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans, const 
         float f[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            int d = (int)(((b < 4 ? lo[j] >> (8 * b) : hi[j] >> (8 * (b - 4)))) & 0xFFu) + carry[j];
-            if (s > 0 && d >= 128) { d -= 256; carry[j] = 1; } else carry[j] = 0;
+            const uint32_t w = b < 4 ? lo[j] >> (8 * b) : hi[j] >> (8 * (b - 4));
+            const int d = s > 0 ? (int)(w & 0xFFu) - 128 : (int)w;   // the top digit: all of W above
             f[j] = bad[j] ? __int_as_float(0x7FC00000) : (float)(sgn[j] * d) * p2;   // exact: |q| <= 2^7
         }
         uint4 w;   // every value is exact in bf16
