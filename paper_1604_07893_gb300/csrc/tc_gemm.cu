@@ -735,47 +735,56 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 }
 
 // ------------------------------------------------------------------ slicing
-// Rows of op(X) (op(X)[i][k] = trans ? X[k][i] : X[i][k]): mx[i] receives the
-// bit pattern of max_k |op(X)[i][k]| (non-negative doubles order like their
-// bits, so integer max is the floating max, taken on the integer pipe; a NaN
-// or infinity wins and poisons the row).  mx must be zeroed first.
-__global__ void row_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx,
-                                  long long stride) {
-    X += (long long)blockIdx.y * stride;
-    mx += (size_t)blockIdx.y * rows;
-    const int warps = blockDim.x >> 5;
-    const int i = blockIdx.x * warps + (threadIdx.x >> 5);
-    const int lane = threadIdx.x & 31;
-    if (i >= rows) return;
+// One operand's row maxima pass: rows of op(X) (op(X)[i][k] = trans ? X[k][i]
+// : X[i][k]); mx[i] receives the bit pattern of max_k |op(X)[i][k]|
+// (non-negative doubles order like their bits, so integer max is the floating
+// max, taken on the integer pipe; a NaN or infinity wins and poisons the row).
+// gx x gy blocks of 256 threads per instance: one row per warp (trans = 0), or
+// a (32 columns) x (256 rows of X) patch per block, coalesced along the
+// columns and combined with atomicMax into a zeroed mx (trans = 1).
+struct MaxOp {
+    int rows, K;
+    const double* X;
+    int ld, trans;
+    unsigned long long* mx;
+    long long stride;
+    int gx, gy;
+};
+__device__ __forceinline__ void absmax_block(const MaxOp& o, int bx, int by, int bz, unsigned long long (*sh)[33]) {
+    const double* X = o.X + (long long)bz * o.stride;
+    unsigned long long* mx = o.mx + (size_t)bz * o.rows;
     const unsigned long long* Xb = reinterpret_cast<const unsigned long long*>(X);
     constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (!o.trans) {
+        const int i = bx * 8 + w;
+        if (i >= o.rows) return;
+        unsigned long long m = 0;
+        for (int k = lane; k < o.K; k += 32) m = max(m, Xb[(size_t)i * o.ld + k] & ABS);
+        for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
+        if (lane == 0) mx[i] = m;
+        return;
+    }
+    const int i = bx * 32 + lane;
+    const int k0 = by * 256, k1 = min(o.K, k0 + 256);
     unsigned long long m = 0;
-    for (int k = lane; k < K; k += 32) m = max(m, Xb[(size_t)i * ld + k] & ABS);
-    for (int off = 16; off; off >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, off));
-    if (lane == 0) mx[i] = m;
-}
-// Transposed view: X is K x rows; a (32 columns) x (256 rows of X) patch per
-// block, coalesced along the columns, combined with atomicMax.
-__global__ void col_absmax_kernel(int rows, int K, const double* X, int ld, unsigned long long* mx,
-                                  long long stride) {
-    __shared__ unsigned long long sh[8][33];
-    X += (long long)blockIdx.z * stride;
-    mx += (size_t)blockIdx.z * rows;
-    const unsigned long long* Xb = reinterpret_cast<const unsigned long long*>(X);
-    constexpr unsigned long long ABS = 0x7FFFFFFFFFFFFFFFull;
-    const int tx = threadIdx.x, ty = threadIdx.y;   // 32 x 8
-    const int i = blockIdx.x * 32 + tx;
-    const int k0 = blockIdx.y * 256;
-    const int k1 = min(K, k0 + 256);
-    unsigned long long m = 0;
-    if (i < rows)
-        for (int k = k0 + ty; k < k1; k += 8) m = max(m, Xb[(size_t)k * ld + i] & ABS);
-    sh[ty][tx] = m;
+    if (i < o.rows)
+        for (int k = k0 + w; k < k1; k += 8) m = max(m, Xb[(size_t)k * o.ld + i] & ABS);
+    sh[w][lane] = m;
     __syncthreads();
-    if (ty == 0 && i < rows) {
-        for (int j = 1; j < 8; ++j) m = max(m, sh[j][tx]);
+    if (w == 0 && i < o.rows) {
+        for (int j = 1; j < 8; ++j) m = max(m, sh[j][lane]);
         atomicMax(&mx[i], m);
     }
+}
+// The maxima passes of both operands of a product in one launch: blocks
+// [0, a.gx a.gy) serve a, the rest b; blockIdx.y is the instance.
+__global__ void __launch_bounds__(256) absmax_pair_kernel(MaxOp a, MaxOp b) {
+    __shared__ unsigned long long sh[8][33];
+    const int na = a.gx * a.gy;
+    const int id = (int)blockIdx.x;
+    if (id < na) absmax_block(a, id % a.gx, id / a.gx, blockIdx.y, sh);
+    else absmax_block(b, (id - na) % b.gx, (id - na) / b.gx, blockIdx.y, sh);
 }
 
 // out[s][i][k] (bf16, row length Kp, Kp a multiple of 8) for 32 x 64 tiles of
@@ -783,14 +792,22 @@ __global__ void col_absmax_kernel(int rows, int K, const double* X, int ld, unsi
 // row into one 16-byte store per slice plane.  exact = 1: base-256 digit
 // slices of the row-normalised value (slice s holds q_s 2^(8(S-1-s) - T),
 // T = 8S - 1); exact = 0: one round-to-nearest slice.
-__global__ void __launch_bounds__(256)
-slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans, const unsigned long long* mx, int S,
-             int exact, __nv_bfloat16* out, long long stride) {
-    __shared__ double t[64][33];   // transposed staging: t[k_local][i_local]
-    X += (long long)blockIdx.z * stride;                  // instance blockIdx.z
-    out += (size_t)blockIdx.z * S * rows * Kp;
-    if (mx) mx += (size_t)blockIdx.z * rows;
-    const int i0 = blockIdx.y * 32, k0 = blockIdx.x * 64;
+struct SliceOp {
+    int rows, K, Kp;
+    const double* X;
+    int ld, trans;
+    const unsigned long long* mx;
+    int S, exact;
+    __nv_bfloat16* out;
+    long long stride;
+    int gx, gy;   // (Kp / 64) x (rows / 32) tiles per instance
+};
+__device__ __forceinline__ void slice_tile(const SliceOp& o, int bx, int by, int bz, double (*t)[33]) {
+    const int rows = o.rows, K = o.K, Kp = o.Kp, ld = o.ld, trans = o.trans, S = o.S, exact = o.exact;
+    const double* X = o.X + (long long)bz * o.stride;   // instance bz
+    __nv_bfloat16* out = o.out + (size_t)bz * S * rows * Kp;
+    const unsigned long long* mx = o.mx ? o.mx + (size_t)bz * rows : nullptr;
+    const int i0 = by * 32, k0 = bx * 64;
     const int tid = threadIdx.x;
     const int il = tid >> 3, kb = k0 + (tid & 7) * 8;   // row in the tile, first of 8 k
     const int i = i0 + il;
@@ -878,6 +895,16 @@ slice_kernel(int rows, int K, int Kp, const double* X, int ld, int trans, const 
         w.w = pack(__float2bfloat16_rn(f[6]), __float2bfloat16_rn(f[7]));
         dst[s * pstep] = w;
     }
+}
+
+// The slicing of both operands of a product in one launch: blocks
+// [0, a.gx a.gy) serve a, the rest b; blockIdx.y is the instance.
+__global__ void __launch_bounds__(256) slice_pair_kernel(SliceOp a, SliceOp b) {
+    __shared__ double t[64][33];   // transposed staging: t[k_local][i_local]
+    const int na = a.gx * a.gy;
+    const int id = (int)blockIdx.x;
+    if (id < na) slice_tile(a, id % a.gx, id / a.gx, blockIdx.y, t);
+    else slice_tile(b, (id - na) % b.gx, (id - na) / b.gx, blockIdx.y, t);
 }
 
 // ------------------------------------------------------------------ host side
@@ -1012,20 +1039,27 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
     if (mode.exact) {
         // per-row maxima of op(A) and of op(B)^T (= columns of op(B))
         if (cudaMemsetAsync(ea, 0, 8 * (size_t)batch * (M + N), st) != cudaSuccess) return -1;
-        dim3 blk(32, 8);
-        if (!transA) row_absmax_kernel<<<dim3((M + 7) / 8, batch), 256, 0, st>>>(M, K, A, lda, ea, stride);
-        else col_absmax_kernel<<<dim3((M + 31) / 32, (K + 255) / 256, batch), blk, 0, st>>>(M, K, A, lda, ea, stride);
-        if (transB) row_absmax_kernel<<<dim3((N + 7) / 8, batch), 256, 0, st>>>(N, K, B, ldb, eb, stride);
-        else col_absmax_kernel<<<dim3((N + 31) / 32, (K + 255) / 256, batch), blk, 0, st>>>(N, K, B, ldb, eb, stride);
-        *kernels += 2;
+        // both operands in one launch (the rows of op(A) and of op(B)^T)
+        auto maxop = [&](int rows, const double* X, int ld, int colkind, unsigned long long* mx) {
+            MaxOp o{rows, K, X, ld, colkind, mx, stride, 0, 0};
+            o.gx = colkind ? (rows + 31) / 32 : (rows + 7) / 8;
+            o.gy = colkind ? (K + 255) / 256 : 1;
+            return o;
+        };
+        const MaxOp oa = maxop(M, A, lda, transA ? 1 : 0, ea), ob = maxop(N, B, ldb, transB ? 0 : 1, eb);
+        absmax_pair_kernel<<<dim3(oa.gx * oa.gy + ob.gx * ob.gy, batch), 256, 0, st>>>(oa, ob);
+        *kernels += 1;
     }
     {
-        dim3 ga((Kp + 63) / 64, (M + 31) / 32, batch), gb((Kp + 63) / 64, (N + 31) / 32, batch);
-        slice_kernel<<<ga, 256, 0, st>>>(M, K, Kp, A, lda, transA ? 1 : 0, mode.exact ? ea : nullptr,
-                                         mode.S, mode.exact, sa, stride);
-        slice_kernel<<<gb, 256, 0, st>>>(N, K, Kp, B, ldb, transB ? 0 : 1, mode.exact ? eb : nullptr,
-                                         mode.S, mode.exact, sb, stride);
-        *kernels += 2;
+        auto sliceop = [&](int rows, const double* X, int ld, int trans, const unsigned long long* mx,
+                           __nv_bfloat16* out) {
+            return SliceOp{rows, K, Kp, X, ld, trans, mode.exact ? mx : nullptr, mode.S, mode.exact, out, stride,
+                           (Kp + 63) / 64, (rows + 31) / 32};
+        };
+        const SliceOp sa_op = sliceop(M, A, lda, transA ? 1 : 0, ea, sa);
+        const SliceOp sb_op = sliceop(N, B, ldb, transB ? 0 : 1, eb, sb);
+        slice_pair_kernel<<<dim3(sa_op.gx * sa_op.gy + sb_op.gx * sb_op.gy, batch), 256, 0, st>>>(sa_op, sb_op);
+        *kernels += 1;
     }
     CUtensorMap ma, mb;
     if (!make_map(&ma, sa, batch * mode.S, M, Kp, BM) || !make_map(&mb, sb, batch * mode.S, N, Kp, BN))
