@@ -134,6 +134,7 @@ __device__ __forceinline__ int grid_exponent(const unsigned long long* mx, int i
 // every call and discard it (predication).
 __device__ __noinline__ double fixed_to_double_slow(long long V, int E) { return ldexp((double)V, E); }
 __device__ __noinline__ double float_to_double_slow(uint32_t f) { return (double)__uint_as_float(f); }
+__device__ __noinline__ float double_to_float_slow(double x) { return __double2float_rn(x); }
 
 
 // One path for every magnitude (normalise, keep 53 bits, round the 11 below
@@ -156,11 +157,32 @@ __device__ __forceinline__ double fixed_to_double(long long V, int E) {
 // values.
 __device__ __forceinline__ double float_bits_to_double(uint32_t f) {
     const uint32_t ex = (f >> 23) & 0xFFu;
-    if (ex == 0 || ex == 0xFFu) return float_to_double_slow(f);   // zero, subnormal, inf, NaN
+    if ((f & 0x7FFFFFFFu) == 0) return __longlong_as_double((long long)((unsigned long long)f << 32));   // +-0
+    if (ex == 0 || ex == 0xFFu) return float_to_double_slow(f);   // subnormal, inf, NaN
     const unsigned long long bits = ((unsigned long long)(f & 0x80000000u) << 32) |
                                     ((unsigned long long)(ex - 127 + 1023) << 52) |
                                     ((unsigned long long)(f & 0x7FFFFFu) << 29);
     return __longlong_as_double((long long)bits);
+}
+
+// x rounded to FP32 (to nearest, ties to even) by integer operations on its
+// bit pattern: the 29 fraction bits that FP32 lacks are dropped and the 23 it
+// keeps rounded up when the dropped part is above half an FP32 unit, or
+// exactly half with an odd last bit (a carry out of the fraction raises the
+// exponent, and past the largest finite FP32 gives infinity, as IEEE 754
+// rounding does).  Zeros stay exact; values that leave FP32's normal range
+// (and infinities, NaNs) take the library conversion.
+__device__ __forceinline__ float double_to_float(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned long long mag = b & 0x7FFFFFFFFFFFFFFFull;
+    const uint32_t sign = (uint32_t)(b >> 32) & 0x80000000u;
+    if (mag == 0) return __uint_as_float(sign);
+    const int e = (int)(mag >> 52) - 1023 + 127;   // FP32 biased exponent
+    if (e < 1 || e > 254) return double_to_float_slow(x);
+    const uint32_t rem = (uint32_t)mag & 0x1FFFFFFFu;   // the 29 bits dropped
+    uint32_t f = ((uint32_t)e << 23) | (uint32_t)((mag >> 29) & 0x7FFFFFu);
+    f += (rem > 0x10000000u || (rem == 0x10000000u && (f & 1u))) ? 1u : 0u;
+    return __uint_as_float(sign | f);
 }
 
 
@@ -333,10 +355,9 @@ __device__ __forceinline__ void final_pass(const TcParams& P, const Epilogue& E,
         }
 #pragma unroll
         for (int j = 0; j < 8; ++j) {
-            // the tile sum: fixed point (exact modes) or FP32 bits (BF16)
-            a[j] = P.exact ? fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
-                                                     erow + (rmax ? ecol[c + j] : 0))
-                           : float_bits_to_double(r[2 * j]);
+            // the tile sum in fixed point (exact modes)
+            a[j] = fixed_to_double((long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j]),
+                                   erow + (rmax ? ecol[c + j] : 0));
             if (!v1wide) v1[j] = (s1 && j < ncol) ? s1[cb + j] : 0.0;
         }
         const bool diag = cb < row0w + 32 && cb + 8 > row0w;   // the diagonal crosses this group
@@ -413,7 +434,123 @@ __device__ __forceinline__ void final_pass(const TcParams& P, const Epilogue& E,
 }
 
 
-template <bool LEAN>
+// Final pass of a BF16 product (one slice pair, FP32 accumulation): the same
+// combination, outputs and stop-norm partials as final_pass, formed in FP32.
+// The tile sum is already an FP32 value whose error is that of BF16 operands
+// (relative 2^-8 and more); side inputs and coefficients are rounded to FP32
+// (2^-24) and the FP32 result is stored exactly as a double.  No FP64
+// instruction runs per element: the conversions are integer operations and
+// the arithmetic is on the FP32 pipe, where GB300 issues about 64 times the
+// FP64 rate.
+__device__ __forceinline__ void final_pass_f32(const TcParams& P, const Epilogue& E, uint32_t acc64, int row,
+                                               int col0, int ncols, int row0w, bool mirror, double& sd,
+                                               double& sx) {
+    const bool rowok = row < P.M;
+    const double* s1 = (E.s1 && rowok) ? E.s1 + (size_t)row * E.ld1 : nullptr;
+    const double* s2 = (E.s2 && rowok) ? E.s2 + (size_t)row * E.ld2 : nullptr;
+    const bool norms = E.partials != nullptr;
+    float fsd = 0.0f, fsx = 0.0f;
+#pragma unroll 1
+    for (int c = 0; c < ncols; c += 8) {   // 8 columns per TMEM load
+        uint32_t r[16];
+        tmem_ld16_raw(acc64 + 2 * c, r);
+        if (!rowok) continue;
+        const int cb = col0 + c;
+        const int ncol = min(8, P.N - cb);
+        if (ncol <= 0) continue;
+        float v1[8];
+        {
+            double d1[8];
+            if (s1 && ncol == 8 && ((unsigned)reinterpret_cast<uintptr_t>(s1 + cb) & 31u) == 0) {
+                ld_global_v4(s1 + cb, d1);
+                ld_global_v4(s1 + cb + 4, d1 + 4);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) d1[j] = (s1 && j < ncol) ? s1[cb + j] : 0.0;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v1[j] = double_to_float(d1[j]);
+        }
+        const bool diag = cb < row0w + 32 && cb + 8 > row0w;
+        const int dg = row - cb;
+#pragma unroll
+        for (int o = 0; o < 3; ++o) {
+            if (o < E.nout) {
+                const EpiTerm& t = E.o[o];
+                const int kind = P.okind[o];
+                double* out = (kind & OUT_STORE) ? t.out + (size_t)row * t.ld + cb : nullptr;
+                float v[8];
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const float a = __uint_as_float(r[2 * j]);
+                    v[j] = (kind & OUT_NEG) ? -a : a;
+                }
+                if (kind & OUT_MUL) {
+                    const float ca = double_to_float(t.a_acc);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] *= ca;
+                }
+                if (kind & OUT_S1) {
+                    const float c1 = double_to_float(t.a_s1);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = fmaf(c1, v1[j], v[j]);
+                }
+                if ((kind & OUT_S2) && s2 != nullptr) {
+                    const float c2 = double_to_float(t.a_s2);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) v[j] = fmaf(c2, double_to_float(j < ncol ? s2[cb + j] : 0.0), v[j]);
+                }
+                if ((kind & OUT_ID) && diag && dg >= 0 && dg < 8) {
+                    const float ci = double_to_float(t.a_id);
+#pragma unroll
+                    for (int j = 0; j < 8; ++j)
+                        if (j == dg) v[j] += ci;
+                }
+                if (out) {
+                    double w[8];
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) w[j] = float_bits_to_double(__float_as_uint(v[j]));
+                    const unsigned mis = (unsigned)reinterpret_cast<uintptr_t>(out) & 31u;
+                    if (ncol == 8 && mis == 0) {
+                        st_global_v4(out, w[0], w[1], w[2], w[3]);
+                        st_global_v4(out + 4, w[4], w[5], w[6], w[7]);
+                    } else if (ncol == 8 && (mis & 15u) == 0) {
+#pragma unroll
+                        for (int j = 0; j < 8; j += 2)
+                            *reinterpret_cast<double2*>(out + j) = make_double2(w[j], w[j + 1]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (j < ncol) out[j] = w[j];
+                    }
+                    if (mirror) {
+#pragma unroll
+                        for (int j = 0; j < 8; ++j)
+                            if (j < ncol) t.out[(size_t)(cb + j) * t.ld + row] = w[j];
+                    }
+                }
+                if (o == 0 && norms) {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        if (j < ncol) {
+                            const float dd = v[j] - v1[j];
+                            fsd = fmaf(dd, dd, fsd);
+                            fsx = fmaf(v1[j], v1[j], fsx);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    sd = float_bits_to_double(__float_as_uint(fsd));
+    sx = float_bits_to_double(__float_as_uint(fsx));
+}
+
+// LEAN: products of one K-chunk per pair (fewer stages); EXACT: the slice
+// classes (fixed-point tile sums), else BF16 (FP32 accumulator, FP32 final
+// pass), a separate instantiation so that the two final passes do not share
+// one register allocation.
+template <bool LEAN, bool EXACT>
 __global__ void __launch_bounds__(THREADS, 1)   // 10 warps: 3 share a sub-partition (16K registers): <= 168 each
 tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB,
                const __grid_constant__ TcParams P) {
@@ -567,7 +704,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
         // pass turns V into a double with integer operations; FP64
         // instructions -- about 2 per clock per SM on GB300 -- are left to the
         // fused combination only.  BF16 products (one unit) keep the FP32
-        // accumulator bits.
+        // accumulator bits, and their final pass forms the combination in FP32.
         const int lg = warp & 3;                 // TMEM lane group of this warp
         const int half = (warp - 2) >> 2;        // which BN/2 columns of the tile
         const int ew = warp - 2;                 // epilogue warp index
@@ -618,7 +755,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                 const uint32_t taddr = lane_base + buf * BN + cbase;   // first 32 columns
                 const uint32_t taddr2 = narrow ? lane_base + buf * BN + EPI_COLS + cbase : taddr + 32;
                 const int uexp = 14 + 8 * d;   // slice products q q' 2^-(14+8d): accumulator / unit
-                const bool horner = P.exact && d <= P.dint;
+                const bool horner = EXACT && d <= P.dint;
                 // exact diagonals: the accumulator in integer units; later ones:
                 // FP32 in units of 2^-ubase
                 const float unit = ldexpf(1.0f, horner ? uexp : P.ubase);
@@ -636,7 +773,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
 #pragma unroll
                     for (int j = 0; j < 32; ++j) {
                         if (horner) iacc[hh + j] += __float2int_rn(__uint_as_float(r[j]) * unit);
-                        else if (P.exact)
+                        else if (EXACT)
                             iacc[hh + j] = __float_as_int(fmaf(__uint_as_float(r[j]), unit, __int_as_float(iacc[hh + j])));
                         else iacc[hh + j] = (int)r[j];   // one drain only: keep the FP32 bits
                     }
@@ -680,7 +817,7 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
                             if (have64) tmem_ld32_raw(acc64 + 2 * c, r);
 #pragma unroll
                             for (int j = 0; j < 16; ++j) {
-                                if (P.exact) {
+                                if (EXACT) {
                                     long long V = have64 ? (long long)(((unsigned long long)r[2 * j + 1] << 32) | r[2 * j])
                                                          : 0LL;
                                     V = V * hmul + __float2ll_rn(__int_as_float(iacc[c + j]) * fh);
@@ -699,8 +836,11 @@ tc_gemm_kernel(const __grid_constant__ CUtensorMap mapA, const __grid_constant__
             }
             if (!ok) break;
             double sd = 0.0, sx = 0.0;
-            final_pass(P, E, acc64, m0 + lg * 32 + lane, n0 + cbase, ncols, m0 + lg * 32, rmax, cmax, ew,
-                            mirror, lane, sd, sx);
+            if (EXACT)
+                final_pass(P, E, acc64, m0 + lg * 32 + lane, n0 + cbase, ncols, m0 + lg * 32, rmax, cmax, ew,
+                           mirror, lane, sd, sx);
+            else
+                final_pass_f32(P, E, acc64, m0 + lg * 32 + lane, n0 + cbase, ncols, m0 + lg * 32, mirror, sd, sx);
             if (P.epi.partials) {  // one pair per (tile, epilogue warp): no barrier between warps
 #pragma unroll
                 for (int off = 16; off; off >>= 1) {
@@ -977,10 +1117,11 @@ bool prepare_kernels() {
     const int dev = current_device();
     std::lock_guard<std::mutex> lk(g_dev_mu);
     if (g_dev[dev].attr) return true;
-    const void* kernels[2] = {(const void*)tc_gemm_kernel<false>, (const void*)tc_gemm_kernel<true>};
-    for (int i = 0; i < 2; ++i) {
+    const void* kernels[3] = {(const void*)tc_gemm_kernel<false, true>, (const void*)tc_gemm_kernel<true, true>,
+                              (const void*)tc_gemm_kernel<true, false>};
+    for (int i = 0; i < 3; ++i) {
         const void* k = kernels[i];
-        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(i == 1));
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes(i >= 1));
         cudaFuncAttributes fa;
         if (cudaFuncGetAttributes(&fa, k) == cudaSuccess && fa.maxThreadsPerBlock < THREADS) {
             std::fprintf(stderr, "tc_gemm: kernel uses %d registers; at most %d threads per block fit\n",
@@ -1132,8 +1273,9 @@ int tc_gemm(int M, int N, int K, const double* A, int lda, bool transA, const do
         // persistent (one CTA per SM walking the tiles) unless the caller wants
         // the SMs released after every tile (so higher-priority streams get in)
         const int grid = (one_tile_per_cta || all_tiles < num_sms()) ? all_tiles : num_sms();
-        if (lean) tc_gemm_kernel<true><<<grid, THREADS, smem_bytes(true), st>>>(ma, mb, P);
-        else tc_gemm_kernel<false><<<grid, THREADS, smem_bytes(false), st>>>(ma, mb, P);
+        if (!mode.exact) tc_gemm_kernel<true, false><<<grid, THREADS, smem_bytes(true), st>>>(ma, mb, P);
+        else if (lean) tc_gemm_kernel<true, true><<<grid, THREADS, smem_bytes(true), st>>>(ma, mb, P);
+        else tc_gemm_kernel<false, true><<<grid, THREADS, smem_bytes(false), st>>>(ma, mb, P);
     }
     if (ev_end) cudaEventRecord(ev_end, st);
     *kernels += 1;

@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 
 from oracle import hyperpower as H
+from oracle import precision as PM
 from paper_1604_07893_gb300 import workloads as W
 from tests.helpers import drazin_closed_form, pinv_closed_form, rel
 
@@ -108,6 +109,32 @@ def test_one_loop_fp64_tc_matches_naive_step(handle, m, n):
         got = got.cpu().numpy()
         assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
         X = ref
+
+
+@pytest.mark.parametrize("m,n", [(200, 136), (136, 200)])
+def test_one_bf16_loop_matches_the_bf16_model(handle, m, n):
+    """One loop with BF16 products (FP32 accumulation; the linear combinations
+    formed in FP32 in the final pass), against the CPU model of the same loop
+    (oracle/precision.py: the same rounded operands, combinations in FP64)
+    and the exact FP64 step.  Ragged tiles on both sides; the iterate is two
+    exact loops into the growth phase, so that every term of the loop matters.
+    A dropped or mis-signed term moves the result by O(1); the BF16 rounding
+    itself moves it by a few per cent at most."""
+    w = W.rectangular(m, n, None, 1.0, 1e-2, seed=m + 3 * n)
+    side = H.choose_side(m, n)
+    X = H.x0_moore_penrose(w.A, 1.0 / w.s[0] ** 2)
+    for _ in range(2):
+        X = H.hyperpower_step(w.A, X, side=side)
+    ref = H.hyperpower_step(w.A, X, side=side)
+    model = PM.pm_loop(w.A, X, PM.bf16_product, side)
+    got, step = handle.step(dev(w.A), dev(X), prec="mixed_bf16")
+    got = got.cpu().numpy()
+    e_model = rel(model, ref)
+    assert e_model < 0.05
+    assert rel(got, model) <= 0.25 * e_model + 1e-4
+    assert rel(got, ref) <= 1.5 * e_model + 1e-4
+    step_model = float(np.linalg.norm(model - X) / np.linalg.norm(X))
+    assert abs(step - step_model) <= 1e-2 * step_model
 
 
 @pytest.mark.parametrize("variant", ["plain", "stabilized"])
