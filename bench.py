@@ -65,13 +65,13 @@ METRIC = "pseudoinverses/s at 1e-9 Penrose residual"
 UNIT = "solves/s"
 WORKLOAD = "moore_penrose_rank_deficient_4096x3072_r2304"
 # dram__bytes_read.sum + dram__bytes_write.sum of one 3072x3072x4096 launch of
-# the dominant kernel in each product class (one ncu --set full capture of the
-# current kernel per class), per FP64-equivalent flop of that launch; a solve's mean launch weights them by
+# the dominant kernel in each product class (one ncu capture of the current
+# kernel per class), per FP64-equivalent flop of that launch; a solve's mean launch weights them by
 # the FP64-equivalent work each class processed (this workload's products are
 # n x n x m and n x n x n with n = 3072, m = 4096: the captured shapes).
 TRAFFIC_REF_FLOPS = 2.0 * 3072 * 3072 * 4096   # the captured launches' 2MNK
-TRAFFIC_PER_FLOP = {"fp32": (960.9e6 + 75.0e6) / TRAFFIC_REF_FLOPS,
-                    "fp64_tc": (3.269e9 + 75.0e6) / TRAFFIC_REF_FLOPS}
+TRAFFIC_PER_FLOP = {"fp32": (964.2e6 + 62.8e6) / TRAFFIC_REF_FLOPS,
+                    "fp64_tc": (3.277e9 + 62.8e6) / TRAFFIC_REF_FLOPS}
 
 
 def mean_launch_traffic(prec, gemm_flops, tensor_flops, launches):
@@ -79,7 +79,7 @@ def mean_launch_traffic(prec, gemm_flops, tensor_flops, launches):
     figures: the FP64-class and FP32-class work (28 and 10 slice products per
     FP64-equivalent flop) are separated from the totals.  None where the solve
     ran classes without a captured figure (BF16, native FP64)."""
-    if not launches or prec not in ("fp32", "fp64_tc"):
+    if not launches or prec not in ("fp32", "fp32_refine", "fp64_tc"):
         return None
     if prec == "fp64_tc":
         f64, f32 = gemm_flops, 0.0
@@ -238,7 +238,10 @@ def cpu_oracle_sample(A, alpha, loops_per_solve=ORACLE_LOOPS, stab_loops=ORACLE_
             "s_per_solve": per_solve}
 
 
-SCHEDULES = {"fp32": "fp32-class products while the step is >= 1, then fp64-class; finish fp64-class",
+SCHEDULES = {"fp32_refine": "fp32-class loops while the step is >= 1; after the first loop below 1, X A X in "
+                            "fp32 class, then fp64-class order-2 refinement steps until a step is below 1e-5; "
+                            "finish fp64-class",
+             "fp32": "fp32-class products while the step is >= 1, then fp64-class; finish fp64-class",
              "fp64_tc": "fp64-class products throughout",
              "fp64": "native fp64 (DMMA) products throughout",
              "mixed_bf16": "bf16 while the step is > 0.5, fp32-class, then fp64-class"}
@@ -360,6 +363,7 @@ def run_ours(args):
         ms = s0.elapsed_time(s1) / reps
         return {"value": 1e3 / ms, "unit": UNIT, "ms_per_solve": ms, "loops": io["iters"],
                 "stabilized_loops": io["stabilized_loops"], "penrose_max": max(co["penrose"])}
+    fp32_loops = other_arm("fp32", 3) if args.prec == "fp32_refine" and not args.no_fp64 else None
     fp64_tc = other_arm("fp64_tc", 3) if args.prec != "fp64_tc" and not args.no_fp64 else None
     fp64 = other_arm("fp64", 1) if args.prec != "fp64" and not args.no_fp64 else None
 
@@ -387,7 +391,10 @@ def run_ours(args):
     p99 = sorted_ms[min(len(sorted_ms) - 1, int(math.ceil(0.99 * len(sorted_ms))) - 1)]
     cpu = None
     if not args.no_cpu and world == 1:   # the loop counts this solve ran (the oracle runs the same)
-        cpu = cpu_oracle_sample(w.A, alpha, infos[-1]["iters"], infos[-1]["stabilized_loops"])
+        # (the refine schedule's order-2 steps have no counterpart in the oracle,
+        # which converges in its own ORACLE_LOOPS loops)
+        cpu = (cpu_oracle_sample(w.A, alpha) if args.prec == "fp32_refine" else
+               cpu_oracle_sample(w.A, alpha, infos[-1]["iters"], infos[-1]["stabilized_loops"]))
         cpu.pop("s_per_solve", None)
 
     line = {
@@ -396,13 +403,14 @@ def run_ours(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp64": "f64", "fp64_tc": "bf16 slices (fp64-class)",
                   "fp32": "bf16 slices (fp32-class, then fp64-class)",
+                  "fp32_refine": "bf16 slices (fp32-class loops, fp64-class refinement)",
                   "mixed_bf16": "bf16 + bf16 slices"}[args.prec],
         "data": "synthetic",
         "config": bench_config(args.prec, world),
         "latency_ms": {"p50": p50, "p99": p99},
         "accuracy": {"penrose_max": penrose, "sampled_rows_rel_err": row_err, "meets_1e-9": ok,
                      "loops": infos[-1]["iters"], "stabilized_loops": infos[-1]["stabilized_loops"],
-                     "loop_classes": ["fp64" if p == 0 else {1: "bf16", 3: "fp32-class", 4: "fp64-class"}[p]
+                     "loop_classes": ["fp64" if p == 0 else {1: "bf16", 3: "fp32-class", 4: "fp64-class", 6: "fp64-class order-2"}[p]
                                       for p in infos[-1]["precision"]]},
         "e2e": {"value": world / e2e_s if ok else 0.0, "unit": UNIT,
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": N * M * 8},
@@ -414,6 +422,7 @@ def run_ours(args):
                      "gemm_launches": gemm_launches, "gemm_share_of_step": gemm_ms / total_ms},
         "clocks": clocks,
         "cpu_baseline": cpu,
+        "fp32_loops": fp32_loops,
         "fp64_tc": fp64_tc,
         "fp64_gpu": fp64,
     }
@@ -523,9 +532,11 @@ def _roofline(infos, peaks_prec="bf16"):
 def run_drazin(args):
     """Drazin inverse of a 2048 x 2048 index-2 matrix (C 1536 x 1536, 256 2x2
     Jordan blocks), X0 = A^2 / Tr(A^3), order-18 stop (step < 1e-2), finish
-    A^2 X^5 A^2 + one order-2 step.  The line's value is the mixed form
-    (FP32-class growth loops, then FP64-class); every product FP64-class on the
-    tensor cores (fp64_tc) and native FP64 (fp64_gpu) are timed beside it."""
+    A^2 X^5 A^2 + one order-2 step.  The line's value is the refinement form
+    (FP32-class loops, X A X, FP64-class order-2 steps, the finish); the loop
+    schedule (FP32-class growth loops, then FP64-class loops), every product
+    FP64-class on the tensor cores (fp64_tc) and native FP64 (fp64_gpu) are
+    timed beside it."""
     import torch
     from oracle import hyperpower as H
     from paper_1604_07893_gb300 import Handle, workloads as W
@@ -542,7 +553,7 @@ def run_drazin(args):
     res = {}
     roof = None
     total_ms = None
-    for prec in ("fp32", "fp64_tc", "fp64"):
+    for prec in ("fp32_refine", "fp32", "fp64_tc", "fp64"):
         kw = dict(kind="drazin", drazin_index=2, alpha=0.0, tol=1e-2, stop="order18", prec=prec, finish="clean")
         for _ in range(args.warmup if prec != "fp64" else 1):
             h.solve(A, X, **kw)
@@ -550,7 +561,7 @@ def run_drazin(args):
         for _ in range(args.steps if prec != "fp64" else 1):
             e0, e1 = _events(st)
             e0.record(st)
-            _, info = h.solve(A, X, profile=(prec == "fp32"), **kw)
+            _, info = h.solve(A, X, profile=(prec == "fp32_refine"), **kw)
             e1.record(st)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -560,9 +571,9 @@ def run_drazin(args):
         res[prec] = {"value": 1e3 / statistics.mean(times), "ms_per_solve": statistics.mean(times),
                      "loops": info["iters"], "drazin_residuals": cinfo["drazin"], "sampled_rows_rel_err": err,
                      "meets_1e-9": bool(err <= 1e-9 and max(cinfo["drazin"]) <= 1e-9),
-                     "loop_classes": ["fp64" if p == 0 else {1: "bf16", 3: "fp32-class", 4: "fp64-class"}[p]
+                     "loop_classes": ["fp64" if p == 0 else {1: "bf16", 3: "fp32-class", 4: "fp64-class", 6: "fp64-class order-2"}[p]
                                       for p in info["precision"]]}
-        if prec == "fp32":
+        if prec == "fp32_refine":
             roof = _roofline(infos)
             total_ms = sum(times)
             if roof:
@@ -593,13 +604,13 @@ def run_drazin(args):
     t_loop = time.perf_counter() - t0
     loops = res["fp32"]["loops"] + 2
     _emit({"metric": "Drazin inverses/s at 1e-9 (2048x2048, index 2)",
-           "value": res["fp32"]["value"] if res["fp32"]["meets_1e-9"] else 0.0,
+           "value": res["fp32_refine"]["value"] if res["fp32_refine"]["meets_1e-9"] else 0.0,
            "unit": "solves/s", "n_gpus": 1, "higher_is_better": True, "data": "synthetic",
-           "dtype": "bf16 slices (fp32-class, then fp64-class)",
+           "dtype": "bf16 slices (fp32-class loops, fp64-class refinement)",
            "config": {"workload": "drazin_2048_index2", "n_nilpotent": 512, "spectrum": "sector |arg| <= pi/8",
-                      "prec": "fp32", "schedule": SCHEDULES["fp32"], "stop": "order18", "tol": 1e-2,
+                      "prec": "fp32_refine", "schedule": SCHEDULES["fp32_refine"], "stop": "order18", "tol": 1e-2,
                       "steps": args.steps, "warmup": args.warmup},
-           "mixed": res["fp32"], "roofline": roof,
+           "mixed": res["fp32_refine"], "fp32_loops": res["fp32"], "roofline": roof,
            "fp64_tc": res["fp64_tc"], "fp64_gpu": res["fp64"], "full_annulus_spectrum": res["annulus_literal"],
            "cpu_baseline": {"value": 1.0 / (t_loop * loops), "unit": "solves/s", "kind": "oracle",
                             "cores": len(os.sched_getaffinity(0)),
@@ -1146,7 +1157,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--prec", default="fp32", choices=["fp32", "fp64_tc", "fp64", "mixed_bf16"])
+    ap.add_argument("--prec", default="fp32_refine", choices=["fp32_refine", "fp32", "fp64_tc", "fp64", "mixed_bf16"])
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--workload", default="mp4096x3072",

@@ -188,6 +188,14 @@ def xax(A: np.ndarray, X: np.ndarray, mul, side: str) -> np.ndarray:
     return mul(X, mul(A, X))
 
 
+def order2_step(A: np.ndarray, X: np.ndarray, mul, side: str) -> np.ndarray:
+    """One step of the hyperpower family with p = 2 (Eq. hyper): X + (I - XA) X
+    (left residual) or X + X (I - AX) (right), both products formed by ``mul``."""
+    if side == "left":
+        return X + mul(np.eye(X.shape[0]) - mul(X, A), X)
+    return X + mul(X, np.eye(A.shape[0]) - mul(A, X))
+
+
 def finish_moore_penrose(A: np.ndarray, X: np.ndarray, mul, side: str, step: str = "order2") -> np.ndarray:
     """The build's finish: X <- (XA)^T X (AX)^T, then one order-2 step
     X + (I - XA) X (or X + X (I - AX)), or one order-18 loop (step='order18')."""

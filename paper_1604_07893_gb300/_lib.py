@@ -20,7 +20,8 @@ ERRORS = {-1: "PINV_ERR_ARG", -2: "PINV_ERR_BUDGET", -3: "PINV_ERR_NONFINITE", -
           -9: "PINV_ERR_BUSY"}
 KIND = {"moore_penrose": 0, "drazin": 1, "outer_g": 2, "drazin_normal": 3}
 STOP = {"rel_fro": 0, "paper": 1, "order18": 2}
-PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3, "fp64_tc": 4, "bf16_fp32": 5}
+PREC = {"fp64": 0, "mixed_bf16": 1, "mixed_fp8": 2, "fp32": 3, "fp64_tc": 4, "bf16_fp32": 5,
+        "fp32_refine": 6}
 VARIANT = {"plain": 0, "stabilized": 1}
 FINISH = {None: 0, "none": 0, "clean": 1}
 HISTORY = 128

@@ -548,8 +548,11 @@ int validate(const pinv_desc* d) {
         return PINV_ERR_ARG;
     if (d->max_iter < 0 || d->max_iter > PINV_HISTORY) return PINV_ERR_ARG;
     if (d->prec != PINV_PREC_FP64 && d->prec != PINV_PREC_MIXED_BF16 && d->prec != PINV_PREC_FP32 &&
-        d->prec != PINV_PREC_FP64_TC && d->prec != PINV_PREC_BF16_FP32)
+        d->prec != PINV_PREC_FP64_TC && d->prec != PINV_PREC_BF16_FP32 && d->prec != PINV_PREC_FP32_REFINE)
         return PINV_ERR_ARG;
+    // the refinement steps end with the finish (its projection removes the
+    // first-order rounding that order-2 steps do not contract)
+    if (d->prec == PINV_PREC_FP32_REFINE && d->finish != PINV_FINISH_CLEAN) return PINV_ERR_ARG;
     if (d->variant != PINV_VARIANT_PLAIN && d->variant != PINV_VARIANT_STABILIZED) return PINV_ERR_ARG;
     if (d->finish != PINV_FINISH_NONE && d->finish != PINV_FINISH_CLEAN) return PINV_ERR_ARG;
     // BF16/FP32-class loops leave rounding in the block the iteration does not
@@ -1070,6 +1073,51 @@ int precond_one(pinv_handle* h, const pinv_precond_desc* p, cudaStream_t st, pin
     return info->status = rc;
 }
 
+// The refinement of PINV_PREC_FP32_REFINE, after its last FP32-class loop
+// (X[cur] holds that loop's iterate, X[cur ^ 1] is free):
+//  1. X <- X A X in FP32 class (Section 7's stabilising product; XAX = X holds
+//     for every outer inverse, Eq. 1): it removes the loop's first-order
+//     rounding outside R(X) and N(X), which an order-2 step would double
+//     (order p multiplies the blocks the iteration does not contract by p,
+//     Theorem 6.2);
+//  2. order-2 steps X <- X + (I - XA) X (Eq. hyper, p = 2) in FP64 class: the
+//     step's relative change e is the error of its input, its output's range
+//     error is about e^2, so the steps stop after the first with e < 1e-5.
+// The kept iterate ends in X[cur].  Returns PINV_OK, or an error status.
+constexpr int kRefineMaxSteps = 8;
+constexpr double kRefineTol = 1e-5;
+
+int refine_steps(Ctx& c, int& cur, pinv_info* info, int* reason) {
+    c.prec_k = TC_FP32;
+    int parts = stabilise_f64(c, c.X[cur], c.X[cur ^ 1], c.X[2]);
+    if (parts < 0) return PINV_ERR_CUDA;
+    ++info->stabilized_loops;
+    c.prec_k = TC_FP64;
+    const double* src = c.X[2];
+    for (int j = 0; j < kRefineMaxSteps; ++j) {
+        parts = ns_step_f64(c, src, c.X[cur ^ 1]);
+        if (parts < 0) return PINV_ERR_CUDA;
+        double dx2, x2;
+        int rc = read_norms(c, parts, &dx2, &x2);
+        if (rc) return rc;
+        cur ^= 1;
+        src = c.X[cur];
+        const double e = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
+        const int k = info->loops_run++;
+        if (k < PINV_HISTORY) {
+            info->history[k] = e;
+            info->precision[k] = 6;
+        }
+        ++info->iters;
+        info->rel_step = e;
+        if (!std::isfinite(e)) return PINV_ERR_NONFINITE;
+        if (e > 1e3) return PINV_ERR_DIVERGED;
+        if (e < kRefineTol) { *reason = 0; return PINV_OK; }
+    }
+    *reason = 2;
+    return PINV_ERR_MAXITER;
+}
+
 int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* info, bool cplx = false) {
     auto t0 = std::chrono::steady_clock::now();
     std::memset(info, 0, sizeof(*info));
@@ -1102,8 +1150,10 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
     // Precision schedule (next_level): the class only rises, BF16 -> FP32-class
     // -> final class; the stop rule and the stabilising product use final-class
     // loops only.
+    const bool refine = d->prec == PINV_PREC_FP32_REFINE;
     int level = (d->prec == PINV_PREC_MIXED_BF16 || d->prec == PINV_PREC_BF16_FP32)
-                    ? TC_BF16 : (d->prec == PINV_PREC_FP32 ? TC_FP32 : fp64_class);
+                    ? TC_BF16 : ((d->prec == PINV_PREC_FP32 || refine) ? TC_FP32 : fp64_class);
+    bool refine_now = false;  // the FP32-class loops of the refine schedule have ended
     int prev_prec = -1;
     double prev_rel = INFINITY;   // relative step of the last loop (schedule input)
     bool bf16_ran = false;
@@ -1167,6 +1217,9 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         // most a factor 18 (|p(r)| <= 18 for |r| <= 1)
         const double rel = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
         if (rel > 1e3 && k > 0) { status = PINV_ERR_DIVERGED; info->iters = k; break; }
+        // refine schedule: the first loop whose step is below 1 is one order-18
+        // contraction from its limit; the FP64-class order-2 steps take it from there
+        if (refine && rel < 1.0) { refine_now = true; cur ^= 1; info->iters = k + 1; info->rel_step = e; break; }
         if (d->variant == PINV_VARIANT_STABILIZED && e < switch_tol) stabilise = true;
         prev = e;
         prev_rel = rel;
@@ -1174,6 +1227,10 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         info->rel_step = e;
         cur ^= 1;
         info->iters = k + 1;
+    }
+    if (refine_now) {
+        status = refine_steps(c, cur, info, &reason);
+        if (status == PINV_ERR_CUDA || status == PINV_ERR_TIMEOUT) return info->status = status;
     }
     info->stop_reason = reason;
     c.prec_k = fp64_class;   // the finish runs in the schedule's final class
@@ -1868,7 +1925,7 @@ int pinv_solve_batched(pinv_handle* h, int count, const pinv_desc* descs, void* 
         int rc = validate(&descs[i]);
         if (rc) return rc;
         if (descs[i].kind == PINV_DRAZIN || descs[i].kind == PINV_DRAZIN_NORMAL || descs[i].host_buffers ||
-            descs[i].check)
+            descs[i].check || descs[i].prec == PINV_PREC_FP32_REFINE)
             return PINV_ERR_ARG;
     }
     // the caller's stream is ordered before the groups' streams
@@ -1918,7 +1975,8 @@ int pinv_submit(pinv_handle* h, const pinv_desc* desc, uint64_t* id) {
     if (!h || !desc || !id) return PINV_ERR_ARG;
     int rc = validate(desc);
     if (rc) return rc;
-    if (desc->kind == PINV_DRAZIN || desc->kind == PINV_DRAZIN_NORMAL || desc->host_buffers || desc->check)
+    if (desc->kind == PINV_DRAZIN || desc->kind == PINV_DRAZIN_NORMAL || desc->host_buffers || desc->check ||
+        desc->prec == PINV_PREC_FP32_REFINE)
         return PINV_ERR_ARG;
     const size_t need = group_bytes(1, pad_to(desc->m, 64), pad_to(desc->n, 64), desc->prec,
                                     desc->finish == PINV_FINISH_CLEAN, desc->kind == PINV_OUTER_G);

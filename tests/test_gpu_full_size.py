@@ -46,15 +46,30 @@ def test_moore_penrose_4096x3072_as_benchmarked(handle):
 
 
 def test_moore_penrose_4096x3072_mixed_schedule_as_benchmarked(handle):
-    """The benchmark's default: FP32-class loops while the iterate grows, then
-    FP64-class loops (the last one stabilised), alpha = 1/s_1^2, order-18 stop,
-    cleanup finish in FP64 class."""
+    """The benchmark's loop-schedule arm: FP32-class loops while the iterate
+    grows, then FP64-class loops (the last one stabilised), alpha = 1/s_1^2,
+    order-18 stop, cleanup finish in FP64 class."""
     w = W.rectangular(4096, 3072, 2304, 1.0, 1e-4, seed=1)
     alpha = 1.0 / w.s[0] ** 2
     X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp32",
                            variant="stabilized", switch_tol=0.9, finish="clean", check=True)
     assert info["status"] == 0
     assert 3 in info["precision"] and info["precision"][-1] == 4
+    rows = np.random.default_rng(0).choice(3072, 32, replace=False)
+    assert rel(X.cpu().numpy()[rows], (w.V[rows] / w.s) @ w.U.T) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9
+
+
+def test_moore_penrose_4096x3072_refinement_schedule_as_benchmarked(handle):
+    """The benchmark's default: FP32-class loops until a step falls below 1,
+    X A X in FP32 class, FP64-class order-2 steps until a step is below 1e-5,
+    alpha = 1/s_1^2, cleanup finish in FP64 class."""
+    w = W.rectangular(4096, 3072, 2304, 1.0, 1e-4, seed=1)
+    alpha = 1.0 / w.s[0] ** 2
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp32_refine",
+                           variant="stabilized", switch_tol=0.9, finish="clean", check=True)
+    assert info["status"] == 0
+    assert info["precision"][0] == 3 and info["precision"][-1] == 6 and info["stabilized_loops"] == 1
     rows = np.random.default_rng(0).choice(3072, 32, replace=False)
     assert rel(X.cpu().numpy()[rows], (w.V[rows] / w.s) @ w.U.T) <= 1e-9
     assert max(info["penrose"]) <= 1e-9
@@ -89,12 +104,28 @@ def test_drazin_2048_as_benchmarked(handle):
 
 
 def test_drazin_2048_mixed_schedule_as_benchmarked(handle):
-    """The Drazin line's default: FP32-class growth loops, then FP64-class."""
+    """The Drazin line's loop-schedule arm: FP32-class growth loops, then FP64-class."""
     d = W.drazin_index2(2048, 512, seed=2)
     X, info = handle.solve(dev(d.A), kind="drazin", drazin_index=2, alpha=0.0, tol=1e-2, stop="order18",
                            prec="fp32", finish="clean", check=True)
     assert info["status"] == 0
     assert 3 in info["precision"] and info["precision"][-1] == 4
+    B = np.zeros((2048, 2048))
+    B[:1536, :1536] = np.linalg.inv(d.C)
+    rows = np.random.default_rng(0).choice(2048, 32, replace=False)
+    ref = d.P[rows] @ B @ np.linalg.inv(d.P)
+    assert rel(X.cpu().numpy()[rows], ref) <= 1e-9
+    assert max(info["drazin"]) <= 1e-9
+
+
+def test_drazin_2048_refinement_schedule_as_benchmarked(handle):
+    """The Drazin line's default: FP32-class loops, X A X, FP64-class order-2
+    steps, the finish in FP64 class."""
+    d = W.drazin_index2(2048, 512, seed=2)
+    X, info = handle.solve(dev(d.A), kind="drazin", drazin_index=2, alpha=0.0, tol=1e-2, stop="order18",
+                           prec="fp32_refine", finish="clean", check=True)
+    assert info["status"] == 0
+    assert info["precision"][0] == 3 and info["precision"][-1] == 6
     B = np.zeros((2048, 2048))
     B[:1536, :1536] = np.linalg.inv(d.C)
     rows = np.random.default_rng(0).choice(2048, 32, replace=False)

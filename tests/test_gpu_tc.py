@@ -185,6 +185,39 @@ def test_fp32_class_schedule_on_a_rank_deficient_problem(handle, m, n, r):
     assert max(info["penrose"]) <= 1e-9
 
 
+@pytest.mark.parametrize("m,n,r", [(512, 384, 288), (300, 420, 250)])
+def test_refinement_schedule_on_a_rank_deficient_problem(handle, m, n, r):
+    """FP32-class loops until a step falls below 1, X A X in FP32 class, FP64-
+    class order-2 steps until a step is below 1e-5, then the finish: the same
+    answer as the FP64 oracle to 1e-9 on both residual sides; the record shows
+    the FP32-class loops, then the order-2 steps (code 6)."""
+    w = W.rectangular(m, n, r, 1.0, 1e-4, seed=12)
+    alpha = 1.0 / w.s[0] ** 2
+    ref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-2, stop=H.STOP_ORDER18, alpha=alpha,
+                     finish="moore_penrose")
+    X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp32_refine",
+                           variant="stabilized", switch_tol=0.9, finish="clean", check=True)
+    assert info["status"] == 0
+    prec = info["precision"]
+    loops = [p for p in prec if p == 3]
+    steps = [e for p, e in zip(prec, info["history"]) if p == 6]
+    assert prec == loops + [6] * len(steps) and 1 <= len(steps) <= 3
+    assert steps[-1] < 1e-5 and info["stabilized_loops"] == 1
+    assert rel(X.cpu().numpy(), ref) <= 1e-9
+    assert rel(X.cpu().numpy(), pinv_closed_form(w)) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9
+
+
+def test_refinement_schedule_needs_the_finish_and_a_single_solve(handle):
+    w = W.rectangular(96, 64, 48, 1.0, 1e-2, seed=3)
+    _, info = handle.solve(dev(w.A), alpha=1.0, prec="fp32_refine", finish="none", raise_on_error=False)
+    assert info["status"] == -1
+    from paper_1604_07893_gb300._lib import PinvError
+    with pytest.raises(PinvError) as e:
+        handle.solve_batched([dev(w.A)], alpha=1.0, prec="fp32_refine", finish="clean")
+    assert e.value.code == -1
+
+
 def test_mixed_solve_spd(handle):
     s = W.spd(512, 1e-3, 1.0, seed=5)
     alpha = 1.0 / s.lam.max()          # BF16 loops need alpha <= 1/lambda_max
@@ -335,6 +368,24 @@ def test_drazin_fp32_class_schedule_parity(handle, n, nil):
                            finish="clean", prec="fp32", check=True)
     assert info["status"] == 0
     assert info["precision"][0] == 3 and info["precision"][-1] == 4
+    assert rel(X.cpu().numpy(), ref) <= 1e-9
+    assert rel(X.cpu().numpy(), drazin_closed_form(d)) <= 1e-9
+    assert max(info["drazin"]) <= 1e-9
+
+
+@pytest.mark.parametrize("n,nil", [(256, 64), (600, 150)])
+def test_drazin_refinement_schedule_parity(handle, n, nil):
+    """The Drazin family in the refinement schedule (FP32-class loops, X A X,
+    FP64-class order-2 steps, the finish in FP64 class): within 1e-9 of the
+    FP64 oracle and of the closed form, Drazin residuals below 1e-9."""
+    d = W.drazin_index2(n, nil, seed=2)
+    alpha = 1.0 / np.trace(np.linalg.matrix_power(d.A, 3))
+    ref, _ = H.solve(d.A, H.x0_drazin(d.A, 2, alpha), tol=1e-2, stop=H.STOP_ORDER18, alpha=alpha,
+                     finish="drazin", drazin_index=2)
+    X, info = handle.solve(dev(d.A), kind="drazin", drazin_index=2, alpha=0.0, tol=1e-2, stop="order18",
+                           finish="clean", prec="fp32_refine", check=True)
+    assert info["status"] == 0
+    assert info["precision"][0] == 3 and info["precision"][-1] == 6
     assert rel(X.cpu().numpy(), ref) <= 1e-9
     assert rel(X.cpu().numpy(), drazin_closed_form(d)) <= 1e-9
     assert max(info["drazin"]) <= 1e-9
