@@ -114,22 +114,26 @@ typedef enum {
     PINV_PREC_FP32_REFINE = 6 /* FP32-class loops of Eq. PM while the step is >= 1;
                                  the first loop whose step is below 1 is followed
                                  by X <- X A X in FP32 class (Section 7's stabilising
-                                 product, counted in stabilized_loops), then FP64-
-                                 class order-2 refinement steps X <- X + (I - XA) X
-                                 (Eq. hyper, p = 2; R formed in FP64 class) until a
-                                 step's relative Frobenius change is below 1e-5
-                                 (at most 8 steps), then the finish; `stop` and
+                                 product, counted in stabilized_loops), then order-2
+                                 refinement steps X <- X + (I - XA) X (Eq. hyper,
+                                 p = 2): the first in FP32 class, the others in
+                                 FP64 class (R formed in FP64 class) until one's
+                                 relative Frobenius change e_j, or the square of
+                                 the previous step's e_{j-1} (each step squares
+                                 the range error), is below 1e-5 (at most 8
+                                 steps), then the finish; `stop` and
                                  `tol` are not used (the loops end at that switch,
                                  max_iter still bounds them).  Each refinement step squares the
                                  error of the range block, so two of them (4
-                                 products) replace the FP64-class order-18 loop
-                                 (7 or 9 products) of PINV_PREC_FP32.  Single
+                                 products, 2 of them FP64-class) replace the
+                                 FP64-class order-18 loop (7 or 9 products) of
+                                 PINV_PREC_FP32.  Single
                                  solves only (pinv_solve, pinv_solve_complex):
                                  the batched and served calls return PINV_ERR_ARG.
                                  Requires finish = PINV_FINISH_CLEAN and alpha <=
                                  1/sigma_max^2, as PINV_PREC_FP32.  The steps are
                                  recorded after the loops in info->history with
-                                 precision code 6                              */
+                                 precision codes 5 (FP32 class) and 6 (FP64)    */
 } pinv_prec;
 
 typedef enum {
@@ -260,8 +264,9 @@ typedef struct {
     double tensor_flops;     /* BF16 tensor-core flops issued: 2 M N K per slice product */
     double history[PINV_HISTORY];  /* stop measure per loop                          */
     signed char precision[PINV_HISTORY]; /* per loop: 0 FP64, 1 BF16, 3 FP32-class,
-                                            4 FP64-class; 6 an FP64-class order-2
-                                            refinement step (PINV_PREC_FP32_REFINE) */
+                                            4 FP64-class; 5 / 6 an FP32- / FP64-
+                                            class order-2 refinement step
+                                            (PINV_PREC_FP32_REFINE)              */
 } pinv_info;
 
 typedef struct pinv_handle pinv_handle;

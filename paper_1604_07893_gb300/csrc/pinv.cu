@@ -1080,9 +1080,16 @@ int precond_one(pinv_handle* h, const pinv_precond_desc* p, cudaStream_t st, pin
 //     rounding outside R(X) and N(X), which an order-2 step would double
 //     (order p multiplies the blocks the iteration does not contract by p,
 //     Theorem 6.2);
-//  2. order-2 steps X <- X + (I - XA) X (Eq. hyper, p = 2) in FP64 class: the
-//     step's relative change e is the error of its input, its output's range
-//     error is about e^2, so the steps stop after the first with e < 1e-5.
+//  2. order-2 steps X <- X + (I - XA) X (Eq. hyper, p = 2): the step's
+//     relative change e_j bounds the error of its input in the range, and each
+//     step squares that error, so the input error of step j is also below
+//     e_{j-1}^2.  The steps stop after the first FP64-class one with
+//     min(e_j, e_{j-1}^2) < 1e-5: its output's range error is below the square
+//     of that.  (On a Drazin problem e_j keeps a part that does not contract,
+//     from the block of the nilpotent part that the finish removes; there the
+//     e_{j-1}^2 bound ends the steps.)  The first step runs in FP32 class: its
+//     input error (~1e-3 after the loop) squared is still far above its own
+//     rounding, which the next, FP64-class step squares away in turn.
 // The kept iterate ends in X[cur].  Returns PINV_OK, or an error status.
 constexpr int kRefineMaxSteps = 8;
 constexpr double kRefineTol = 1e-5;
@@ -1092,9 +1099,10 @@ int refine_steps(Ctx& c, int& cur, pinv_info* info, int* reason) {
     int parts = stabilise_f64(c, c.X[cur], c.X[cur ^ 1], c.X[2]);
     if (parts < 0) return PINV_ERR_CUDA;
     ++info->stabilized_loops;
-    c.prec_k = TC_FP64;
     const double* src = c.X[2];
+    double prev_e = INFINITY;
     for (int j = 0; j < kRefineMaxSteps; ++j) {
+        c.prec_k = j == 0 ? TC_FP32 : TC_FP64;
         parts = ns_step_f64(c, src, c.X[cur ^ 1]);
         if (parts < 0) return PINV_ERR_CUDA;
         double dx2, x2;
@@ -1106,13 +1114,14 @@ int refine_steps(Ctx& c, int& cur, pinv_info* info, int* reason) {
         const int k = info->loops_run++;
         if (k < PINV_HISTORY) {
             info->history[k] = e;
-            info->precision[k] = 6;
+            info->precision[k] = j == 0 ? 5 : 6;
         }
         ++info->iters;
         info->rel_step = e;
         if (!std::isfinite(e)) return PINV_ERR_NONFINITE;
         if (e > 1e3) return PINV_ERR_DIVERGED;
-        if (e < kRefineTol) { *reason = 0; return PINV_OK; }
+        if (j > 0 && std::min(e, prev_e * prev_e) < kRefineTol) { *reason = 0; return PINV_OK; }
+        prev_e = e;
     }
     *reason = 2;
     return PINV_ERR_MAXITER;

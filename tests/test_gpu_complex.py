@@ -78,6 +78,23 @@ def test_complex_mp_rank_deficient_with_finish(handle, variant):
     assert max(H.penrose_residuals(w.A, host(X))) < 1e-9
 
 
+def test_complex_refinement_schedule_rank_deficient(handle):
+    """The refinement schedule on a complex rank-deficient problem (kappa 1e4,
+    alpha = 1/s_1^2): FP32-class loops, X A X, order-2 steps and the finish on
+    the real embedding give the oracle's answer and the closed form to 1e-9."""
+    w = W.rectangular_complex(300, 200, 150, 1.0, 1e-4, seed=22)
+    alpha = 1.0 / w.s[0] ** 2
+    X, info = handle.solve_complex(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp32_refine",
+                                   variant="stabilized", switch_tol=0.9, finish="clean", check=True)
+    assert info["status"] == 0
+    assert info["precision"][0] == 3 and info["precision"][-1] == 6
+    assert rel(host(X), pinv_closed_form(w)) < 1e-9
+    assert max(info["penrose"]) < 1e-9
+    oref, _ = H.solve(w.A, H.x0_moore_penrose(w.A, alpha), tol=1e-2, stop=H.STOP_ORDER18, alpha=alpha,
+                      finish="moore_penrose")
+    assert rel(host(X), oref) < 1e-9
+
+
 def test_complex_alpha_recipe_uses_complex_moduli(handle):
     w = W.rectangular_complex(40, 28, None, 1.0, 1e-2, seed=21)
     X, info = handle.solve_complex(dev(w.A), alpha=0.0, tol=1e-12)

@@ -62,8 +62,8 @@ def test_moore_penrose_4096x3072_mixed_schedule_as_benchmarked(handle):
 
 def test_moore_penrose_4096x3072_refinement_schedule_as_benchmarked(handle):
     """The benchmark's default: FP32-class loops until a step falls below 1,
-    X A X in FP32 class, FP64-class order-2 steps until a step is below 1e-5,
-    alpha = 1/s_1^2, cleanup finish in FP64 class."""
+    X A X in FP32 class, one FP32-class order-2 step, FP64-class order-2 steps
+    until a step is below 1e-5, alpha = 1/s_1^2, cleanup finish in FP64 class."""
     w = W.rectangular(4096, 3072, 2304, 1.0, 1e-4, seed=1)
     alpha = 1.0 / w.s[0] ** 2
     X, info = handle.solve(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp32_refine",
@@ -77,11 +77,24 @@ def test_moore_penrose_4096x3072_refinement_schedule_as_benchmarked(handle):
 
 def test_complex_moore_penrose_2048x1536_as_benchmarked(handle):
     """Complex rank 1152, s log-spaced in [1e-4, 1] (the complex workload of the
-    benchmark: its embedding has the headline's 4096 x 3072 shape)."""
+    benchmark, its FP64-class arm: its embedding has the headline's 4096 x 3072
+    shape)."""
     w = W.rectangular_complex(2048, 1536, 1152, 1.0, 1e-4, seed=1)
     alpha = 2.0 / (w.s[0] ** 2 + w.s[-1] ** 2)
     X, info = handle.solve_complex(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp64_tc",
                                    variant="stabilized", switch_tol=0.5, finish="clean", check=True)
+    assert info["status"] == 0
+    rows = np.random.default_rng(0).choice(1536, 32, replace=False)
+    assert rel(X.cpu().numpy()[rows], (w.V[rows] / w.s) @ w.U.conj().T) <= 1e-9
+    assert max(info["penrose"]) <= 1e-9
+
+
+def test_complex_moore_penrose_2048x1536_refinement_as_benchmarked(handle):
+    """The complex line's default: the refinement schedule with alpha = 1/s_1^2."""
+    w = W.rectangular_complex(2048, 1536, 1152, 1.0, 1e-4, seed=1)
+    alpha = 1.0 / w.s[0] ** 2
+    X, info = handle.solve_complex(dev(w.A), alpha=alpha, tol=1e-2, stop="order18", prec="fp32_refine",
+                                   variant="stabilized", switch_tol=0.9, finish="clean", check=True)
     assert info["status"] == 0
     rows = np.random.default_rng(0).choice(1536, 32, replace=False)
     assert rel(X.cpu().numpy()[rows], (w.V[rows] / w.s) @ w.U.conj().T) <= 1e-9
@@ -126,6 +139,8 @@ def test_drazin_2048_refinement_schedule_as_benchmarked(handle):
                            prec="fp32_refine", finish="clean", check=True)
     assert info["status"] == 0
     assert info["precision"][0] == 3 and info["precision"][-1] == 6
+    # the e_{j-1}^2 bound ends the steps: one FP32-class, one or two FP64-class
+    assert info["precision"].count(5) == 1 and 1 <= info["precision"].count(6) <= 2
     B = np.zeros((2048, 2048))
     B[:1536, :1536] = np.linalg.inv(d.C)
     rows = np.random.default_rng(0).choice(2048, 32, replace=False)

@@ -17,10 +17,11 @@ iteration tolerates in its early loops:
   lands in the null block, which grows by 18 per loop (Theorem 6.2) faster
   than the finish can remove it.
 * The refinement schedule: the same FP32-class loops up to the first step
-  below 1, X A X in FP32 class, then FP64-class order-2 steps until a step is
-  below 1e-5 (two here), then the finish: within 3e-12 of A^+ as well.
-  Without the X A X the second order-2 step measures the doubled null-block
-  rounding (~1e-4), not the squared range error, so that stop test needs it.
+  below 1, X A X in FP32 class, one FP32-class order-2 step, then FP64-class
+  order-2 steps until min(step, previous step^2) < 1e-5 (one here), then the
+  finish: within 3e-12 of A^+ as well.  Without the X A X the second order-2
+  step measures the doubled null-block rounding (~1e-4), not the squared
+  range error.
 * On a full-rank problem (no null block) BF16 growth loops are harmless.
 * On the Drazin family (index 2: a nilpotent block, on which I - AX keeps the
   eigenvalue 1), FP32-class growth loops then FP64 class meet the FP64
@@ -170,8 +171,9 @@ def test_fp32_class_growth_loops_then_fp64_class_meet_the_fp64_accuracy(rank_def
 
 def _refine(w, alpha, with_xax=True):
     """FP32-class loops while the step is >= 1 (the loop that first steps below
-    1 included), X A X in FP32 class, FP64-class order-2 steps until a step is
-    below 1e-5 (at most 8), the finish in FP64 class."""
+    1 included), X A X in FP32 class, one FP32-class order-2 step, FP64-class
+    order-2 steps until min(step, previous step^2) < 1e-5 (at most 8), the
+    finish in FP64 class."""
     A = w.A
     side = H.choose_side(*A.shape)
     f32, f64 = PM.CLASSES["fp32_class"], PM.CLASSES["fp64_class"]
@@ -186,11 +188,11 @@ def _refine(w, alpha, with_xax=True):
     if with_xax:
         X = PM.xax(A, X, f32, side)
     steps = []
-    for _ in range(8):
-        Xn = PM.order2_step(A, X, f64, side)
+    for j in range(8):
+        Xn = PM.order2_step(A, X, f32 if j == 0 else f64, side)
         steps.append(float(np.linalg.norm(Xn - X) / np.linalg.norm(X)))
         X = Xn
-        if steps[-1] < 1e-5:
+        if j > 0 and min(steps[-1], steps[-2] ** 2) < 1e-5:
             break
     X = PM.finish_moore_penrose(A, X, f64, side, "order2")
     return rel(X, pinv_closed_form(w)), float(max(H.penrose_residuals(A, X))), loops, steps
@@ -200,16 +202,17 @@ def test_refinement_schedule_meets_the_fp64_accuracy(rank_deficient):
     w = rank_deficient
     err, pen, loops, steps = _refine(w, 1.0 / w.s[0] ** 2)
     assert len(loops) == 7 and loops[-1] < 1.0 <= loops[-2]
-    # two order-2 steps: the first measures the loop's error (~1e-3), the
-    # second its square
+    # two order-2 steps: the first (FP32 class) measures the loop's error
+    # (~1e-3), the second (FP64 class) its square
     assert len(steps) == 2 and 1e-4 < steps[0] < 1e-2 and steps[1] < 1e-5
     assert err <= 3e-12 and pen <= 1e-9
 
 
-def test_refinement_stop_test_needs_the_stabilising_product(rank_deficient):
+def test_refinement_without_the_stabilising_product_sees_the_doubled_block(rank_deficient):
     """Without X A X the order-2 steps double the FP32-class rounding outside
     the range (order p multiplies that block by p, Theorem 6.2), so the second
-    step's change stays near the first's instead of falling to its square."""
+    step's change stays near the first's instead of falling to its square; the
+    square of the first step's change is what bounds the range error then."""
     w = rank_deficient
     _, _, _, steps = _refine(w, 1.0 / w.s[0] ** 2, with_xax=False)
     assert steps[1] > 1e-4
