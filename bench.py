@@ -411,7 +411,8 @@ def run_ours(args):
         "accuracy": {"penrose_max": penrose, "sampled_rows_rel_err": row_err, "meets_1e-9": ok,
                      "loops": infos[-1]["iters"], "stabilized_loops": infos[-1]["stabilized_loops"],
                      "loop_classes": ["fp64" if p == 0 else {1: "bf16", 3: "fp32-class", 4: "fp64-class", 5: "fp32-class order-2", 6: "fp64-class order-2"}[p]
-                                      for p in infos[-1]["precision"]]},
+                                      for p in infos[-1]["precision"]],
+                     "step_measures": infos[-1]["history"]},
         "e2e": {"value": world / e2e_s if ok else 0.0, "unit": UNIT,
                 "h2d_bytes_per_step": M * N * 8, "d2h_bytes_per_step": N * M * 8},
         "gpu_launches": sum(i["kernels"] for i in infos),
@@ -572,7 +573,8 @@ def run_drazin(args):
                      "loops": info["iters"], "drazin_residuals": cinfo["drazin"], "sampled_rows_rel_err": err,
                      "meets_1e-9": bool(err <= 1e-9 and max(cinfo["drazin"]) <= 1e-9),
                      "loop_classes": ["fp64" if p == 0 else {1: "bf16", 3: "fp32-class", 4: "fp64-class", 5: "fp32-class order-2", 6: "fp64-class order-2"}[p]
-                                      for p in info["precision"]]}
+                                      for p in info["precision"]],
+                     "step_measures": info["history"]}
         if prec == "fp32_refine":
             roof = _roofline(infos)
             total_ms = sum(times)
