@@ -131,7 +131,10 @@ typedef enum {
                                  solves only (pinv_solve, pinv_solve_complex):
                                  the batched and served calls return PINV_ERR_ARG.
                                  Requires finish = PINV_FINISH_CLEAN and alpha <=
-                                 1/sigma_max^2, as PINV_PREC_FP32.  The steps are
+                                 1/sigma_max^2, as PINV_PREC_FP32, and kind
+                                 PINV_MOORE_PENROSE or PINV_DRAZIN (the X A X
+                                 finish of a general G leaves the FP32-class
+                                 rounding: PINV_ERR_ARG).  The steps are
                                  recorded after the loops in info->history with
                                  precision codes 5 (FP32 class) and 6 (FP64)    */
 } pinv_prec;

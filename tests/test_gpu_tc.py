@@ -209,9 +209,12 @@ def test_refinement_schedule_on_a_rank_deficient_problem(handle, m, n, r):
     assert max(info["penrose"]) <= 1e-9
 
 
-def test_refinement_schedule_needs_the_finish_and_a_single_solve(handle):
+def test_refinement_schedule_needs_the_finish_a_single_solve_and_its_kinds(handle):
     w = W.rectangular(96, 64, 48, 1.0, 1e-2, seed=3)
     _, info = handle.solve(dev(w.A), alpha=1.0, prec="fp32_refine", finish="none", raise_on_error=False)
+    assert info["status"] == -1
+    _, info = handle.solve(dev(w.A), kind="outer_g", G=dev(np.ascontiguousarray(w.A.T)), alpha=1.0,
+                           prec="fp32_refine", finish="clean", raise_on_error=False)
     assert info["status"] == -1
     from paper_1604_07893_gb300._lib import PinvError
     with pytest.raises(PinvError) as e:
