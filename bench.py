@@ -638,8 +638,11 @@ def run_batched(args):
     h = Handle(0)
     st = torch.cuda.current_stream()
 
+    # order-18 stop (R12): the loop whose step is below 1e-2 has reached the
+    # final class's rounding floor, and its result is kept
     def run(prec, tol):
-        descs = (Desc * count)(*[h.make_desc(A, X, alpha=1.0 / w.s[0] ** 2, tol=tol, prec=prec, finish="clean")
+        descs = (Desc * count)(*[h.make_desc(A, X, alpha=1.0 / w.s[0] ** 2, tol=tol, stop="order18", prec=prec,
+                                             finish="clean")
                                  for A, X, w in zip(As, Xs, ws)])
         infos = (Info * count)()
         torch.cuda.synchronize()
@@ -648,26 +651,27 @@ def run_batched(args):
         torch.cuda.synchronize()
         return rc, time.perf_counter() - t0, infos
 
-    run("bf16_fp32", 1e-6)     # warm-up (allocations, tensor maps)
+    run("bf16_fp32", 1e-2)     # warm-up (allocations, tensor maps)
     times = []
     for _ in range(args.steps):
-        rc, t, infos = run("bf16_fp32", 1e-6)
+        rc, t, infos = run("bf16_fp32", 1e-2)
         times.append(t)
     sample = np.random.default_rng(0).choice(count, 64, replace=False)
     errs = [float(np.linalg.norm(Xs[i].cpu().numpy() - (ws[i].V / ws[i].s) @ ws[i].U.T) /
                   np.linalg.norm((ws[i].V / ws[i].s) @ ws[i].U.T)) for i in sample]
     loops = [infos[i].iters for i in range(count)]
-    rc64, t64, _ = run("fp64", 1e-12)
+    rc64, t64, _ = run("fp64", 1e-2)
     # per-matrix FP64 solves on a sample, extrapolated
     t0 = time.perf_counter()
     for i in sample[:32]:
-        h.solve(As[i], Xs[i], alpha=1.0 / ws[i].s[0] ** 2, tol=1e-12, prec="fp64")
+        h.solve(As[i], Xs[i], alpha=1.0 / ws[i].s[0] ** 2, tol=1e-2, stop="order18", prec="fp64")
     torch.cuda.synchronize()
     per_matrix = (time.perf_counter() - t0) / 32
     t0 = time.perf_counter()
     for i in sample[:8]:
         w = ws[i]
-        H.solve(w.A, H.x0_moore_penrose(w.A, 1.0 / w.s[0] ** 2), tol=1e-12, alpha=1.0 / w.s[0] ** 2)
+        H.solve(w.A, H.x0_moore_penrose(w.A, 1.0 / w.s[0] ** 2), tol=1e-2, stop=H.STOP_ORDER18,
+                alpha=1.0 / w.s[0] ** 2)
     t_cpu = (time.perf_counter() - t0) / 8
     t = statistics.median(times)
     # roofline of the batch: the tensor-core work every instance's products
@@ -687,7 +691,7 @@ def run_batched(args):
            "n_gpus": 1, "higher_is_better": True, "data": "synthetic", "dtype": "bf16 + bf16 slices",
            "config": {"workload": f"uneven_batch_{count}", "m": [32, 512], "n": [16, "m"],
                       "prec": "bf16_fp32 (BF16 growth loops, FP32-class loops, FP32-class projection + order-18 loop)",
-                      "tol": 1e-6,
+                      "stop": "order18", "tol": 1e-2,
                       "finish": "clean",
                       "steps": args.steps},
            "ms_per_batch": t * 1e3, "status_ok": sum(1 for i in range(count) if infos[i].status == 0),
@@ -816,7 +820,7 @@ def run_serving(args):
             if k == 0:
                 spd[n] = (Q, lam)
     torch.cuda.synchronize()
-    kw = dict(kind="outer_g", alpha=1.0, tol=1e-6, prec="bf16_fp32", symmetric=True)
+    kw = dict(kind="outer_g", alpha=1.0, tol=1e-2, stop="order18", prec="bf16_fp32", symmetric=True)
     # warm-up (untimed): every size alone, then a short stream, so the
     # stream-ordered pool has grown to what the timed streams need
     for n in mats:
@@ -847,7 +851,7 @@ def run_serving(args):
     for n in (256, 512):
         A = mats[n][0][0].cpu().numpy()
         t0 = time.perf_counter()
-        H.solve(A, np.eye(n), tol=1e-6, alpha=1.0)
+        H.solve(A, np.eye(n), tol=1e-2, stop=H.STOP_ORDER18, alpha=1.0)
         cpu_s[n] = time.perf_counter() - t0
     A = mats[1024][0][0].cpu().numpy()
     t0 = time.perf_counter()
@@ -861,7 +865,7 @@ def run_serving(args):
            "data": "synthetic", "dtype": "bf16 + bf16 slices (fp32-class)",
            "config": {"workload": "serving_spd_poisson2000", "sizes": [256, 512, 1024, 2048, 4096, 8192],
                       "weights": [0.40, 0.25, 0.15, 0.10, 0.07, 0.03], "hbm_budget_gb": 120, "max_queued": 32,
-                      "tol": 1e-6, "prec": "bf16_fp32 (BF16 growth loops, FP32-class to the end)",
+                      "stop": "order18", "tol": 1e-2, "prec": "bf16_fp32 (BF16 growth loops, FP32-class to the end)",
                       "symmetric": True, "duration_s": duration},
            "offered_2000_per_s": s1, "sustainable": {"rate": rate2, **s2},
            "latency_ms": s1["latency_ms"], "roofline": s1["roofline"],

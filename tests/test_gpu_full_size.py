@@ -158,7 +158,8 @@ def test_uneven_batch_4096_as_benchmarked(handle):
     ws = W.uneven_batch_fast(4096, seed=3)
     As = [dev(w.A) for w in ws]
     Xs = [torch.empty(w.A.shape[1], w.A.shape[0], dtype=torch.float64, device="cuda") for w in ws]
-    descs = (Desc * len(ws))(*[handle.make_desc(A, X, alpha=1.0 / w.s[0] ** 2, tol=1e-6, prec="bf16_fp32",
+    descs = (Desc * len(ws))(*[handle.make_desc(A, X, alpha=1.0 / w.s[0] ** 2, tol=1e-2, stop="order18",
+                                                prec="bf16_fp32",
                                                 finish="clean") for A, X, w in zip(As, Xs, ws)])
     infos = (Info * len(ws))()
     rc = handle._lib.pinv_solve_batched(handle._h, len(ws), descs, C.c_void_p(0), infos)
@@ -181,7 +182,7 @@ def test_serving_sizes_256_to_8192(handle):
         A = (0.5 * (A + A.T)).contiguous()
         X = torch.empty(n, n, dtype=torch.float64, device="cuda")
         rid = handle.submit(A, X, G=torch.eye(n, dtype=torch.float64, device="cuda"), kind="outer_g", alpha=1.0,
-                            tol=1e-6, prec="bf16_fp32", symmetric=True)
+                            tol=1e-2, stop="order18", prec="bf16_fp32", symmetric=True)
         reqs.append((rid, n, Q, lam, X, A))
     pending = {r[0] for r in reqs}
     status = {}
