@@ -143,6 +143,19 @@ def test_model_loop_equals_the_naive_step_in_fp64():
         assert rel(got, want) < 1e-13
 
 
+def test_order2_step_squares_the_residual():
+    """Eq. hyper with p = 2: X' = X + X R (R = I - AX) gives I - AX' = R^2
+    exactly in exact arithmetic (left side: I - X'A = (I - XA)^2)."""
+    w = W.rectangular(40, 30, None, 1.0, 1e-1, seed=6)
+    X = H.x0_moore_penrose(w.A, 1.0 / w.s[0] ** 2)
+    R = np.eye(40) - w.A @ X
+    Xr = PM.order2_step(w.A, X, PM.CLASSES["fp64"], "right")
+    assert np.abs((np.eye(40) - w.A @ Xr) - R @ R).max() < 1e-14
+    L = np.eye(30) - X @ w.A
+    Xl = PM.order2_step(w.A, X, PM.CLASSES["fp64"], "left")
+    assert np.abs((np.eye(30) - Xl @ w.A) - L @ L).max() < 1e-14
+
+
 # ---------------------------------------------------------------- schedules
 
 @pytest.fixture(scope="module")
@@ -252,6 +265,34 @@ def _drazin_schedule(d, classes):
     if not np.all(np.isfinite(X)):
         return np.inf, steps
     return rel(X, drazin_closed_form(d)), steps
+
+
+def test_drazin_refinement_schedule(drazin_family):
+    """FP32-class loops to the first step below 1, X A X, one FP32-class and
+    then FP64-class order-2 steps until min(step, previous step^2) < 1e-5, the
+    Drazin finish: the FP64 accuracy of the loop schedule."""
+    d = drazin_family
+    A = d.A
+    f32, f64 = PM.CLASSES["fp32_class"], PM.CLASSES["fp64_class"]
+    X = H.x0_drazin(A, 2)
+    for _ in range(20):
+        Xn = PM.pm_loop(A, X, f32, "right")
+        step = float(np.linalg.norm(Xn - X) / np.linalg.norm(X))
+        X = Xn
+        if step < 1.0:
+            break
+    X = PM.xax(A, X, f32, "right")
+    steps = []
+    for j in range(8):
+        Xn = PM.order2_step(A, X, f32 if j == 0 else f64, "right")
+        steps.append(float(np.linalg.norm(Xn - X) / np.linalg.norm(X)))
+        X = Xn
+        if j > 0 and min(steps[-1], steps[-2] ** 2) < 1e-5:
+            break
+    X = PM.finish_drazin(A, X, 2, f64)
+    ref, _ = _drazin_schedule(d, ["fp64_class"] * 5)
+    assert len(steps) <= 4
+    assert rel(X, drazin_closed_form(d)) <= max(1e-13, 2 * ref)
 
 
 def test_drazin_fp32_class_growth_loops_then_fp64_class(drazin_family):
