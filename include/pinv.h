@@ -120,7 +120,7 @@ typedef enum {
                                  FP64 class (R formed in FP64 class) until one's
                                  relative Frobenius change e_j, or the square of
                                  the previous step's e_{j-1} (each step squares
-                                 the range error), is below 1e-5 (at most 8
+                                 the range error), is below 1e-5 (at most 16
                                  steps), then the finish; `stop` and
                                  `tol` are not used (the loops end at that switch,
                                  max_iter still bounds them).  Each refinement step squares the

@@ -1096,7 +1096,7 @@ int precond_one(pinv_handle* h, const pinv_precond_desc* p, cudaStream_t st, pin
 //     input error (~1e-3 after the loop) squared is still far above its own
 //     rounding, which the next, FP64-class step squares away in turn.
 // The kept iterate ends in X[cur].  Returns PINV_OK, or an error status.
-constexpr int kRefineMaxSteps = 8;
+constexpr int kRefineMaxSteps = 16;   // from an error near 1, eleven steps reach 1e-9
 constexpr double kRefineTol = 1e-5;
 
 int refine_steps(Ctx& c, int& cur, pinv_info* info, int* reason) {
