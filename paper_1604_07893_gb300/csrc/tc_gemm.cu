@@ -962,11 +962,6 @@ __device__ __forceinline__ void slice_tile(const SliceOp& o, int bx, int by, int
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = t[(tid & 7) * 8 + j][il];
-    } else if (i < rows && kb + 8 <= K &&
-               (reinterpret_cast<uintptr_t>(X + (size_t)i * ld + kb) & 31) == 0) {
-        // the 8 values in two 32-byte loads (an aligned row segment wholly inside K)
-        ld_global_v4(X + (size_t)i * ld + kb, v);
-        ld_global_v4(X + (size_t)i * ld + kb + 4, v + 4);
     } else {
 #pragma unroll
         for (int j = 0; j < 8; ++j) v[j] = (i < rows && kb + j < K) ? X[(size_t)i * ld + kb + j] : 0.0;
