@@ -4,7 +4,8 @@
 
 m ~ U{32..512}, n ~ U{16..m}, rank n, singular values log-uniform in
 [1e-3, 1] (Householder-product factors), alpha = 1/s_1^2, BF16 growth loops
-then FP32-class loops and an FP32-class finish (PINV_PREC_BF16_FP32, tol 1e-6):
+then FP32-class loops and an FP32-class finish (PINV_PREC_BF16_FP32), the
+order-18 stop at 1e-2 (`--stop rel_fro`: the relative-step stop at 1e-6):
 the settings of the batched workload line.  Prints, per call, the wall time
 around the call (device synchronised on both sides), the tensor-core work the
 instances' products executed and the loop counts.
@@ -26,6 +27,7 @@ def main():
     ap.add_argument("--count", type=int, default=1024)
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--seed", type=int, default=3)
+    ap.add_argument("--stop", default="order18", choices=["order18", "rel_fro"])
     a = ap.parse_args()
     ws = W.uneven_batch_fast(a.count, seed=a.seed)
     As = [torch.from_numpy(w.A).cuda() for w in ws]
@@ -33,8 +35,9 @@ def main():
     h = Handle(0)
     st = torch.cuda.current_stream()
     for r in range(a.reps):
-        descs = (Desc * a.count)(*[h.make_desc(A, X, alpha=1.0 / w.s[0] ** 2, tol=1e-6, prec="bf16_fp32",
-                                               finish="clean") for A, X, w in zip(As, Xs, ws)])
+        tol = 1e-2 if a.stop == "order18" else 1e-6
+        descs = (Desc * a.count)(*[h.make_desc(A, X, alpha=1.0 / w.s[0] ** 2, tol=tol, stop=a.stop,
+                                               prec="bf16_fp32", finish="clean") for A, X, w in zip(As, Xs, ws)])
         infos = (Info * a.count)()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
