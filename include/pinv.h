@@ -136,7 +136,8 @@ typedef enum {
                                  finish of a general G leaves the FP32-class
                                  rounding: PINV_ERR_ARG).  The steps are
                                  recorded after the loops in info->history with
-                                 precision codes 5 (FP32 class) and 6 (FP64)    */
+                                 precision codes 5 (FP32 class) and 6 (FP64) and
+                                 counted in iters and loops_run                 */
 } pinv_prec;
 
 typedef enum {
