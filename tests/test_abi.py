@@ -109,3 +109,37 @@ int use(void) {
                                                  "-Wno-unused-parameter", "-Wno-maybe-uninitialized",
                                                  "-Wno-uninitialized", "-I", os.path.dirname(HEADER),
                                                  "-c", src, "-o", os.path.join(d, f"u_{ext}.o")], check=True)
+
+
+def test_binding_enum_codes_match_the_header():
+    """The binding's name -> code tables equal the header's enum constants,
+    compiled against the header (a renumbered or added constant would
+    otherwise reach the library as another choice)."""
+    import subprocess
+    import tempfile
+    names = {
+        "KIND": {"moore_penrose": "PINV_MOORE_PENROSE", "drazin": "PINV_DRAZIN", "outer_g": "PINV_OUTER_G",
+                 "drazin_normal": "PINV_DRAZIN_NORMAL"},
+        "STOP": {"rel_fro": "PINV_STOP_REL_FRO", "paper": "PINV_STOP_PAPER", "order18": "PINV_STOP_ORDER18"},
+        "PREC": {"fp64": "PINV_PREC_FP64", "mixed_bf16": "PINV_PREC_MIXED_BF16", "mixed_fp8": "PINV_PREC_MIXED_FP8",
+                 "fp32": "PINV_PREC_FP32", "fp64_tc": "PINV_PREC_FP64_TC", "bf16_fp32": "PINV_PREC_BF16_FP32",
+                 "fp32_refine": "PINV_PREC_FP32_REFINE"},
+        "VARIANT": {"plain": "PINV_VARIANT_PLAIN", "stabilized": "PINV_VARIANT_STABILIZED"},
+        "FINISH": {"none": "PINV_FINISH_NONE", "clean": "PINV_FINISH_CLEAN"},
+    }
+    consts = [c for table in names.values() for c in table.values()]
+    src = "#include <stdio.h>\n#include \"pinv.h\"\nint main(void) {\n"
+    src += "".join(f'    printf("%d\\n", (int){c});\n' for c in consts) + "    return 0;\n}\n"
+    with tempfile.TemporaryDirectory() as d:
+        c = os.path.join(d, "e.c")
+        exe = os.path.join(d, "e")
+        open(c, "w").write(src)
+        subprocess.run(["gcc", "-I", os.path.dirname(HEADER), c, "-o", exe], check=True)
+        vals = [int(x) for x in subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()]
+    header = dict(zip(consts, vals))
+    for table, m in names.items():
+        binding = getattr(_lib, table)
+        for key, const in m.items():
+            assert binding[key] == header[const], (table, key)
+    # every code the binding offers is one the header names
+    assert set(_lib.PREC) == set(names["PREC"])
