@@ -221,6 +221,16 @@ def test_refinement_schedule_meets_the_fp64_accuracy(rank_deficient):
     assert err <= 3e-12 and pen <= 1e-9
 
 
+def test_refinement_schedule_on_the_right_residual_side():
+    """A wide rank-deficient problem (m < n: the right residual I - AX) under
+    the same refinement schedule: within 3e-12 of A^+."""
+    w = W.rectangular(300, 420, 250, 1.0, 1e-4, seed=12)
+    err, pen, loops, steps = _refine(w, 1.0 / w.s[0] ** 2)
+    assert H.choose_side(300, 420) == "right"
+    assert loops[-1] < 1.0 and len(steps) == 2
+    assert err <= 3e-12 and pen <= 1e-9
+
+
 def test_refinement_without_the_stabilising_product_sees_the_doubled_block(rank_deficient):
     """Without X A X the order-2 steps double the FP32-class rounding outside
     the range (order p multiplies that block by p, Theorem 6.2), so the second
