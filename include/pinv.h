@@ -76,7 +76,9 @@ typedef enum {
     PINV_STOP_REL_FRO = 0,   /* ||X_{k+1} - X_k||_F / ||X_k||_F < tol             */
     PINV_STOP_PAPER   = 1,   /* ||X_{k+1} - X_k||_F / (18^k alpha) < tol (Eq. stopreliable) */
     PINV_STOP_ORDER18 = 2    /* relative step < tol, with tol a threshold delta such
-                                that delta^18 is below the unit roundoff (e.g. 1e-2):
+                                that delta^18 is below the unit roundoff of the final
+                                product class (e.g. 1e-2 for FP64 class, 0.25 for
+                                FP32 class):
                                 by Theorem 3.1 (F_{k+1} = F_k^18) the loop that made
                                 that step has reached the rounding floor; its result
                                 is kept and no loop is spent observing the floor   */

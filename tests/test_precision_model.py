@@ -241,6 +241,35 @@ def test_refinement_without_the_stabilising_product_sees_the_doubled_block(rank_
     assert steps[1] > 1e-4
 
 
+@pytest.mark.parametrize("m,n,seed", [(256, 192, 21), (200, 64, 7)])
+def test_order18_stop_threshold_of_the_fp32_finished_schedule(m, n, seed):
+    """BF16 growth loops, FP32-class loops stopped by the order-18 rule, the
+    FP32-class projection and order-18 loop: delta = 0.25 (0.25^18 = 1.5e-11,
+    below the FP32 class's 2^-31) keeps the first FP32-class loop whose step is
+    below it, one loop before delta = 1e-2, at the same accuracy."""
+    w = W.rectangular(m, n, None, 1.0, 1e-3, seed=seed, spacing="loguniform")
+    A = w.A
+    side = H.choose_side(m, n)
+    f32 = PM.CLASSES["fp32_class"]
+    out = {}
+    for delta in (1e-2, 0.25):
+        X = H.x0_moore_penrose(A, 1.0 / w.s[0] ** 2)
+        cls, loops = "bf16", 0
+        for _ in range(30):
+            Xn = PM.pm_loop(A, X, PM.CLASSES[cls], side)
+            step = float(np.linalg.norm(Xn - X) / np.linalg.norm(X))
+            X, loops = Xn, loops + 1
+            if cls == "bf16":
+                if step <= 0.5:
+                    cls = "fp32_class"
+            elif step < delta:
+                break
+        X = PM.finish_moore_penrose(A, X, f32, side, "order18")
+        out[delta] = (loops, rel(X, pinv_closed_form(w)))
+    assert out[0.25][0] == out[1e-2][0] - 1
+    assert out[0.25][1] <= 1e-6 and out[0.25][1] <= 2 * out[1e-2][1]
+
+
 def test_fp32_class_loops_fail_with_the_two_sided_alpha(rank_deficient):
     w = rank_deficient
     alpha = 2.0 / (w.s[0] ** 2 + w.s[-1] ** 2)
