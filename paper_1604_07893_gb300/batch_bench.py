@@ -28,6 +28,7 @@ def main():
     ap.add_argument("--reps", type=int, default=1)
     ap.add_argument("--seed", type=int, default=3)
     ap.add_argument("--stop", default="order18", choices=["order18", "rel_fro"])
+    ap.add_argument("--tol", type=float, default=None, help="default: 0.25 (order18), 1e-6 (rel_fro)")
     a = ap.parse_args()
     ws = W.uneven_batch_fast(a.count, seed=a.seed)
     As = [torch.from_numpy(w.A).cuda() for w in ws]
@@ -35,7 +36,7 @@ def main():
     h = Handle(0)
     st = torch.cuda.current_stream()
     for r in range(a.reps):
-        tol = 0.25 if a.stop == "order18" else 1e-6
+        tol = a.tol if a.tol is not None else (0.25 if a.stop == "order18" else 1e-6)
         descs = (Desc * a.count)(*[h.make_desc(A, X, alpha=1.0 / w.s[0] ** 2, tol=tol, stop=a.stop,
                                                prec="bf16_fp32", finish="clean") for A, X, w in zip(As, Xs, ws)])
         infos = (Info * a.count)()
