@@ -555,7 +555,8 @@ int validate(const pinv_desc* d) {
     if (d->prec == PINV_PREC_FP32_REFINE && d->finish != PINV_FINISH_CLEAN) return PINV_ERR_ARG;
     // ... and only the Moore-Penrose and Drazin finishes remove the FP32-class
     // rounding outside the range (measured on a weighted Moore-Penrose problem
-    // through G: 3.9e-6 after the X A X finish, against 1e-12 for FP64 class)
+    // through G: 3.9e-6 after the X A X finish, where FP64-class products stay
+    // within 1e-9)
     if (d->prec == PINV_PREC_FP32_REFINE && d->kind != PINV_MOORE_PENROSE && d->kind != PINV_DRAZIN)
         return PINV_ERR_ARG;
     if (d->variant != PINV_VARIANT_PLAIN && d->variant != PINV_VARIANT_STABILIZED) return PINV_ERR_ARG;
@@ -1232,7 +1233,7 @@ int solve_one(pinv_handle* h, const pinv_desc* d, cudaStream_t st, pinv_info* in
         const double rel = dx2 == 0.0 ? 0.0 : (x2 > 0 ? std::sqrt(dx2 / x2) : INFINITY);
         if (rel > 1e3 && k > 0) { status = PINV_ERR_DIVERGED; info->iters = k; break; }
         // refine schedule: the first loop whose step is below 1 is one order-18
-        // contraction from its limit; the FP64-class order-2 steps take it from there
+        // contraction from its limit; the order-2 refinement steps take it from there
         if (refine && rel < 1.0) { refine_now = true; cur ^= 1; info->iters = k + 1; info->rel_step = e; break; }
         if (d->variant == PINV_VARIANT_STABILIZED && e < switch_tol) stabilise = true;
         prev = e;
